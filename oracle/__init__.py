@@ -1,0 +1,239 @@
+"""CPU oracle for the k-d tree queries of arXiv 2210.12859 (Wald).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The CUDA library never imports, links
+or loads anything from here.
+
+The arithmetic lives in ``kdt_oracle.c`` (plain C, compiled with
+``-O2 -ffp-contract=off``, no fast-math), this module only marshals numpy
+arrays.  ``ensure_built()`` compiles the shared object when it is missing or
+older than its source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kdt_oracle.c")
+_LIB = os.path.join(_HERE, "libkdt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# gcc flags: every float operation evaluated as written (no contraction into
+# fused multiply-add, which GCC does by default on aarch64), no fast-math.
+CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def ensure_built(force: bool = False) -> str:
+    """Compile ``libkdt_oracle.so`` next to its source if needed; return its path."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"], check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(ensure_built())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        i32 = ctypes.c_int
+        f32 = ctypes.c_float
+        lib.orc_left_size.argtypes = [i64]
+        lib.orc_left_size.restype = i64
+        lib.orc_build.argtypes = [P, i64, i32, P]
+        lib.orc_build.restype = i32
+        lib.orc_knn_brute.argtypes = [P, i64, i32, P, i64, i32, f32, P, P]
+        lib.orc_knn_brute.restype = None
+        lib.orc_knn_brute_f64.argtypes = [P, i64, i32, P, i64, i32, P, P]
+        lib.orc_knn_brute_f64.restype = None
+        trav = [P, P, i64, i32, P, i32, f32, i32, P, P, P, i64, P, P, i64, P]
+        lib.orc_knn_recursive.argtypes = trav
+        lib.orc_knn_recursive.restype = i32
+        lib.orc_knn_stackfree.argtypes = trav
+        lib.orc_knn_stackfree.restype = i32
+        lib.orc_knn_stackfree_batch.argtypes = [P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
+        lib.orc_knn_stackfree_batch.restype = i32
+        lib.orc_descent_leaf.argtypes = [P, P, i64, i32, P]
+        lib.orc_descent_leaf.restype = f32
+        lib.orc_round_bf16.argtypes = [f32]
+        lib.orc_round_bf16.restype = f32
+        lib.orc_mlp_forward.argtypes = [P, i32, P, i64, P]
+        lib.orc_mlp_forward.restype = None
+        lib.orc_mlp_loss_grad.argtypes = [P, i32, P, P, i64, P]
+        lib.orc_mlp_loss_grad.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def left_size(n: int) -> int:
+    """Left-subtree size of the root of a complete tree with n nodes."""
+    return int(_load().orc_left_size(int(n)))
+
+
+def build(points) -> np.ndarray:
+    """Level-order tree as node -> input index (int32[N])."""
+    pts = _f32(points)
+    N, D = pts.shape
+    out = np.empty(N, dtype=np.int32)
+    if _load().orc_build(_ptr(pts), N, D, _ptr(out)) != 0:
+        raise ValueError("oracle build failed (bad arguments or non-finite point)")
+    return out
+
+
+def knn_brute(points, queries, k: int, max_radius: float = float("inf")):
+    """Plain definition: k smallest (d2, id) with d2 <= r2, FP32 distances."""
+    pts, qs = _f32(points), _f32(queries)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float32)
+    _load().orc_knn_brute(_ptr(pts), N, D, _ptr(qs), Q, k, float(max_radius), _ptr(ids), _ptr(d2))
+    return ids, d2
+
+
+def knn_brute_threaded(points, queries, k: int, max_radius: float = float("inf"), threads: int = 0):
+    """``knn_brute`` split over host threads by query (the C call releases the GIL)."""
+    pts, qs = _f32(points), _f32(queries)
+    Q = qs.shape[0]
+    threads = threads or (os.cpu_count() or 1)
+    threads = max(1, min(threads, Q))
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float32)
+    bounds = np.linspace(0, Q, threads + 1).astype(np.int64)
+    lib = _load()
+    N, D = pts.shape
+
+    def work(a, b):
+        if b > a:
+            sub = np.ascontiguousarray(qs[a:b])
+            oi = np.empty((b - a, k), dtype=np.int32)
+            od = np.empty((b - a, k), dtype=np.float32)
+            lib.orc_knn_brute(_ptr(pts), N, D, _ptr(sub), b - a, k, float(max_radius), _ptr(oi), _ptr(od))
+            ids[a:b] = oi
+            d2[a:b] = od
+
+    ts = [threading.Thread(target=work, args=(int(bounds[i]), int(bounds[i + 1]))) for i in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return ids, d2
+
+
+def knn_brute_f64(points, queries, k: int):
+    """k smallest (d2, id) with distances of the FP32 inputs evaluated in FP64."""
+    pts, qs = _f32(points), _f32(queries)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float64)
+    _load().orc_knn_brute_f64(_ptr(pts), N, D, _ptr(qs), Q, k, _ptr(ids), _ptr(d2))
+    return ids, d2
+
+
+def _traverse(fn, points, node_pid, q, k, max_radius, ordered, log_cap):
+    pts = _f32(points)
+    node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    N, D = pts.shape
+    qv = _f32(q).reshape(D)
+    ids = np.empty(k, dtype=np.int32)
+    d2 = np.empty(k, dtype=np.float32)
+    visits = np.empty(log_cap, dtype=np.int32)
+    steps = np.empty(4 * log_cap, dtype=np.int32)
+    nv = ctypes.c_int64(0)
+    ns = ctypes.c_int64(0)
+    rc = fn(_ptr(pts), _ptr(node_pid), N, D, _ptr(qv), k, float(max_radius), int(ordered),
+            _ptr(ids), _ptr(d2), _ptr(visits), log_cap, ctypes.byref(nv), _ptr(steps),
+            4 * log_cap, ctypes.byref(ns))
+    if rc != 0:
+        raise RuntimeError("oracle traversal exceeded its step cap")
+    if nv.value > log_cap or ns.value > 4 * log_cap:
+        raise RuntimeError("visit log overflow; raise log_cap")
+    return ids, d2, visits[: nv.value].copy(), steps[: ns.value].copy()
+
+
+def knn_recursive(points, node_pid, q, k, max_radius=float("inf"), ordered=True, log_cap=None):
+    """Recursive traversal of one query: (ids, d2, first-visit log, step log)."""
+    cap = log_cap or (len(node_pid) + 8)
+    return _traverse(_load().orc_knn_recursive, points, node_pid, q, k, max_radius, ordered, cap)
+
+
+def knn_stackfree(points, node_pid, q, k, max_radius=float("inf"), ordered=True, log_cap=None):
+    """Stack-free state machine for one query: (ids, d2, first-visit log, step log)."""
+    cap = log_cap or (len(node_pid) + 8)
+    return _traverse(_load().orc_knn_stackfree, points, node_pid, q, k, max_radius, ordered, cap)
+
+
+def knn_tree(points, node_pid, queries, k, max_radius=float("inf"), ordered=True):
+    """Stack-free traversal of many queries: (ids, d2, first visits per query)."""
+    pts, qs = _f32(points), _f32(queries)
+    node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float32)
+    nv = np.empty(Q, dtype=np.int32)
+    rc = _load().orc_knn_stackfree_batch(_ptr(pts), _ptr(node_pid), N, D, _ptr(qs), Q, k,
+                                         float(max_radius), int(ordered), _ptr(ids), _ptr(d2), _ptr(nv))
+    if rc != 0:
+        raise RuntimeError("oracle traversal exceeded its step cap")
+    return ids, d2, nv
+
+
+def descent_leaf_d2(points, node_pid, queries) -> np.ndarray:
+    """FP32 squared distance to the point where the greedy close-child descent ends."""
+    pts, qs = _f32(points), _f32(queries)
+    node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    N, D = pts.shape
+    lib = _load()
+    out = np.empty(qs.shape[0], dtype=np.float32)
+    for i in range(qs.shape[0]):
+        qi = np.ascontiguousarray(qs[i])
+        out[i] = lib.orc_descent_leaf(_ptr(pts), _ptr(node_pid), N, D, _ptr(qi))
+    return out
+
+
+def round_bf16(x: float) -> float:
+    """Nearest bfloat16 value (ties to even) of a finite float, as float."""
+    return float(_load().orc_round_bf16(float(x)))
+
+
+def mlp_param_count(H: int) -> int:
+    return H * 4 + H + H * H + H + H + 1
+
+
+def mlp_forward(params, H: int, x) -> np.ndarray:
+    """FP64 forward of the 4->H->H->1 ReLU MLP (params: W1,b1,W2,b2,w3,b3)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    y = np.empty(xs.shape[0], dtype=np.float64)
+    _load().orc_mlp_forward(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y))
+    return y
+
+
+def mlp_loss_grad(params, H: int, x, label):
+    """FP64 mean-squared-error loss and its gradient w.r.t. all parameters."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    lab = np.ascontiguousarray(label, dtype=np.float64).reshape(-1)
+    g = np.empty_like(p)
+    loss = _load().orc_mlp_loss_grad(_ptr(p), H, _ptr(xs), _ptr(lab), xs.shape[0], _ptr(g))
+    return float(loss), g

@@ -1,0 +1,600 @@
+/*
+ * CPU oracle for the left-balanced k-d tree queries of Wald, "A Stack-Free
+ * Traversal Algorithm for Left-Balanced k-d Trees" (arXiv 2210.12859).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header or table with the CUDA
+ * library and is deliberately plain and slow.
+ *
+ * Compile with -O2 -ffp-contract=off and without fast-math, so that every
+ * float expression below is evaluated as written: one IEEE-754 binary32
+ * operation at a time, round-to-nearest-even, no fused multiply-add, no
+ * flush-to-zero.
+ *
+ * Contents, each citing the part of the paper it follows:
+ *   orc_left_size       subtree size of a complete tree (Sec. 3, level-order
+ *                       assumption; needed by the builder of Sec. 4)
+ *   orc_build           recursive median builder (Sec. 4: the tree any serial
+ *                       builder produces), round-robin split dimension
+ *   orc_knn_brute       plain definition of the fcp / kNN result (exact method,
+ *                       Sec. 3 "shrinking max radius"), FP32 distances
+ *   orc_knn_brute_f64   the same selection with distances in FP64
+ *   orc_knn_recursive   the recursive ordered / unordered traversal (Sec. 3.1)
+ *   orc_knn_stackfree   the (curr, prev) state machine (Sec. 3.2)
+ *   orc_descent_leaf    greedy close-child descent (feature of the learned
+ *                       radius proposal; not in the paper)
+ *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
+ *                       paper; parity target for the GPU training kernels)
+ *
+ * Parity status: every function above is pinned by tests under tests/ against
+ * values fixed by the paper (the six-point example of Figure 1), closed forms,
+ * brute force on tiny inputs, library routines and invariants.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Tree topology (Sec. 3: level order, lChild = 2n+1, rChild = 2n+2).       */
+/* ------------------------------------------------------------------------ */
+
+static int orc_level(int64_t node)
+{
+    /* level(n) = floor(log2(n + 1)) */
+    int l = 0;
+    int64_t v = node + 1;
+    while (v > 1) {
+        v >>= 1;
+        ++l;
+    }
+    return l;
+}
+
+/* Size of the left subtree of the root of a complete binary tree of n nodes
+ * whose last level is filled from the left.  h = floor(log2 n) is the depth of
+ * the last level; the levels above it hold 2^h - 1 nodes; `last` nodes sit on
+ * the last level, and the left subtree receives up to 2^(h-1) of them. */
+int64_t orc_left_size(int64_t n)
+{
+    if (n <= 1)
+        return 0;
+    int h = 0;
+    while (((int64_t)1 << (h + 1)) <= n)
+        ++h;
+    int64_t half = (int64_t)1 << (h - 1);
+    int64_t last = n - (((int64_t)1 << h) - 1);
+    return (half - 1) + (last < half ? last : half);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Builder (Sec. 4 cites a parallel builder and states that it emits the same */
+/* tree as any serial builder; this is that serial builder).                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const float *pts;
+    int D;
+    int dim;
+} orc_sort_ctx;
+
+/* order by (coordinate in `dim`, input index); float `<`, so -0 == +0 */
+static int orc_cmp_coord_idx(const void *a, const void *b, void *vctx)
+{
+    const orc_sort_ctx *c = (const orc_sort_ctx *)vctx;
+    int32_t ia = *(const int32_t *)a;
+    int32_t ib = *(const int32_t *)b;
+    float ca = c->pts[(int64_t)ia * c->D + c->dim];
+    float cb = c->pts[(int64_t)ib * c->D + c->dim];
+    if (ca < cb)
+        return -1;
+    if (cb < ca)
+        return 1;
+    return (ia > ib) - (ia < ib);
+}
+
+static int orc_build_rec(const float *pts, int64_t N, int D, int32_t *S,
+                         int64_t n, int64_t node, int32_t *node_pid)
+{
+    if (n == 0)
+        return 0;
+    if (node >= N)
+        return -1; /* subtree sizes disagree with the complete tree */
+    orc_sort_ctx ctx = {pts, D, orc_level(node) % D};
+    qsort_r(S, (size_t)n, sizeof(int32_t), orc_cmp_coord_idx, &ctx);
+    int64_t L = orc_left_size(n);
+    node_pid[node] = S[L];
+    if (orc_build_rec(pts, N, D, S, L, 2 * node + 1, node_pid))
+        return -1;
+    return orc_build_rec(pts, N, D, S + L + 1, n - L - 1, 2 * node + 2, node_pid);
+}
+
+/* node_pid[t] = input index of the point stored at level-order node t.
+ * Returns 0 on success, -1 on bad arguments or a non-finite coordinate. */
+int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
+{
+    if (N < 1 || D < 1 || D > 8)
+        return -1;
+    for (int64_t i = 0; i < N * D; ++i)
+        if (!isfinite(pts[i]))
+            return -1;
+    int32_t *S = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    if (!S)
+        return -1;
+    for (int64_t i = 0; i < N; ++i)
+        S[i] = (int32_t)i;
+    int rc = orc_build_rec(pts, N, D, S, N, 0, node_pid);
+    free(S);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Distances and the k-best list.                                           */
+/* ------------------------------------------------------------------------ */
+
+/* d2(p, q) = ((t_0 + t_1) + t_2) + ..., t_j = fl(fl(p_j - q_j)^2), FP32 */
+static float orc_d2(const float *p, const float *q, int D)
+{
+    float diff = p[0] - q[0];
+    float s = diff * diff;
+    for (int j = 1; j < D; ++j) {
+        float dj = p[j] - q[j];
+        float tj = dj * dj;
+        s = s + tj;
+    }
+    return s;
+}
+
+/* (da, ia) < (db, ib) lexicographically */
+static int orc_pair_less(float da, int32_t ia, float db, int32_t ib)
+{
+    if (da < db)
+        return 1;
+    if (db < da)
+        return 0;
+    return ia < ib;
+}
+
+typedef struct {
+    int k;
+    int count;
+    float r2;
+    float *d2;
+    int32_t *id;
+} orc_list;
+
+/* processNode of fcp / kNN: accept iff d2 <= r2 and the list has room or the
+ * pair beats the current worst; keep the list sorted ascending by (d2, id). */
+static void orc_list_offer(orc_list *L, float d2, int32_t id)
+{
+    if (!(d2 <= L->r2))
+        return;
+    if (L->count == L->k && !orc_pair_less(d2, id, L->d2[L->k - 1], L->id[L->k - 1]))
+        return;
+    int pos = L->count < L->k ? L->count : L->k - 1;
+    while (pos > 0 && orc_pair_less(d2, id, L->d2[pos - 1], L->id[pos - 1])) {
+        L->d2[pos] = L->d2[pos - 1];
+        L->id[pos] = L->id[pos - 1];
+        --pos;
+    }
+    L->d2[pos] = d2;
+    L->id[pos] = id;
+    if (L->count < L->k)
+        L->count++;
+}
+
+/* the shrinking cull radius (squared): the k-th best once the list is full */
+static float orc_list_cull(const orc_list *L)
+{
+    return L->count == L->k ? L->d2[L->k - 1] : L->r2;
+}
+
+static void orc_list_emit(const orc_list *L, int32_t *ids, float *d2)
+{
+    for (int i = 0; i < L->k; ++i) {
+        if (i < L->count) {
+            ids[i] = L->id[i];
+            d2[i] = L->d2[i];
+        } else {
+            ids[i] = -1;
+            d2[i] = INFINITY;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plain definition: k lexicographically smallest (d2, id) with d2 <= r2.   */
+/* ------------------------------------------------------------------------ */
+
+void orc_knn_brute(const float *pts, int64_t N, int D, const float *qs, int64_t Q,
+                   int k, float max_radius, int32_t *ids, float *d2)
+{
+    float r2 = max_radius * max_radius;
+    float *ld = (float *)malloc((size_t)k * sizeof(float));
+    int32_t *li = (int32_t *)malloc((size_t)k * sizeof(int32_t));
+    for (int64_t q = 0; q < Q; ++q) {
+        orc_list L = {k, 0, r2, ld, li};
+        for (int64_t i = 0; i < N; ++i)
+            orc_list_offer(&L, orc_d2(pts + i * D, qs + q * D, D), (int32_t)i);
+        orc_list_emit(&L, ids + q * k, d2 + q * k);
+    }
+    free(ld);
+    free(li);
+}
+
+/* FP64 cross-check: distances of the FP32 inputs computed in double. */
+void orc_knn_brute_f64(const float *pts, int64_t N, int D, const float *qs, int64_t Q,
+                       int k, int32_t *ids, double *d2)
+{
+    for (int64_t q = 0; q < Q; ++q) {
+        int32_t *oi = ids + q * k;
+        double *od = d2 + q * k;
+        int count = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < D; ++j) {
+                double dj = (double)pts[i * D + j] - (double)qs[q * D + j];
+                s += dj * dj;
+            }
+            if (count == k && !(s < od[k - 1] || (s == od[k - 1] && i < oi[k - 1])))
+                continue;
+            int pos = count < k ? count : k - 1;
+            while (pos > 0 && (s < od[pos - 1] || (s == od[pos - 1] && i < oi[pos - 1]))) {
+                od[pos] = od[pos - 1];
+                oi[pos] = oi[pos - 1];
+                --pos;
+            }
+            od[pos] = s;
+            oi[pos] = (int32_t)i;
+            if (count < k)
+                ++count;
+        }
+        for (int i = count; i < k; ++i) {
+            oi[i] = -1;
+            od[i] = INFINITY;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Traversals over a built tree.  The tree is given as node -> input index; */
+/* node coordinates are read from the input points.                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const float *pts;
+    const int32_t *node_pid;
+    int64_t N;
+    int D;
+    const float *q;
+    int ordered;
+    orc_list *L;
+    int32_t *visits;   /* first visits (processNode calls), may be NULL */
+    int64_t nvisits;
+    int64_t vcap;
+    int32_t *steps;    /* every node the traversal is "at", may be NULL */
+    int64_t nsteps;
+    int64_t scap;
+} orc_trav;
+
+static void orc_log(int32_t *buf, int64_t *n, int64_t cap, int64_t node)
+{
+    if (buf && *n < cap)
+        buf[*n] = (int32_t)node;
+    ++*n;
+}
+
+static void orc_process(orc_trav *T, int64_t node)
+{
+    int32_t pid = T->node_pid[node];
+    float d2 = orc_d2(T->pts + (int64_t)pid * T->D, T->q, T->D);
+    orc_list_offer(T->L, d2, pid);
+    orc_log(T->visits, &T->nvisits, T->vcap, node);
+}
+
+/* Sec. 3.1, second formulation: empty subtree -> return; process; close child;
+ * far child if it still overlaps the (possibly shrunk) query range.  The
+ * unordered variant always takes the left child first and enters a child iff
+ * the query lies on its side or the plane is within the cull radius. */
+static void orc_rec(orc_trav *T, int64_t node)
+{
+    orc_log(T->steps, &T->nsteps, T->scap, node);
+    if (node >= T->N)
+        return;
+    orc_process(T, node);
+    int dim = orc_level(node) % T->D;
+    float split = T->pts[(int64_t)T->node_pid[node] * T->D + dim];
+    float sd = T->q[dim] - split;
+    if (T->ordered) {
+        int close_side = sd > 0.0f;
+        int64_t close_child = 2 * node + 1 + close_side;
+        int64_t far_child = 2 * node + 2 - close_side;
+        orc_rec(T, close_child);
+        orc_log(T->steps, &T->nsteps, T->scap, node);
+        if (sd * sd <= orc_list_cull(T->L)) {
+            orc_rec(T, far_child);
+            orc_log(T->steps, &T->nsteps, T->scap, node);
+        }
+    } else {
+        if (sd <= 0.0f || sd * sd <= orc_list_cull(T->L)) {
+            orc_rec(T, 2 * node + 1);
+            orc_log(T->steps, &T->nsteps, T->scap, node);
+        }
+        if (sd > 0.0f || sd * sd <= orc_list_cull(T->L)) {
+            orc_rec(T, 2 * node + 2);
+            orc_log(T->steps, &T->nsteps, T->scap, node);
+        }
+    }
+}
+
+/* Sec. 3.2: only the current and the previous node are kept.  The ordered
+ * branch follows the published step logic; the unordered branch is the same
+ * machine with the child order fixed to (left, right). */
+static int orc_stackfree(orc_trav *T)
+{
+    int64_t curr = 0;
+    int64_t prev = -1;
+    int64_t cap = 3 * (2 * T->N + 1) + 8;
+    for (int64_t step = 0; step < cap; ++step) {
+        orc_log(T->steps, &T->nsteps, T->scap, curr);
+        int64_t parent = (curr + 1) / 2 - 1;
+        if (curr >= T->N) {
+            prev = curr;
+            curr = parent;
+            continue;
+        }
+        int from_parent = prev < curr;
+        if (from_parent)
+            orc_process(T, curr);
+        float cull = orc_list_cull(T->L);
+        int dim = orc_level(curr) % T->D;
+        float split = T->pts[(int64_t)T->node_pid[curr] * T->D + dim];
+        float sd = T->q[dim] - split;
+        int64_t next;
+        if (T->ordered) {
+            int close_side = sd > 0.0f;
+            int64_t close_child = 2 * curr + 1 + close_side;
+            int64_t far_child = 2 * curr + 2 - close_side;
+            int far_in_range = sd * sd <= cull;
+            if (from_parent)
+                next = close_child;
+            else if (prev == close_child)
+                next = far_in_range ? far_child : parent;
+            else
+                next = parent;
+        } else {
+            int64_t lc = 2 * curr + 1;
+            int64_t rc = 2 * curr + 2;
+            int left_in = sd <= 0.0f || sd * sd <= cull;
+            int right_in = sd > 0.0f || sd * sd <= cull;
+            if (from_parent)
+                next = left_in ? lc : (right_in ? rc : parent);
+            else if (prev == lc)
+                next = right_in ? rc : parent;
+            else
+                next = parent;
+        }
+        if (next == -1)
+            return 0;
+        prev = curr;
+        curr = next;
+    }
+    return -1; /* step cap exceeded: cannot happen for a correct machine */
+}
+
+static int orc_knn_tree(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                        const float *q, int k, float max_radius, int ordered,
+                        int stackfree, int32_t *ids, float *d2,
+                        int32_t *visits, int64_t vcap, int64_t *nvisits,
+                        int32_t *steps, int64_t scap, int64_t *nsteps)
+{
+    float *ld = (float *)malloc((size_t)k * sizeof(float));
+    int32_t *li = (int32_t *)malloc((size_t)k * sizeof(int32_t));
+    orc_list L = {k, 0, max_radius * max_radius, ld, li};
+    orc_trav T = {pts, node_pid, N, D, q, ordered, &L, visits, 0, vcap, steps, 0, scap};
+    int rc = 0;
+    if (stackfree)
+        rc = orc_stackfree(&T);
+    else
+        orc_rec(&T, 0);
+    orc_list_emit(&L, ids, d2);
+    if (nvisits)
+        *nvisits = T.nvisits;
+    if (nsteps)
+        *nsteps = T.nsteps;
+    free(ld);
+    free(li);
+    return rc;
+}
+
+/* One query, recursive traversal, with optional visit / step logs. */
+int orc_knn_recursive(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                      const float *q, int k, float max_radius, int ordered,
+                      int32_t *ids, float *d2, int32_t *visits, int64_t vcap,
+                      int64_t *nvisits, int32_t *steps, int64_t scap, int64_t *nsteps)
+{
+    return orc_knn_tree(pts, node_pid, N, D, q, k, max_radius, ordered, 0, ids, d2,
+                        visits, vcap, nvisits, steps, scap, nsteps);
+}
+
+/* One query, stack-free state machine, with optional visit / step logs. */
+int orc_knn_stackfree(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                      const float *q, int k, float max_radius, int ordered,
+                      int32_t *ids, float *d2, int32_t *visits, int64_t vcap,
+                      int64_t *nvisits, int32_t *steps, int64_t scap, int64_t *nsteps)
+{
+    return orc_knn_tree(pts, node_pid, N, D, q, k, max_radius, ordered, 1, ids, d2,
+                        visits, vcap, nvisits, steps, scap, nsteps);
+}
+
+/* Many queries through the stack-free machine; per-query first-visit counts. */
+int orc_knn_stackfree_batch(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                            const float *qs, int64_t Q, int k, float max_radius,
+                            int ordered, int32_t *ids, float *d2, int32_t *nvisit)
+{
+    int rc = 0;
+    for (int64_t i = 0; i < Q; ++i) {
+        int64_t nv = 0;
+        if (orc_knn_tree(pts, node_pid, N, D, qs + i * D, k, max_radius, ordered, 1,
+                         ids + i * k, d2 + i * k, NULL, 0, &nv, NULL, 0, NULL))
+            rc = -1;
+        if (nvisit)
+            nvisit[i] = (int32_t)nv;
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned radius proposal (not in the paper).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Greedy descent from the root, always to the close child (the child on the
+ * query's side, Sec. 3.2 closeSide rule), until that child does not exist.
+ * Returns the FP32 squared distance from q to the last valid node's point. */
+float orc_descent_leaf(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                       const float *q)
+{
+    int64_t node = 0;
+    for (;;) {
+        int dim = orc_level(node) % D;
+        float sd = q[dim] - pts[(int64_t)node_pid[node] * D + dim];
+        int64_t child = 2 * node + 1 + (sd > 0.0f);
+        if (child >= N)
+            break;
+        node = child;
+    }
+    return orc_d2(pts + (int64_t)node_pid[node] * D, q, D);
+}
+
+/* Round a float to the nearest bfloat16 (ties to even), returned as float.
+ * bfloat16 keeps the top 16 bits of binary32; finite inputs only. */
+float orc_round_bf16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u = u + 0x7FFFu + lsb;
+    u &= 0xFFFF0000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
+/* MLP 4 -> H -> H -> 1 with ReLU, parameters laid out as
+ *   W1[H][4], b1[H], W2[H][H], b2[H], w3[H], b3
+ * (row-major, W[out][in]); evaluated in FP64 on the given parameter values
+ * (the caller passes BF16-rounded weights to mirror the device model). */
+void orc_mlp_forward(const double *params, int H, const double *x, int64_t n, double *y)
+{
+    const double *W1 = params;
+    const double *b1 = W1 + (int64_t)H * 4;
+    const double *W2 = b1 + H;
+    const double *b2 = W2 + (int64_t)H * H;
+    const double *w3 = b2 + H;
+    const double *b3 = w3 + H;
+    double *h1 = (double *)malloc((size_t)H * sizeof(double));
+    double *h2 = (double *)malloc((size_t)H * sizeof(double));
+    for (int64_t s = 0; s < n; ++s) {
+        const double *xs = x + s * 4;
+        for (int i = 0; i < H; ++i) {
+            double a = b1[i];
+            for (int j = 0; j < 4; ++j)
+                a += W1[i * 4 + j] * xs[j];
+            h1[i] = a > 0.0 ? a : 0.0;
+        }
+        for (int i = 0; i < H; ++i) {
+            double a = b2[i];
+            for (int j = 0; j < H; ++j)
+                a += W2[(int64_t)i * H + j] * h1[j];
+            h2[i] = a > 0.0 ? a : 0.0;
+        }
+        double o = b3[0];
+        for (int i = 0; i < H; ++i)
+            o += w3[i] * h2[i];
+        y[s] = o;
+    }
+    free(h1);
+    free(h2);
+}
+
+/* Loss = (1/n) * sum_s (y_s - label_s)^2 and its gradient with respect to every
+ * parameter (same layout as params), by the chain rule through the ReLUs.
+ * Returns the loss. */
+double orc_mlp_loss_grad(const double *params, int H, const double *x,
+                         const double *label, int64_t n, double *grad)
+{
+    const double *W1 = params;
+    const double *b1 = W1 + (int64_t)H * 4;
+    const double *W2 = b1 + H;
+    const double *b2 = W2 + (int64_t)H * H;
+    const double *w3 = b2 + H;
+    const double *b3 = w3 + H;
+    int64_t P = (int64_t)H * 4 + H + (int64_t)H * H + H + H + 1;
+    double *gW1 = grad;
+    double *gb1 = gW1 + (int64_t)H * 4;
+    double *gW2 = gb1 + H;
+    double *gb2 = gW2 + (int64_t)H * H;
+    double *gw3 = gb2 + H;
+    double *gb3 = gw3 + H;
+    for (int64_t i = 0; i < P; ++i)
+        grad[i] = 0.0;
+    double *z1 = (double *)malloc((size_t)H * sizeof(double));
+    double *h1 = (double *)malloc((size_t)H * sizeof(double));
+    double *z2 = (double *)malloc((size_t)H * sizeof(double));
+    double *h2 = (double *)malloc((size_t)H * sizeof(double));
+    double *g2 = (double *)malloc((size_t)H * sizeof(double));
+    double *g1 = (double *)malloc((size_t)H * sizeof(double));
+    double loss = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+        const double *xs = x + s * 4;
+        for (int i = 0; i < H; ++i) {
+            double a = b1[i];
+            for (int j = 0; j < 4; ++j)
+                a += W1[i * 4 + j] * xs[j];
+            z1[i] = a;
+            h1[i] = a > 0.0 ? a : 0.0;
+        }
+        for (int i = 0; i < H; ++i) {
+            double a = b2[i];
+            for (int j = 0; j < H; ++j)
+                a += W2[(int64_t)i * H + j] * h1[j];
+            z2[i] = a;
+            h2[i] = a > 0.0 ? a : 0.0;
+        }
+        double o = b3[0];
+        for (int i = 0; i < H; ++i)
+            o += w3[i] * h2[i];
+        double e = o - label[s];
+        loss += e * e;
+        double go = 2.0 * e / (double)n;   /* dLoss / dy_s */
+        gb3[0] += go;
+        for (int i = 0; i < H; ++i) {
+            gw3[i] += go * h2[i];
+            g2[i] = z2[i] > 0.0 ? go * w3[i] : 0.0;   /* dLoss / dz2_i */
+        }
+        for (int i = 0; i < H; ++i) {
+            gb2[i] += g2[i];
+            for (int j = 0; j < H; ++j)
+                gW2[(int64_t)i * H + j] += g2[i] * h1[j];
+        }
+        for (int j = 0; j < H; ++j) {
+            double a = 0.0;
+            for (int i = 0; i < H; ++i)
+                a += W2[(int64_t)i * H + j] * g2[i];
+            g1[j] = z1[j] > 0.0 ? a : 0.0;             /* dLoss / dz1_j */
+        }
+        for (int i = 0; i < H; ++i) {
+            gb1[i] += g1[i];
+            for (int j = 0; j < 4; ++j)
+                gW1[i * 4 + j] += g1[i] * xs[j];
+        }
+    }
+    free(z1);
+    free(h1);
+    free(z2);
+    free(h2);
+    free(g2);
+    free(g1);
+    return loss / (double)n;
+}

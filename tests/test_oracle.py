@@ -1,0 +1,362 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test checks the oracle against something other than itself: the worked
+example of the paper's Figure 1, closed forms, library routines (numpy sorting
+and searching, torch's bfloat16 conversion), independent brute force and the
+invariants the paper states (Sec. 3.1: the state machine visits the same nodes
+in the same order as the recursion).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_12859_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "six_point_2d.json")
+
+
+# ---------------------------------------------------------------- topology
+
+def _subtree_size_by_ancestry(n: int, root: int) -> int:
+    """Count nodes of an n-node level-order tree having `root` as ancestor
+    (or being it), by walking parent links (n-1)//2 ... independently of any
+    size formula."""
+    idx = np.arange(n)
+    hit = idx == root
+    cur = idx.copy()
+    while (cur > 0).any():
+        cur = np.where(cur > 0, (cur - 1) // 2, -1)
+        hit |= cur == root
+    return int(hit.sum())
+
+
+@pytest.mark.parametrize("n", list(range(1, 70)) + [127, 128, 129, 255, 256, 257, 1000, 2047, 2048, 2049])
+def test_left_size_matches_enumeration(n):
+    assert oracle.left_size(n) == _subtree_size_by_ancestry(n, 1) if n > 1 else oracle.left_size(n) == 0
+
+
+def test_parent_child_identities():
+    n = np.arange(0, 1 << 20)
+    parent = lambda c: (c + 1) // 2 - 1  # noqa: E731  (Sec. 3.2 parent rule)
+    assert np.array_equal(parent(2 * n + 1), n)
+    assert np.array_equal(parent(2 * n + 2), n)
+    assert parent(np.array([0]))[0] == -1
+
+
+# ---------------------------------------------------------------- builder
+
+def test_six_point_tree():
+    g = json.load(open(GOLDEN))
+    pts = np.array(g["points"], dtype=np.float32)
+    assert oracle.build(pts).tolist() == g["tree_ids"]
+
+
+def _check_tree_property(pts: np.ndarray, node_pid: np.ndarray):
+    """The level-order array is the unique complete tree whose every node
+    separates its subtrees in its level's dimension (mod D) under the
+    (coordinate, input index) order.  Checked bottom-up with subtree min/max
+    keys, independently of how the tree was built."""
+    N, D = pts.shape
+    assert sorted(node_pid.tolist()) == list(range(N))
+    # per node and dim: key = (coord, id); track subtree min and max keys
+    coords = pts[node_pid].astype(np.float64)
+    ids = node_pid.astype(np.int64)
+    kmin_c = coords.copy()
+    kmin_i = np.repeat(ids[:, None], D, axis=1)
+    kmax_c = coords.copy()
+    kmax_i = kmin_i.copy()
+
+    def less(ac, ai, bc, bi):
+        return (ac < bc) | ((ac == bc) & (ai < bi))
+
+    for t in range(N - 1, -1, -1):
+        for c in (2 * t + 1, 2 * t + 2):
+            if c < N:
+                m = less(kmin_c[c], kmin_i[c], kmin_c[t], kmin_i[t])
+                kmin_c[t] = np.where(m, kmin_c[c], kmin_c[t])
+                kmin_i[t] = np.where(m, kmin_i[c], kmin_i[t])
+                m = less(kmax_c[t], kmax_i[t], kmax_c[c], kmax_i[c])
+                kmax_c[t] = np.where(m, kmax_c[c], kmax_c[t])
+                kmax_i[t] = np.where(m, kmax_i[c], kmax_i[t])
+    for t in range(N):
+        d = int(math.floor(math.log2(t + 1))) % D
+        l, r = 2 * t + 1, 2 * t + 2
+        if l < N:
+            assert less(kmax_c[l, d], kmax_i[l, d], coords[t, d], ids[t]), t
+        if r < N:
+            assert less(coords[t, d], ids[t], kmin_c[r, d], kmin_i[r, d]), t
+
+
+@pytest.mark.parametrize("N,D,seed", [(1, 3, 0), (2, 3, 1), (3, 2, 2), (7, 3, 3), (100, 3, 4),
+                                      (257, 2, 5), (500, 4, 6), (333, 8, 7), (64, 1, 8), (1000, 3, 9)])
+def test_build_separation_property(N, D, seed):
+    g = np.random.default_rng(seed)
+    pts = g.integers(0, 6, size=(N, D)).astype(np.float32)  # many ties
+    if seed % 2:
+        pts = g.random((N, D)).astype(np.float32)
+    _check_tree_property(pts, oracle.build(pts))
+
+
+def test_build_signed_zero_and_ties():
+    pts = np.array([[0.0], [-0.0], [0.0], [-0.0], [1.0]], dtype=np.float32)
+    node_pid = oracle.build(pts)
+    _check_tree_property(pts, node_pid)
+    # -0 == +0 under float <, so ties resolve by index: sorted order 0,1,2,3,4
+    # L(5) = 3 -> root holds index 3
+    assert node_pid[0] == 3
+
+
+def test_build_rejects_nonfinite():
+    pts = np.zeros((4, 3), dtype=np.float32)
+    pts[2, 1] = np.nan
+    with pytest.raises(ValueError):
+        oracle.build(pts)
+
+
+# ---------------------------------------------------------------- definition
+
+def _numpy_knn(pts, qs, k, max_radius):
+    """Independent statement of the result: d2 per term in float32 summed in
+    coordinate order, filter d2 <= r2, lexsort by (d2, id), first k."""
+    r2 = np.float32(max_radius) * np.float32(max_radius)
+    Q = qs.shape[0]
+    ids = np.full((Q, k), -1, dtype=np.int32)
+    d2 = np.full((Q, k), np.inf, dtype=np.float32)
+    for i in range(Q):
+        diff = (pts - qs[i]).astype(np.float32)
+        t = (diff * diff).astype(np.float32)
+        s = t[:, 0].copy()
+        for j in range(1, pts.shape[1]):
+            s = (s + t[:, j]).astype(np.float32)
+        cand = np.nonzero(s <= r2)[0]
+        order = cand[np.lexsort((cand, s[cand]))][:k]
+        ids[i, : len(order)] = order
+        d2[i, : len(order)] = s[order]
+    return ids, d2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_matches_numpy_definition(seed):
+    g = np.random.default_rng(100 + seed)
+    N, D = int(g.integers(1, 80)), int(g.integers(1, 9))
+    pts = g.integers(0, 4, size=(N, D)).astype(np.float32) * np.float32(0.25)
+    if seed % 2:
+        pts = g.random((N, D)).astype(np.float32)
+    qs = g.random((40, D)).astype(np.float32)
+    for k in (1, 3, 8, N + 2):
+        for r in (math.inf, 0.3, 0.0):
+            a = oracle.knn_brute(pts, qs, k, r)
+            b = _numpy_knn(pts, qs, k, r)
+            assert np.array_equal(a[0], b[0])
+            assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
+
+def test_zero_radius_returns_exact_duplicates_only():
+    g = np.random.default_rng(7)
+    pts = g.integers(0, 3, size=(60, 2)).astype(np.float32)
+    qs = pts[:10].copy()
+    ids, d2 = oracle.knn_brute(pts, qs, 60, 0.0)
+    for i in range(10):
+        want = np.nonzero((pts == qs[i]).all(axis=1))[0]
+        got = ids[i][ids[i] >= 0]
+        assert got.tolist() == want.tolist()
+        assert (d2[i][: len(want)] == 0).all()
+
+
+def test_k_at_least_n_returns_all_sorted():
+    g = np.random.default_rng(8)
+    pts = g.random((17, 3)).astype(np.float32)
+    q = g.random((1, 3)).astype(np.float32)
+    ids, d2 = oracle.knn_brute(pts, q, 20, math.inf)
+    assert sorted(ids[0, :17].tolist()) == list(range(17))
+    assert ids[0, 17:].tolist() == [-1, -1, -1] and np.isinf(d2[0, 17:]).all()
+    assert (np.diff(d2[0, :17]) >= 0).all()
+
+
+def test_one_dimension_is_sorted_array_search():
+    """D = 1: the nearest point is a neighbour of the insertion position in
+    the sorted coordinates (textbook)."""
+    g = np.random.default_rng(9)
+    x = np.unique(g.random(500).astype(np.float32))
+    pts = g.permutation(x)[:, None]
+    qs = g.random((300, 1)).astype(np.float32)
+    ids, d2 = oracle.knn_brute(pts, qs, 1)
+    xs = np.sort(x)
+    for i, q in enumerate(qs[:, 0]):
+        j = np.searchsorted(xs, q)
+        cands = [c for c in (j - 1, j) if 0 <= c < len(xs)]
+        best = min(cands, key=lambda c: (np.float32(xs[c] - q) ** 2, c))
+        assert pts[ids[i, 0], 0] == xs[best]
+
+
+def test_fp32_matches_fp64_up_to_rounding():
+    g = np.random.default_rng(10)
+    pts = g.random((3000, 3)).astype(np.float32)
+    qs = g.random((200, 3)).astype(np.float32)
+    k = 8
+    i32, d32 = oracle.knn_brute(pts, qs, k)
+    i64, d64 = oracle.knn_brute_f64(pts, qs, k)
+    # each FP32 distance is within a few ulps of the exact one
+    exact = np.array([[np.sum((pts[j].astype(np.float64) - qs[q].astype(np.float64)) ** 2) for j in i32[q]]
+                      for q in range(len(qs))])
+    assert np.allclose(d32, exact, rtol=4 * 2.0 ** -23, atol=0)
+    # the k-th FP32 distance equals the exact k-th up to rounding; ids agree
+    # except where two exact distances fall within rounding of each other
+    assert np.allclose(d32[:, -1], d64[:, -1], rtol=8 * 2.0 ** -23)
+    agree = (i32 == i64).mean()
+    assert agree > 0.99
+
+
+# ---------------------------------------------------------------- traversal
+
+def test_six_point_traces():
+    g = json.load(open(GOLDEN))
+    pts = np.array(g["points"], dtype=np.float32)
+    node_pid = np.array(g["tree_ids"], dtype=np.int32)
+    for tr in g["traces"]:
+        for fn in (oracle.knn_recursive, oracle.knn_stackfree):
+            ids, d2, visits, _ = fn(pts, node_pid, tr["query"], tr["k"], math.inf, tr["ordered"])
+            assert ids.tolist() == tr["ids"], (fn, tr)
+            assert d2.tolist() == tr["d2"], (fn, tr)
+            assert visits.tolist() == tr["visits"], (fn, tr)
+
+
+def _cases():
+    for seed in range(12):
+        g = np.random.default_rng(200 + seed)
+        N = int(g.integers(1, 70))
+        D = int(g.integers(1, 5))
+        if seed % 3 == 0:
+            pts = g.integers(0, 3, size=(N, D)).astype(np.float32)  # duplicates
+        elif seed % 3 == 1:
+            pts = np.repeat(g.random((N, 1)), D, axis=1).astype(np.float32)  # collinear
+        else:
+            pts = g.random((N, D)).astype(np.float32)
+        qs = (g.random((25, D)) * 1.4 - 0.2).astype(np.float32)
+        yield seed, pts, qs
+
+
+@pytest.mark.parametrize("seed,pts,qs", list(_cases()))
+def test_traversals_match_brute_and_each_other(seed, pts, qs):
+    node_pid = oracle.build(pts)
+    N = len(pts)
+    for k in (1, 2, 5, N + 1):
+        for r in (math.inf, 0.35, 0.0):
+            want_i, want_d = oracle.knn_brute(pts, qs, k, r)
+            for q in range(len(qs)):
+                runs = {}
+                for ordered in (True, False):
+                    for name, fn in (("rec", oracle.knn_recursive), ("sm", oracle.knn_stackfree)):
+                        ids, d2, visits, steps = fn(pts, node_pid, qs[q], k, r, ordered)
+                        assert ids.tolist() == want_i[q].tolist()
+                        assert np.array_equal(d2.view(np.uint32), want_d[q].view(np.uint32))
+                        runs[(ordered, name)] = (visits, steps)
+                    # Sec. 3.1: same nodes, same order, as the recursion
+                    assert np.array_equal(runs[(ordered, "rec")][0], runs[(ordered, "sm")][0])
+                    assert np.array_equal(runs[(ordered, "rec")][1], runs[(ordered, "sm")][1])
+
+
+def _preorder(N):
+    out, stack = [], [0]
+    while stack:
+        n = stack.pop()
+        if n < N:
+            out.append(n)
+            stack.extend([2 * n + 2, 2 * n + 1])
+    return out
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 6, 31, 32, 33, 100])
+def test_unordered_unbounded_visits_every_node_once_in_preorder(N):
+    g = np.random.default_rng(N)
+    pts = g.random((N, 3)).astype(np.float32)
+    node_pid = oracle.build(pts)
+    q = g.random(3).astype(np.float32)
+    _, _, visits, steps = oracle.knn_stackfree(pts, node_pid, q, N, math.inf, ordered=False)
+    assert visits.tolist() == _preorder(N)
+    # each valid node is stepped on at most three times, each missing child once
+    counts = np.bincount(steps[steps < N], minlength=N)
+    assert counts.max() <= 3
+
+
+def test_ordered_visit_counts_uniform_3d():
+    """Batch entry agrees with per-query entry; visit counts are positive and
+    the ordered traversal processes far fewer nodes than there are points."""
+    pts, qs = synth.uniform_small(4096, 256)
+    node_pid = oracle.build(pts)
+    ids, d2, nv = oracle.knn_tree(pts, node_pid, qs, 8)
+    bi, bd = oracle.knn_brute(pts, qs, 8)
+    assert np.array_equal(ids, bi) and np.array_equal(d2, bd)
+    for q in (0, 17, 255):
+        _, _, visits, _ = oracle.knn_stackfree(pts, node_pid, qs[q], 8)
+        assert len(visits) == nv[q]
+    assert 8 <= nv.min() and nv.mean() < 0.1 * len(pts)
+
+
+def test_descent_leaf_is_first_leaf_of_ordered_traversal():
+    """The greedy close-child descent ends where the ordered traversal first
+    turns back: the last node stepped on before the first missing child."""
+    pts, qs = synth.uniform_small(1000, 50)
+    node_pid = oracle.build(pts)
+    N = len(pts)
+    leaf_d2 = oracle.descent_leaf_d2(pts, node_pid, qs)
+    for i in range(len(qs)):
+        _, _, _, steps = oracle.knn_stackfree(pts, node_pid, qs[i], 1)
+        first_missing = int(np.argmax(steps >= N))
+        leaf = steps[first_missing - 1]
+        diff = (pts[node_pid[leaf]] - qs[i]).astype(np.float32)
+        t = (diff * diff).astype(np.float32)
+        assert leaf_d2[i] == np.float32(np.float32(t[0] + t[1]) + t[2])
+
+
+# ---------------------------------------------------------------- MLP
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(11)
+    xs = np.concatenate([g.standard_normal(2000) * 10.0 ** g.integers(-8, 8, 2000),
+                         [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38]]).astype(np.float32)
+    want = torch.from_numpy(xs).to(torch.bfloat16).to(torch.float32).numpy()
+    got = np.array([oracle.round_bf16(float(x)) for x in xs], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def _numpy_mlp(params, H, x):
+    W1 = params[: 4 * H].reshape(H, 4)
+    b1 = params[4 * H: 5 * H]
+    W2 = params[5 * H: 5 * H + H * H].reshape(H, H)
+    b2 = params[5 * H + H * H: 6 * H + H * H]
+    w3 = params[6 * H + H * H: 7 * H + H * H]
+    b3 = params[7 * H + H * H]
+    h1 = np.maximum(x @ W1.T + b1, 0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0)
+    return h2 @ w3 + b3
+
+
+def test_mlp_forward_matches_matrix_form():
+    H = 16
+    g = np.random.default_rng(12)
+    p = g.standard_normal(oracle.mlp_param_count(H)) * 0.5
+    x = g.standard_normal((64, 4))
+    assert np.allclose(oracle.mlp_forward(p, H, x), _numpy_mlp(p, H, x), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    H = 8
+    g = np.random.default_rng(13)
+    p = g.standard_normal(oracle.mlp_param_count(H)) * 0.5
+    x = g.standard_normal((32, 4))
+    lab = g.standard_normal(32)
+    loss, grad = oracle.mlp_loss_grad(p, H, x, lab)
+    assert math.isclose(loss, float(np.mean((_numpy_mlp(p, H, x) - lab) ** 2)), rel_tol=1e-12)
+    eps = 1e-6
+    for i in range(len(p)):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += eps
+        pm[i] -= eps
+        fd = (np.mean((_numpy_mlp(pp, H, x) - lab) ** 2) - np.mean((_numpy_mlp(pm, H, x) - lab) ** 2)) / (2 * eps)
+        assert abs(fd - grad[i]) <= 1e-5 * max(1.0, abs(fd)), i
