@@ -1,0 +1,227 @@
+/*
+ * kdt.h - C ABI of the GB300 k-d tree query library.
+ *
+ * Find-closest-point (fcp) and k-nearest-neighbour (kNN) queries over a
+ * left-balanced, complete k-d tree stored in level order, traversed with the
+ * stack-free (curr, prev) state machine of Wald, "A Stack-Free Traversal
+ * Algorithm for Left-Balanced k-d Trees" (arXiv 2210.12859), Sec. 3.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers prefixed d_ are DEVICE pointers on the current CUDA device,
+ *     owned by the caller; pointers prefixed h_ are HOST pointers owned by the
+ *     caller.  Point and query arrays are dense row-major float32 [count][D].
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue their work on it and return without waiting,
+ *     unless the entry point says it synchronises.
+ *   - Every call returns KDT_OK (0) or a negative KDT_E* status; the text of
+ *     the last failure on the calling host thread is kdt_last_error().
+ *   - IDs are indices of the input points (within their own cloud for the
+ *     batched calls), not node indices.  Result rows are sorted ascending by
+ *     (squared distance, id); empty slots hold id -1 and distance +inf.
+ *   - Squared distances are FP32: d2 = ((t_0 + t_1) + t_2) + ..., with
+ *     t_j = (p_j - q_j)^2 each rounded to float, no fused multiply-add.  A
+ *     point is a candidate iff d2 <= max_radius * max_radius (rounded to
+ *     float); ties in d2 go to the smaller id.  The result is the exact
+ *     k-best set under that order whatever flags are used.
+ *   - Objects (kdt_tree, kdt_forest) are not thread-safe: serialise calls
+ *     that use one object on one stream.
+ */
+#ifndef KDT_H
+#define KDT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define KDT_OK          0
+#define KDT_EINVAL     -1  /* bad argument: N < 1, D outside [1,8], k outside [1,64], Q < 0,
+                              max_radius < 0 or NaN, N >= 2^30, NULL pointer, ... */
+#define KDT_ENONFINITE -2  /* a point coordinate is NaN or infinite */
+#define KDT_ENOMEM     -3  /* device or host allocation failed */
+#define KDT_ECUDA      -4  /* a CUDA runtime call failed */
+#define KDT_ETRAVERSAL -5  /* a traversal exceeded its step bound (never for a valid tree) */
+#define KDT_ENOMODEL   -6  /* KDT_LEARNED requested but the tree has no trained radius model */
+#define KDT_EIO        -7  /* model file could not be read or written, or has a bad header */
+
+/* ---- query flags ------------------------------------------------------- */
+#define KDT_ORDERED    0x0 /* close child first (Sec. 3, ordered traversal), the default */
+#define KDT_UNORDERED  0x1 /* left child first; a child is entered iff the query is on its
+                              side or the splitting plane is within the cull radius
+                              (Sec. 3: unordered traversal as a simplification) */
+#define KDT_MORTON     0x2 /* sort queries along a 30-bit Morton curve before traversal so
+                              that the threads of a warp walk nearby paths; results are
+                              written to the caller's query order */
+#define KDT_LEARNED    0x4 /* seed each query's cull radius with the trained radius model
+                              and re-run the queries that find fewer than k points with
+                              the caller's radius (not in the paper; results unchanged) */
+#define KDT_NO_STAGE   0x8 /* do not stage the top tree levels in shared memory */
+
+/* ---- build options ----------------------------------------------------- */
+#define KDT_BUILD_ASYNC 0x1 /* kdt_build_ex: do not synchronise to check the points for
+                               NaN / inf; the check result is reported by kdt_status */
+
+typedef struct kdt_tree kdt_tree;
+typedef struct kdt_forest kdt_forest;
+
+/* Text of the last failure on the calling thread ("" if none). */
+const char *kdt_last_error(void);
+
+/* ---- single tree ------------------------------------------------------- */
+
+/* Build the left-balanced complete tree of N points of dimension D in level
+ * order (Sec. 3: node n has children 2n+1 and 2n+2).  Split dimension of a
+ * node on level l is l mod D; the point stored at a node is the element of
+ * rank L(n) (the complete tree's left-subtree size) of its subtree's points in
+ * (coordinate, input index) order, so the tree is the one any serial median
+ * builder produces (Sec. 4).
+ *   d_points: float32 [N][D], read only during the call's stream work.
+ *   N in [1, 2^30), D in [1, 8].
+ *   *out receives a library-owned tree; release it with kdt_free.
+ * Synchronises `stream` once to report KDT_ENONFINITE. */
+int kdt_build(const float *d_points, int64_t N, int D, void *stream, kdt_tree **out);
+
+/* As kdt_build; opts = 0 or KDT_BUILD_ASYNC (no synchronisation). */
+int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream, kdt_tree **out);
+
+/* Rebuild `tree` in place from new points with the same N and D, reusing its
+ * device memory (a trained radius model is kept).  opts as for kdt_build_ex. */
+int kdt_rebuild(kdt_tree *tree, const float *d_points, int opts, void *stream);
+
+/* N and D of a tree (host values, no synchronisation). */
+int kdt_tree_info(const kdt_tree *tree, int64_t *N, int *D);
+
+/* Copy the level-order tree: d_coords float32 [N][D] (coordinates of the
+ * point at each node) and d_ids int32 [N] (its input index). */
+int kdt_tree_export(const kdt_tree *tree, float *d_coords, int32_t *d_ids, void *stream);
+
+/* Find-closest-point (Sec. 4, fcp): kNN with k = 1.
+ *   d_queries float32 [Q][D]; d_ids int32 [Q]; d_d2 float32 [Q]. */
+int kdt_fcp(const kdt_tree *tree, const float *d_queries, int64_t Q, float max_radius,
+            int flags, int32_t *d_ids, float *d_d2, void *stream);
+
+/* k nearest neighbours within max_radius (inclusive; +inf = unbounded) with a
+ * shrinking cull radius (Sec. 3).  k in [1, 64].
+ *   d_queries float32 [Q][D]; d_ids int32 [Q][k]; d_d2 float32 [Q][k].
+ * Q = 0 is a no-op. */
+int kdt_knn(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, float max_radius,
+            int flags, int32_t *d_ids, float *d_d2, void *stream);
+
+/* Per-query count of processed nodes (first visits, the processNode calls of
+ * Sec. 3.2) of the traversal kdt_knn would run with the same arguments.
+ * KDT_LEARNED is not accepted here.  d_visits int32 [Q]. */
+int kdt_knn_visits(const kdt_tree *tree, const float *d_queries, int64_t Q, int k,
+                   float max_radius, int flags, int32_t *d_visits, void *stream);
+
+/* Synchronise `stream` and report device-side failures recorded on the tree
+ * since the last call: KDT_ENONFINITE (asynchronous build) or KDT_ETRAVERSAL.
+ * Clears the recorded state. */
+int kdt_status(kdt_tree *tree, void *stream);
+
+/* Release a tree and its device memory (synchronises the device first). */
+void kdt_free(kdt_tree *tree);
+
+/* One call from host memory to host memory: copies h_points and h_queries to
+ * the device, builds the tree, runs kdt_knn, copies the results back into
+ * h_ids int32 [Q][k] and h_d2 float32 [Q][k], and frees everything.
+ * Synchronous.  Page-locked host buffers copy fastest. */
+int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_queries, int64_t Q,
+                 int k, float max_radius, int flags, int32_t *h_ids, float *h_d2);
+
+/* ---- learned radius proposal (not in the paper) ------------------------- */
+
+typedef struct kdt_train_opts {
+    int epochs;           /* passes over the training queries (default 6 if <= 0) */
+    int batch;            /* minibatch size (default 4096 if <= 0) */
+    float lr;             /* Adam step size (default 2e-3 if <= 0) */
+    uint64_t seed;        /* weight initialisation seed */
+    float margin;         /* cull radius = margin * predicted radius (default 1.25 if <= 0) */
+} kdt_train_opts;
+
+/* Width of the two hidden layers of the radius model. */
+#define KDT_MLP_HIDDEN 64
+/* Number of float parameters: W1[64][4] b1[64] W2[64][64] b2[64] w3[64] b3. */
+#define KDT_MLP_PARAMS (64 * 4 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* Train the radius model of `tree` on Qt training queries for k neighbours:
+ * labels are 0.5*log(d2 of the exact k-th neighbour) from kdt_knn; features
+ * are the query coordinates and log(max(d2 to the greedy-descent leaf, 1e-30))
+ * (the leaf is where repeated close-child steps from the root end), normalised
+ * by their training mean and standard deviation; the MLP 4 -> 64 -> 64 -> 1
+ * (ReLU) runs with BF16-rounded weights and FP32 accumulation and is fitted by
+ * Adam on the mean squared error, entirely by the library's kernels.
+ * Synchronous.  *final_loss (may be NULL) receives the last epoch's mean loss. */
+int kdt_radius_model_train(kdt_tree *tree, const float *d_train_queries, int64_t Qt, int k,
+                           const kdt_train_opts *opts, float *final_loss, void *stream);
+
+/* Copy the model out of / into the tree (host buffers).
+ *   h_params float32 [KDT_MLP_PARAMS] (FP32 master weights), h_norm float32 [8]
+ *   (feature mean[4], std[4]), *margin. */
+int kdt_radius_model_get(const kdt_tree *tree, float *h_params, float *h_norm, float *margin);
+int kdt_radius_model_set(kdt_tree *tree, const float *h_params, const float *h_norm, float margin);
+
+/* Save / load the model as a small versioned binary file. */
+int kdt_radius_model_save(const kdt_tree *tree, const char *path);
+int kdt_radius_model_load(kdt_tree *tree, const char *path);
+
+/* Per-query features: d_feat float32 [Q][4] = (q_0, q_1, q_2, log(max(d2_leaf, 1e-30)))
+ * before normalisation (3-D trees only). */
+int kdt_descent_features(const kdt_tree *tree, const float *d_queries, int64_t Q,
+                         float *d_feat, void *stream);
+
+/* Model forward on normalised features: d_x float32 [n][4] -> d_y float32 [n],
+ * using h_params as given (FP32, rounded to BF16 by the kernel). */
+int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d_y, void *stream);
+
+/* Mean squared error of the model on (d_x, d_label) and its gradient with
+ * respect to the BF16-rounded parameters: h_grad float32 [KDT_MLP_PARAMS].
+ * Synchronous. */
+int kdt_mlp_loss_grad(const float *h_params, const float *d_x, const float *d_label, int64_t n,
+                      float *h_loss, float *h_grad, void *stream);
+
+/* Learned-path statistics of the last KDT_LEARNED query on this tree:
+ * number of queries re-run with the caller's radius, and the mean of
+ * (proposed radius / true k-th neighbour radius) over queries that did not
+ * fall back.  Synchronises `stream`. */
+int kdt_learned_stats(const kdt_tree *tree, int64_t *fallbacks, double *radius_ratio, void *stream);
+
+/* ---- batched: many independent trees ------------------------------------ */
+
+/* Build T trees at once.  Cloud i is d_points rows [h_offsets[i], h_offsets[i+1])
+ * (h_offsets int64 [T+1], h_offsets[0] = 0, non-decreasing; empty clouds are
+ * allowed).  Each tree is exactly the tree kdt_build makes of its cloud. */
+int kdt_build_batched(const float *d_points, const int64_t *h_offsets, int T, int D,
+                      void *stream, kdt_forest **out);
+
+/* kNN of each query set against its own tree: queries of tree i are rows
+ * [h_qoffsets[i], h_qoffsets[i+1]) of d_queries; result rows follow the query
+ * rows; ids are indices within cloud i.  One persistent launch serves all
+ * trees (captured once into a CUDA graph and replayed while the arguments are
+ * unchanged).  With KDT_PER_TREE the same kernel is launched once per tree
+ * instead (for comparison). */
+#define KDT_PER_TREE 0x10
+int kdt_knn_batched(kdt_forest *forest, const float *d_queries, const int64_t *h_qoffsets,
+                    int k, float max_radius, int flags, int32_t *d_ids, float *d_d2, void *stream);
+
+/* Level-order arrays of all trees, concatenated in cloud order:
+ * d_coords float32 [sum N_i][D], d_ids int32 [sum N_i] (ids within the cloud). */
+int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids, void *stream);
+
+void kdt_forest_free(kdt_forest *forest);
+
+/* ---- profiling ----------------------------------------------------------- */
+
+/* Accumulate device time of the traversal kernels launched by kdt_knn /
+ * kdt_fcp on `tree` (CUDA events recorded on the launching stream around each
+ * traversal launch) while enabled. */
+int kdt_profile_enable(kdt_tree *tree, int enable);
+/* Synchronise, then return the accumulated milliseconds and launch count of the
+ * traversal kernels since profiling was enabled, and reset them. */
+int kdt_profile_read(kdt_tree *tree, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDT_H */

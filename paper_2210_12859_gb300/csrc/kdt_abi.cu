@@ -1,0 +1,835 @@
+// C ABI of the library (declared in include/kdt.h): argument checking, object
+// lifetimes, scratch memory, the query reordering and kernel dispatch.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "kdt_learned.cuh"
+#include "kdt_query.cuh"
+
+namespace kdt {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    int code = e == cudaErrorMemoryAllocation ? KDT_ENOMEM : KDT_ECUDA;
+    const char *f = strrchr(file, '/');
+    return set_error(code, "%s:%d: %s failed: %s", f ? f + 1 : file, line, what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- helpers
+
+int grid_for_kernel(const void *fn, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, std::unordered_map<size_t, int>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto &m = cache[fn];
+    auto it = m.find(smem);
+    if (it != m.end())
+        return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int g = per_sm * num_sms();
+    m[smem] = g;
+    return g;
+}
+
+static void pool_setup_once()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev])
+        return;
+    done[dev] = true;
+    // keep freed scratch in the stream-ordered pool of this process instead of
+    // returning it to the driver after every call
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+
+// stream-ordered scratch released at scope exit
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    explicit Scratch(cudaStream_t s_) : s(s_) {}
+    int alloc(size_t bytes)
+    {
+        KDT_CUDA(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s));
+        return KDT_OK;
+    }
+    ~Scratch()
+    {
+        if (p)
+            cudaFreeAsync(p, s);
+    }
+};
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    template <class T> T *take(size_t n)
+    {
+        T *r = (T *)(base + off);
+        off += (n * sizeof(T) + 255) & ~(size_t)255;
+        return r;
+    }
+};
+
+static size_t carve_size(std::initializer_list<size_t> bytes)
+{
+    size_t s = 0;
+    for (size_t b : bytes)
+        s += (b + 255) & ~(size_t)255;
+    return s;
+}
+
+static bool bad_radius(float r) { return !(r >= 0.f); }
+
+// ---------------------------------------------------------------- Morton order
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// 30-bit Morton code of the first min(D,3) coordinates quantised to 10 bits
+// inside the bounding box of the query's tree
+__global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, const float *__restrict__ bbox, int T,
+                              const int64_t *__restrict__ q_off, uint32_t *__restrict__ keys,
+                              uint32_t *__restrict__ vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
+        int t = 0;
+        if (T > 1) {
+            int lo = 0, hi = T - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (q_off[mid] <= i)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            t = lo;
+        }
+        const float *bb = bbox + 6 * t;
+        uint32_t code = 0;
+        for (int j = 0; j < 3 && j < D; ++j) {
+            float ext = bb[3 + j] - bb[j];
+            float x = ext > 0.f ? (qs[i * D + j] - bb[j]) / ext : 0.f;
+            x = fminf(fmaxf(x, 0.f), 1.f);
+            uint32_t c = (uint32_t)fminf(x * 1024.f, 1023.f);
+            code |= spread3(c) << (2 - j);
+        }
+        keys[i] = code;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void tree_of_query_kernel(const uint32_t *__restrict__ vals, int64_t Q, const int64_t *__restrict__ q_off,
+                                     int T, uint32_t *__restrict__ keys)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t qi = vals[i];
+        int lo = 0, hi = T - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (q_off[mid] <= qi)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        keys[i] = (uint32_t)lo;
+    }
+}
+
+static unsigned grid_1d(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
+}
+
+size_t morton_scratch_bytes(int64_t Q)
+{
+    return carve_size({(size_t)Q * 4, (size_t)Q * 4, (size_t)Q * 4, (size_t)Q * 4, radix_scratch_elems(Q) * 4});
+}
+
+// permutation of the queries along the Morton curve (stable: equal codes keep
+// their index order); perm receives traversal order -> query index
+int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
+                 void *scratch, uint32_t **perm_out, cudaStream_t s)
+{
+    Carve c{(char *)scratch};
+    uint32_t *keys = c.take<uint32_t>(Q);
+    uint32_t *perm = c.take<uint32_t>(Q);
+    uint32_t *tk = c.take<uint32_t>(Q);
+    uint32_t *tv = c.take<uint32_t>(Q);
+    uint32_t *rs = c.take<uint32_t>(radix_scratch_elems(Q));
+    morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, keys, perm);
+    KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, 30, rs, s));
+    if (T > 1) {
+        tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
+        KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, tbits, rs, s));
+    }
+    KDT_CUDA(cudaGetLastError());
+    *perm_out = perm;
+    return KDT_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+
+struct Prof {
+    std::vector<cudaEvent_t> ev;   // pairs
+    size_t used = 0;
+};
+
+static int prof_begin(kdt_tree *t, cudaStream_t s, cudaEvent_t *stop)
+{
+    *stop = nullptr;
+    if (!t->profiling)
+        return KDT_OK;
+    Prof *p = (Prof *)t->prof;
+    if (p->used + 2 > p->ev.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            KDT_CUDA(cudaEventCreate(&e));
+            p->ev.push_back(e);
+        }
+    }
+    KDT_CUDA(cudaEventRecord(p->ev[p->used], s));
+    *stop = p->ev[p->used + 1];
+    p->used += 2;
+    return KDT_OK;
+}
+
+// ---------------------------------------------------------------- queries
+
+int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int mode,
+              int32_t *d_ids, float *d_d2, int32_t *d_visits, cudaStream_t s)
+{
+    pool_setup_once();
+    const bool morton = flags & KDT_MORTON;
+    size_t bytes = carve_size({64}) + (morton ? morton_scratch_bytes(Q) : 0);
+    Scratch sc(s);
+    KDT_TRY(sc.alloc(bytes));
+    Carve c{(char *)sc.p};
+    unsigned long long *counter = c.take<unsigned long long>(8);
+    QueryArgs a;
+    if (morton)
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, c.base + c.off, const_cast<uint32_t **>(&a.perm),
+                             s));
+    a.nodes = t->nodes;
+    a.ids = t->ids;
+    a.N = (int)t->N;
+    a.D = t->D;
+    a.queries = d_q;
+    a.Q = Q;
+    a.k = k;
+    a.r2 = r2;
+    a.out_ids = d_ids;
+    a.out_d2 = d_d2;
+    a.visits = d_visits;
+    a.err = t->err;
+    a.counter = counter;
+    int budget = k <= MAX_REG_K ? 32 * 1024 : 16 * 1024;
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, t->layout, budget);
+    cudaEvent_t stop;
+    KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
+    KDT_TRY(launch_query(t->layout, a, !(flags & KDT_UNORDERED), mode, false, s));
+    if (stop)
+        KDT_CUDA(cudaEventRecord(stop, s));
+    return KDT_OK;
+}
+
+static int check_query_args(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, const void *o1,
+                            const void *o2)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (Q < 0)
+        return set_error(KDT_EINVAL, "Q must be >= 0 (got %lld)", (long long)Q);
+    if (k < 1 || k > 64)
+        return set_error(KDT_EINVAL, "k must be in [1, 64] (got %d)", k);
+    if (bad_radius(max_radius))
+        return set_error(KDT_EINVAL, "max_radius must be >= 0 (got %g)", (double)max_radius);
+    if (Q > 0 && (!d_q || !o1 || (o2 == (const void *)1 ? false : !o2)))
+        return set_error(KDT_EINVAL, "NULL query or output pointer");
+    if (Q >= ((int64_t)1 << 32))
+        return set_error(KDT_EINVAL, "Q must be < 2^32");
+    return KDT_OK;
+}
+
+// ---------------------------------------------------------------- export
+
+__global__ void export_kernel(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids, int64_t n, int D,
+                              float *__restrict__ coords, int32_t *__restrict__ out_ids)
+{
+    const int NF = D <= 4 ? 1 : 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        float v[8];
+        float4 a = nodes[t * NF];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        if (NF == 2) {
+            float4 b = nodes[t * NF + 1];
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        }
+        if (coords)
+            for (int j = 0; j < D; ++j)
+                coords[t * D + j] = v[j];
+        if (out_ids)
+            out_ids[t] = D <= 3 ? __float_as_int(a.w) : ids[t];
+    }
+}
+
+}  // namespace kdt
+
+using namespace kdt;
+
+// ======================================================================== ABI
+
+extern "C" {
+
+const char *kdt_last_error(void) { return g_err; }
+
+static int alloc_tree(int64_t N, int D, kdt_tree **out)
+{
+    kdt_tree *t = new (std::nothrow) kdt_tree();
+    if (!t)
+        return set_error(KDT_ENOMEM, "host allocation failed");
+    t->N = N;
+    t->D = D;
+    t->layout = layout_of(D);
+    cudaGetDevice(&t->device);
+    t->prof = new Prof();
+    cudaError_t e = cudaMalloc(&t->nodes, (size_t)N * float4_per_node(D) * sizeof(float4));
+    if (e == cudaSuccess && t->layout > 0)
+        e = cudaMalloc(&t->ids, (size_t)N * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&t->bbox, 6 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&t->err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemset(t->err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        kdt_free(t);
+        return cuda_error(e, "tree allocation", __FILE__, __LINE__);
+    }
+    *out = t;
+    return KDT_OK;
+}
+
+static int check_build_args(const float *d_points, int64_t N, int D)
+{
+    if (!d_points)
+        return set_error(KDT_EINVAL, "d_points is NULL");
+    if (N < 1 || N >= ((int64_t)1 << 30))
+        return set_error(KDT_EINVAL, "N must be in [1, 2^30) (got %lld)", (long long)N);
+    if (D < 1 || D > 8)
+        return set_error(KDT_EINVAL, "D must be in [1, 8] (got %d)", D);
+    return KDT_OK;
+}
+
+static int finish_build(kdt_tree *t, int opts, cudaStream_t s)
+{
+    if (opts & KDT_BUILD_ASYNC)
+        return KDT_OK;
+    int h = 0;
+    KDT_CUDA(cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KDT_CUDA(cudaStreamSynchronize(s));
+    if (h & ERR_NONFINITE)
+        return set_error(KDT_ENONFINITE, "a point coordinate is NaN or infinite");
+    return KDT_OK;
+}
+
+int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream, kdt_tree **out)
+{
+    if (!out)
+        return set_error(KDT_EINVAL, "out is NULL");
+    *out = nullptr;
+    KDT_TRY(check_build_args(d_points, N, D));
+    pool_setup_once();
+    cudaStream_t s = (cudaStream_t)stream;
+    kdt_tree *t = nullptr;
+    KDT_TRY(alloc_tree(N, D, &t));
+    int64_t off[2] = {0, N};
+    int rc = build_forest(d_points, off, 1, D, t->nodes, t->ids, t->bbox, t->err, s);
+    if (rc == KDT_OK)
+        rc = finish_build(t, opts, s);
+    if (rc != KDT_OK) {
+        kdt_free(t);
+        return rc;
+    }
+    *out = t;
+    return KDT_OK;
+}
+
+int kdt_build(const float *d_points, int64_t N, int D, void *stream, kdt_tree **out)
+{
+    return kdt_build_ex(d_points, N, D, 0, stream, out);
+}
+
+int kdt_rebuild(kdt_tree *t, const float *d_points, int opts, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    KDT_TRY(check_build_args(d_points, t->N, t->D));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t off[2] = {0, t->N};
+    KDT_TRY(build_forest(d_points, off, 1, t->D, t->nodes, t->ids, t->bbox, t->err, s));
+    return finish_build(t, opts, s);
+}
+
+int kdt_tree_info(const kdt_tree *t, int64_t *N, int *D)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (N)
+        *N = t->N;
+    if (D)
+        *D = t->D;
+    return KDT_OK;
+}
+
+int kdt_tree_export(const kdt_tree *t, float *d_coords, int32_t *d_ids, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    export_kernel<<<grid_1d(t->N), 256, 0, s>>>(t->nodes, t->ids, t->N, t->D, d_coords, d_ids);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_knn(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, int flags, int32_t *d_ids,
+            float *d_d2, void *stream)
+{
+    KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_ids, d_d2));
+    if (Q == 0)
+        return KDT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    float r2 = max_radius * max_radius;
+    if (flags & KDT_LEARNED)
+        return run_learned_query(const_cast<kdt_tree *>(t), d_q, Q, k, r2, flags, d_ids, d_d2, s);
+    return run_query(t, d_q, Q, k, r2, flags, 0, d_ids, d_d2, nullptr, s);
+}
+
+int kdt_fcp(const kdt_tree *t, const float *d_q, int64_t Q, float max_radius, int flags, int32_t *d_ids, float *d_d2,
+            void *stream)
+{
+    return kdt_knn(t, d_q, Q, 1, max_radius, flags, d_ids, d_d2, stream);
+}
+
+int kdt_knn_visits(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, int flags,
+                   int32_t *d_visits, void *stream)
+{
+    KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_visits, (const void *)1));
+    if (flags & KDT_LEARNED)
+        return set_error(KDT_EINVAL, "kdt_knn_visits does not take KDT_LEARNED");
+    if (Q == 0)
+        return KDT_OK;
+    return run_query(t, d_q, Q, k, max_radius * max_radius, flags, 1, nullptr, nullptr, d_visits,
+                     (cudaStream_t)stream);
+}
+
+int kdt_status(kdt_tree *t, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    KDT_CUDA(cudaStreamSynchronize(s));
+    KDT_CUDA(cudaMemcpy(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost));
+    KDT_CUDA(cudaMemset(t->err, 0, sizeof(int)));
+    if (h & ERR_NONFINITE)
+        return set_error(KDT_ENONFINITE, "a point coordinate is NaN or infinite");
+    if (h & ERR_TRAVERSAL)
+        return set_error(KDT_ETRAVERSAL, "a traversal exceeded its step bound");
+    return KDT_OK;
+}
+
+void kdt_free(kdt_tree *t)
+{
+    if (!t)
+        return;
+    cudaFree(t->nodes);
+    cudaFree(t->ids);
+    cudaFree(t->bbox);
+    cudaFree(t->err);
+    free_model(t);
+    if (t->prof) {
+        Prof *p = (Prof *)t->prof;
+        for (cudaEvent_t e : p->ev)
+            cudaEventDestroy(e);
+        delete p;
+    }
+    delete t;
+}
+
+int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_q, int64_t Q, int k, float max_radius,
+                 int flags, int32_t *h_ids, float *h_d2)
+{
+    if (!h_points || (Q > 0 && (!h_q || !h_ids || !h_d2)))
+        return set_error(KDT_EINVAL, "NULL host pointer");
+    KDT_TRY(check_build_args(h_points, N, D));
+    if (k < 1 || k > 64 || Q < 0 || bad_radius(max_radius))
+        return set_error(KDT_EINVAL, "bad k, Q or max_radius");
+    if (flags & KDT_LEARNED)
+        return set_error(KDT_EINVAL, "kdt_knn_host builds a fresh tree, which has no radius model");
+    pool_setup_once();
+    cudaStream_t s;
+    KDT_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int rc = KDT_OK;
+    kdt_tree *t = nullptr;
+    {
+        Scratch sc(s);
+        size_t pb = (size_t)N * D * 4, qb = (size_t)Q * D * 4, ob = (size_t)Q * k * 4;
+        rc = sc.alloc(carve_size({pb, qb, ob, ob}));
+        if (rc == KDT_OK) {
+            Carve c{(char *)sc.p};
+            float *dp = c.take<float>((size_t)N * D);
+            float *dq = c.take<float>((size_t)Q * D);
+            int32_t *di = c.take<int32_t>((size_t)Q * k);
+            float *dd = c.take<float>((size_t)Q * k);
+            cudaError_t e = cudaMemcpyAsync(dp, h_points, pb, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess && Q > 0)
+                e = cudaMemcpyAsync(dq, h_q, qb, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess)
+                rc = cuda_error(e, "host to device copy", __FILE__, __LINE__);
+            if (rc == KDT_OK)
+                rc = kdt_build_ex(dp, N, D, 0, s, &t);
+            if (rc == KDT_OK && Q > 0)
+                rc = kdt_knn(t, dq, Q, k, max_radius, flags, di, dd, s);
+            if (rc == KDT_OK && Q > 0) {
+                e = cudaMemcpyAsync(h_ids, di, ob, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h_d2, dd, ob, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess)
+                    rc = cuda_error(e, "device to host copy", __FILE__, __LINE__);
+            }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (rc == KDT_OK && e != cudaSuccess)
+        rc = cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    if (rc == KDT_OK && t)
+        rc = kdt_status(t, s);
+    kdt_free(t);
+    cudaStreamDestroy(s);
+    return rc;
+}
+
+int kdt_profile_enable(kdt_tree *t, int enable)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    t->profiling = enable != 0;
+    return KDT_OK;
+}
+
+int kdt_profile_read(kdt_tree *t, double *ms, int64_t *launches)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    Prof *p = (Prof *)t->prof;
+    double total = 0;
+    for (size_t i = 0; i + 1 < p->used; i += 2) {
+        KDT_CUDA(cudaEventSynchronize(p->ev[i + 1]));
+        float m = 0;
+        KDT_CUDA(cudaEventElapsedTime(&m, p->ev[i], p->ev[i + 1]));
+        total += m;
+    }
+    if (ms)
+        *ms = total;
+    if (launches)
+        *launches = (int64_t)(p->used / 2);
+    p->used = 0;
+    return KDT_OK;
+}
+
+// ---------------------------------------------------------------- forests
+
+struct ForestGraph {
+    cudaGraphExec_t exec = nullptr;
+    const float *q = nullptr;
+    int32_t *ids = nullptr;
+    float *d2 = nullptr;
+    int k = 0;
+    float r2 = 0;
+    int flags = 0;
+    std::vector<int64_t> qoff;
+    void *scratch = nullptr;   // persistent scratch referenced by the graph
+    size_t scratch_bytes = 0;
+};
+
+int kdt_build_batched(const float *d_points, const int64_t *h_off, int T, int D, void *stream, kdt_forest **out)
+{
+    if (!out)
+        return set_error(KDT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d_points || !h_off || T < 1 || D < 1 || D > 8)
+        return set_error(KDT_EINVAL, "bad forest arguments (T=%d, D=%d)", T, D);
+    if (h_off[0] != 0)
+        return set_error(KDT_EINVAL, "offsets must start at 0");
+    for (int i = 0; i < T; ++i) {
+        int64_t n = h_off[i + 1] - h_off[i];
+        if (n < 0 || n >= ((int64_t)1 << 30))
+            return set_error(KDT_EINVAL, "cloud %d has bad size %lld", i, (long long)n);
+    }
+    if (h_off[T] >= ((int64_t)1 << 32))
+        return set_error(KDT_EINVAL, "total points must be < 2^32");
+    pool_setup_once();
+    cudaStream_t s = (cudaStream_t)stream;
+    kdt_forest *f = new (std::nothrow) kdt_forest();
+    if (!f)
+        return set_error(KDT_ENOMEM, "host allocation failed");
+    f->f.T = T;
+    f->f.D = D;
+    f->f.total = h_off[T];
+    f->h_offsets = new int64_t[T + 1];
+    memcpy(f->h_offsets, h_off, (T + 1) * sizeof(int64_t));
+    int64_t total = std::max<int64_t>(h_off[T], 1);
+    cudaError_t e = cudaMalloc(&f->nodes, (size_t)total * float4_per_node(D) * sizeof(float4));
+    if (e == cudaSuccess && layout_of(D) > 0)
+        e = cudaMalloc(&f->ids, (size_t)total * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&f->bbox, (size_t)T * 6 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&f->f.d_offsets, (size_t)(T + 1) * sizeof(int64_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&f->err, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(f->err, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f->f.d_offsets, h_off, (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    int rc = e == cudaSuccess ? KDT_OK : cuda_error(e, "forest allocation", __FILE__, __LINE__);
+    if (rc == KDT_OK)
+        rc = build_forest(d_points, h_off, T, D, f->nodes, f->ids, f->bbox, f->err, s);
+    if (rc == KDT_OK) {
+        int h = 0;
+        e = cudaMemcpyAsync(&h, f->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            rc = cuda_error(e, "forest build", __FILE__, __LINE__);
+        else if (h & ERR_NONFINITE)
+            rc = set_error(KDT_ENONFINITE, "a point coordinate is NaN or infinite");
+    }
+    if (rc != KDT_OK) {
+        kdt_forest_free(f);
+        return rc;
+    }
+    *out = f;
+    return KDT_OK;
+}
+
+static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64_t Q, const int64_t *d_qoff, int k,
+                          float r2, int flags, int32_t *d_ids, float *d_d2, cudaStream_t s)
+{
+    const int T = f->f.T;
+    Carve c{(char *)g->scratch};
+    unsigned long long *counter = c.take<unsigned long long>(8);
+    c.take<int64_t>(T + 1);  // query offsets (filled before)
+    QueryArgs a;
+    if (flags & KDT_MORTON) {
+        int tbits = T > 1 ? floor_log2((uint64_t)(T - 1)) + 1 : 0;
+        KDT_TRY(morton_order(d_q, Q, f->f.D, f->bbox, T, d_qoff, tbits, c.base + c.off,
+                             const_cast<uint32_t **>(&a.perm), s));
+    }
+    a.nodes = f->nodes;
+    a.ids = f->ids;
+    a.D = f->f.D;
+    a.queries = d_q;
+    a.Q = Q;
+    a.k = k;
+    a.r2 = r2;
+    a.out_ids = d_ids;
+    a.out_d2 = d_d2;
+    a.err = f->err;
+    a.counter = counter;
+    a.T = T;
+    a.node_off = f->f.d_offsets;
+    a.q_off = d_qoff;
+    return launch_query(layout_of(f->f.D), a, !(flags & KDT_UNORDERED), 0, true, s);
+}
+
+int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int k, float max_radius, int flags,
+                    int32_t *d_ids, float *d_d2, void *stream)
+{
+    if (!f || !h_qoff)
+        return set_error(KDT_EINVAL, "NULL forest or offsets");
+    const int T = f->f.T;
+    if (k < 1 || k > 64 || bad_radius(max_radius))
+        return set_error(KDT_EINVAL, "bad k or max_radius");
+    if (flags & KDT_LEARNED)
+        return set_error(KDT_EINVAL, "KDT_LEARNED is not supported for forests");
+    if (h_qoff[0] != 0)
+        return set_error(KDT_EINVAL, "query offsets must start at 0");
+    for (int i = 0; i < T; ++i)
+        if (h_qoff[i + 1] < h_qoff[i])
+            return set_error(KDT_EINVAL, "query offsets must be non-decreasing");
+    const int64_t Q = h_qoff[T];
+    if (Q >= ((int64_t)1 << 32))
+        return set_error(KDT_EINVAL, "total queries must be < 2^32");
+    if (Q == 0)
+        return KDT_OK;
+    if (!d_q || !d_ids || !d_d2)
+        return set_error(KDT_EINVAL, "NULL query or output pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float r2 = max_radius * max_radius;
+
+    if (flags & KDT_PER_TREE) {
+        // the same traversal, one launch per tree
+        Scratch sc(s);
+        KDT_TRY(sc.alloc(256));
+        unsigned long long *counter = (unsigned long long *)sc.p;
+        const int layout = layout_of(f->f.D);
+        const int NF = float4_per_node(f->f.D);
+        for (int i = 0; i < T; ++i) {
+            int64_t nq = h_qoff[i + 1] - h_qoff[i];
+            int64_t nb = f->h_offsets[i];
+            int64_t n = f->h_offsets[i + 1] - nb;
+            if (nq == 0)
+                continue;
+            if (n == 0) {
+                KDT_CUDA(cudaMemsetAsync(d_ids + h_qoff[i] * k, 0xff, nq * k * 4, s));
+                fill_inf(d_d2 + h_qoff[i] * k, nq * k, s);
+                continue;
+            }
+            QueryArgs a;
+            a.nodes = f->nodes + nb * NF;
+            a.ids = f->ids ? f->ids + nb : nullptr;
+            a.N = (int)n;
+            a.D = f->f.D;
+            a.queries = d_q + h_qoff[i] * f->f.D;
+            a.Q = nq;
+            a.k = k;
+            a.r2 = r2;
+            a.out_ids = d_ids + h_qoff[i] * k;
+            a.out_d2 = d_d2 + h_qoff[i] * k;
+            a.err = f->err;
+            a.counter = counter;
+            a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(n, layout, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+            KDT_TRY(launch_query(layout, a, !(flags & KDT_UNORDERED), 0, false, s));
+        }
+        return KDT_OK;
+    }
+
+    ForestGraph *g = (ForestGraph *)f->graph;
+    if (!g) {
+        g = new ForestGraph();
+        f->graph = g;
+    }
+    const bool same = g->exec && g->q == d_q && g->ids == d_ids && g->d2 == d_d2 && g->k == k && g->r2 == r2 &&
+                      g->flags == flags && g->qoff.size() == (size_t)T + 1 &&
+                      std::equal(g->qoff.begin(), g->qoff.end(), h_qoff);
+    if (!same) {
+        if (g->exec) {
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+        size_t need = carve_size({64, (size_t)(T + 1) * 8}) + ((flags & KDT_MORTON) ? morton_scratch_bytes(Q) : 0);
+        if (need > g->scratch_bytes) {
+            KDT_CUDA(cudaStreamSynchronize(s));
+            cudaFree(g->scratch);
+            g->scratch = nullptr;
+            g->scratch_bytes = 0;
+            KDT_CUDA(cudaMalloc(&g->scratch, need));
+            g->scratch_bytes = need;
+        }
+        g->q = d_q;
+        g->ids = d_ids;
+        g->d2 = d_d2;
+        g->k = k;
+        g->r2 = r2;
+        g->flags = flags;
+        g->qoff.assign(h_qoff, h_qoff + T + 1);
+    }
+    Carve c{(char *)g->scratch};
+    c.take<unsigned long long>(8);
+    int64_t *d_qoff = c.take<int64_t>(T + 1);
+    if (!same)
+        KDT_CUDA(cudaMemcpyAsync(d_qoff, h_qoff, (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KDT_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone || s == nullptr)
+        return forest_enqueue(f, g, d_q, Q, d_qoff, k, r2, flags, d_ids, d_d2, s);
+    if (!g->exec) {
+        cudaGraph_t graph = nullptr;
+        KDT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = forest_enqueue(f, g, d_q, Q, d_qoff, k, r2, flags, d_ids, d_d2, s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rc != KDT_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return rc;
+        }
+        KDT_CUDA(e);
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        KDT_CUDA(e);
+    }
+    KDT_CUDA(cudaGraphLaunch(g->exec, s));
+    return KDT_OK;
+}
+
+int kdt_forest_export(const kdt_forest *f, float *d_coords, int32_t *d_ids, void *stream)
+{
+    if (!f)
+        return set_error(KDT_EINVAL, "forest is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (f->f.total == 0)
+        return KDT_OK;
+    export_kernel<<<grid_1d(f->f.total), 256, 0, s>>>(f->nodes, f->ids, f->f.total, f->f.D, d_coords, d_ids);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+void kdt_forest_free(kdt_forest *f)
+{
+    if (!f)
+        return;
+    if (f->graph) {
+        ForestGraph *g = (ForestGraph *)f->graph;
+        if (g->exec)
+            cudaGraphExecDestroy(g->exec);
+        cudaFree(g->scratch);
+        delete g;
+    }
+    cudaFree(f->nodes);
+    cudaFree(f->ids);
+    cudaFree(f->bbox);
+    cudaFree(f->f.d_offsets);
+    cudaFree(f->err);
+    delete[] f->h_offsets;
+    delete f;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kdt.h"
+
+namespace kdt {
+
+// ---------------------------------------------------------------- errors
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+#define KDT_CUDA(call)                                                          \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess)                                                  \
+            return ::kdt::cuda_error(e_, #call, __FILE__, __LINE__);            \
+    } while (0)
+
+#define KDT_TRY(call)                                                           \
+    do {                                                                        \
+        int rc_ = (call);                                                       \
+        if (rc_ != KDT_OK)                                                      \
+            return rc_;                                                         \
+    } while (0)
+
+// device error word bits
+enum : int { ERR_NONFINITE = 1, ERR_TRAVERSAL = 2 };
+
+// ---------------------------------------------------------------- topology
+// A complete, left-balanced tree of n nodes in level order (root 0, children
+// 2t+1 and 2t+2).  H = floor(log2 n) is the last level and M the number of
+// nodes on it.  In a perfect tree of H+1 levels the in-order index of the
+// j-th node of level l is (2j+1)*2^(H-l) - 1; the complete tree lacks the
+// last-level nodes j >= M, whose perfect in-order indices are the even numbers
+// 2j, so an in-order index shifts down by the number of missing nodes before
+// it.
+
+__host__ __device__ __forceinline__ int floor_log2(uint64_t v)
+{
+#ifdef __CUDA_ARCH__
+    return 63 - __clzll((long long)v);
+#else
+    return 63 - __builtin_clzll(v);
+#endif
+}
+
+__host__ __device__ __forceinline__ int count_tz(uint64_t v)
+{
+#ifdef __CUDA_ARCH__
+    return __ffsll((long long)v) - 1;
+#else
+    return __builtin_ctzll(v);
+#endif
+}
+
+struct Topo {
+    int64_t n;
+    int H;
+    int64_t M;
+    __host__ __device__ __forceinline__ explicit Topo(int64_t n_) : n(n_)
+    {
+        H = n_ > 0 ? floor_log2((uint64_t)n_) : 0;
+        M = n_ - (((int64_t)1 << H) - 1);
+    }
+    __host__ __device__ __forceinline__ static int level(int64_t t) { return floor_log2((uint64_t)(t + 1)); }
+
+    // in-order index of node t (t < n)
+    __host__ __device__ __forceinline__ int64_t inorder(int64_t t) const
+    {
+        int l = level(t);
+        int64_t j = t - (((int64_t)1 << l) - 1);
+        int64_t P = ((2 * j + 1) << (H - l)) - 1;
+        int64_t half = (P + 1) >> 1;
+        int64_t full = (int64_t)1 << H;
+        int64_t missing = (half < full ? half : full) - M;
+        return P - (missing > 0 ? missing : 0);
+    }
+    // node at in-order index p (p < n)
+    __host__ __device__ __forceinline__ int64_t node_at(int64_t p) const
+    {
+        int64_t P = p < 2 * M ? p : 2 * (p - M) + 1;
+        int tz = count_tz((uint64_t)(P + 1));
+        int l = H - tz;
+        int64_t j = (P + 1) >> (tz + 1);
+        return (((int64_t)1 << l) - 1) + j;
+    }
+    // leftmost node of the subtree of t
+    __host__ __device__ __forceinline__ int64_t leftmost(int64_t t) const
+    {
+        int m = H - level(t);
+        int64_t u = ((t + 1) << m) - 1;
+        if (u >= n)
+            u = ((t + 1) << (m - 1)) - 1;
+        return u;
+    }
+    // ancestor of u on level l (level(u) >= l)
+    __host__ __device__ __forceinline__ static int64_t ancestor(int64_t u, int lu, int l)
+    {
+        return ((u + 1) >> (lu - l)) - 1;
+    }
+};
+
+// order-preserving unsigned key of a finite float; -0 is mapped to +0 first
+__host__ __device__ __forceinline__ uint32_t float_key(float x)
+{
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(x);
+#else
+    __builtin_memcpy(&u, &x, 4);
+#endif
+    if (u == 0x80000000u)
+        u = 0;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ---------------------------------------------------------------- layouts
+// Node storage:
+//   layout 0 (D <= 3): float4 {x, y, z, id bits} per node, unused coords = 0
+//   layout 1 (D == 4): float4 {c0..c3} per node + int32 ids[N]
+//   layout 2 (D 5..8): 2 x float4 {c0..c7} per node + int32 ids[N], unused = 0
+__host__ __device__ __forceinline__ int layout_of(int D) { return D <= 3 ? 0 : (D == 4 ? 1 : 2); }
+__host__ __device__ __forceinline__ int float4_per_node(int D) { return D <= 4 ? 1 : 2; }
+
+// ---------------------------------------------------------------- primitives
+// Stable LSD radix sort of (u32 key, u32 value) pairs on bits [0, bits).
+// keys/vals hold the input and receive the output; tmp_k / tmp_v are scratch of
+// n elements each.
+struct SortScratch {
+    uint32_t *hist = nullptr;      // 256 * tiles
+    uint32_t *partials = nullptr;  // scan partials
+    size_t hist_elems = 0;
+};
+size_t radix_scratch_elems(int64_t n);
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *tmp_v, int64_t n,
+                     int bits, uint32_t *scratch, cudaStream_t s);
+
+// exclusive prefix sum of u32 in place (n elements), scratch of
+// scan_scratch_elems(n) elements
+size_t scan_scratch_elems(int64_t n);
+int exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *scratch, cudaStream_t s);
+
+int num_sms();
+
+// ---------------------------------------------------------------- objects
+
+struct Model {
+    bool trained = false;
+    float *d_params = nullptr;     // FP32 master weights [KDT_MLP_PARAMS]
+    float norm[8] = {0, 0, 0, 0, 1, 1, 1, 1};
+    float margin = 1.25f;
+    int k_trained = 0;
+};
+
+struct ForestDesc {
+    int T = 1;
+    int D = 3;
+    int64_t total = 0;
+    int64_t *d_offsets = nullptr;  // [T+1] node offsets of each tree
+    int32_t *d_tree_of = nullptr;  // [total] tree index per node position (T > 1 only)
+    int maxH = 0;
+};
+
+}  // namespace kdt
+
+struct kdt_tree {
+    int64_t N = 0;
+    int D = 0;
+    int layout = 0;
+    int device = 0;
+    float4 *nodes = nullptr;       // N * float4_per_node(D)
+    int32_t *ids = nullptr;        // layout > 0
+    float *bbox = nullptr;         // device [2][3]: lo, hi of the first min(D,3) dims
+    int *err = nullptr;            // device error word
+    kdt::Model model;
+    // learned-path statistics of the last learned query
+    int64_t *stats = nullptr;      // device [2]: fallback count, ratio sum as fixed-point
+    double *ratio_sum = nullptr;   // device
+    int64_t last_learned_q = 0;
+    // profiling
+    bool profiling = false;
+    void *prof = nullptr;
+};
+
+struct kdt_forest {
+    kdt::ForestDesc f;
+    float4 *nodes = nullptr;
+    int32_t *ids = nullptr;
+    float *bbox = nullptr;         // [T][2][3]
+    int64_t *h_offsets = nullptr;  // host copy [T+1]
+    int *err = nullptr;
+    void *graph = nullptr;         // cached graph of the batched query
+};
+
+namespace kdt {
+// builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
+int build_forest(const float *d_points, const int64_t *h_offsets, int T, int D, float4 *nodes,
+                 int32_t *ids, float *bbox, int *err, cudaStream_t s);
+}  // namespace kdt

@@ -1,0 +1,14 @@
+// Learned radius proposal: model storage, features, MLP kernels and the
+// learned query path (not in the paper; results never change).
+#pragma once
+
+#include "kdt_internal.cuh"
+
+namespace kdt {
+int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int32_t *d_ids,
+                      float *d_d2, cudaStream_t s);
+int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int mode, int32_t *d_ids,
+              float *d_d2, int32_t *d_visits, cudaStream_t s);
+void free_model(kdt_tree *t);
+void fill_inf(float *p, int64_t n, cudaStream_t s);
+}  // namespace kdt

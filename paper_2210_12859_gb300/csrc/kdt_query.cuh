@@ -1,0 +1,63 @@
+// Query kernels (plain single-tree and batched forests) and their launcher
+// interface.  Each node layout is instantiated in its own translation unit.
+#pragma once
+
+#include "kdt_traverse.cuh"
+
+namespace kdt {
+
+constexpr int REG_THREADS = 256;   // block size of the register-list kernels
+constexpr int SMEM_THREADS = 128;  // block size of the shared-memory-list kernels
+constexpr int MAX_REG_K = 16;
+
+struct QueryArgs {
+    const float4 *nodes = nullptr;     // single tree: its nodes; batched: all nodes
+    const int32_t *ids = nullptr;
+    int N = 0;                         // single tree size
+    int D = 0;
+    const float *queries = nullptr;
+    int64_t Q = 0;
+    const uint32_t *perm = nullptr;    // traversal order -> query index (optional)
+    int k = 1;
+    float r2 = 0.f;
+    int32_t *out_ids = nullptr;
+    float *out_d2 = nullptr;
+    int32_t *visits = nullptr;         // COUNT variants
+    int *err = nullptr;
+    int staged = 0;                    // nodes staged in shared memory
+    unsigned long long *counter = nullptr;  // dynamic work counter, zeroed before launch
+    // batched forests
+    int T = 1;
+    const int64_t *node_off = nullptr; // [T+1]
+    const int64_t *q_off = nullptr;    // [T+1]
+    int64_t q_begin = 0;               // first query slot served by this launch
+};
+
+// Launch the plain traversal for one layout.  mode: 0 results, 1 visit counts.
+int launch_query_layout0(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
+int launch_query_layout1(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
+int launch_query_layout2(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
+
+inline int launch_query(int layout, const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s)
+{
+    switch (layout) {
+    case 0: return launch_query_layout0(a, ordered, mode, batched, s);
+    case 1: return launch_query_layout1(a, ordered, mode, batched, s);
+    default: return launch_query_layout2(a, ordered, mode, batched, s);
+    }
+}
+
+// number of nodes to stage for a tree of n nodes and a shared-memory budget
+inline int staged_nodes(int64_t n, int layout, int budget_bytes)
+{
+    int per = layout == 2 ? 32 : 16;
+    int64_t lv = 0;
+    while ((((int64_t)2 << lv) - 1) * per <= budget_bytes && lv < 20)
+        ++lv;
+    int64_t cap = ((int64_t)1 << lv) - 1;
+    return (int)(n < cap ? n : cap);
+}
+
+int grid_for_kernel(const void *fn, int threads, size_t smem);
+
+}  // namespace kdt

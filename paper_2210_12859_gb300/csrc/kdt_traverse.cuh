@@ -1,0 +1,266 @@
+// Device-side traversal core shared by the plain, learned and batched query
+// kernels: node fetch for the three node layouts, the FP32 squared distance,
+// the k-best lists and the stack-free (curr, prev) state machine of Sec. 3.2.
+#pragma once
+
+#include "kdt_internal.cuh"
+
+namespace kdt {
+
+// number of coordinate slots per layout (padding slots hold 0 in both the
+// node and the query, and add exactly +0 to a distance)
+template <int LAYOUT> struct LayoutTraits;
+template <> struct LayoutTraits<0> { static constexpr int NC = 3; static constexpr int NF = 1; };
+template <> struct LayoutTraits<1> { static constexpr int NC = 4; static constexpr int NF = 1; };
+template <> struct LayoutTraits<2> { static constexpr int NC = 8; static constexpr int NF = 2; };
+
+template <int LAYOUT>
+struct NodeVal {
+    float c[LayoutTraits<LAYOUT>::NC];
+    uint32_t id;  // layout 0 only
+};
+
+__device__ __forceinline__ float4 ldg_f4(const float4 *p) { return __ldg(p); }
+
+// Fetch node `curr` (from shared memory when it is among the `staged` first
+// nodes).  nodes: the tree's node array (already offset to the tree's base).
+template <int LAYOUT>
+__device__ __forceinline__ NodeVal<LAYOUT> fetch(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged,
+                                                 int curr)
+{
+    NodeVal<LAYOUT> v;
+    if constexpr (LAYOUT == 2) {
+        float4 a, b;
+        if (curr < staged) {
+            a = s_nodes[2 * curr];
+            b = s_nodes[2 * curr + 1];
+        } else {
+            a = ldg_f4(nodes + 2 * curr);
+            b = ldg_f4(nodes + 2 * curr + 1);
+        }
+        v.c[0] = a.x; v.c[1] = a.y; v.c[2] = a.z; v.c[3] = a.w;
+        v.c[4] = b.x; v.c[5] = b.y; v.c[6] = b.z; v.c[7] = b.w;
+        v.id = 0;
+    } else {
+        float4 a = curr < staged ? s_nodes[curr] : ldg_f4(nodes + curr);
+        v.c[0] = a.x; v.c[1] = a.y; v.c[2] = a.z;
+        if constexpr (LAYOUT == 1) {
+            v.c[3] = a.w;
+            v.id = 0;
+        } else {
+            v.id = __float_as_uint(a.w);
+        }
+    }
+    return v;
+}
+
+template <int NC>
+__device__ __forceinline__ float select_dim(const float (&c)[NC], int dim)
+{
+    float r = c[0];
+#pragma unroll
+    for (int j = 1; j < NC; ++j)
+        r = dim == j ? c[j] : r;
+    return r;
+}
+
+// d2 = ((t_0 + t_1) + t_2) + ..., t_j = fl(fl(p_j - q_j)^2); the _rn
+// intrinsics are never contracted into fused multiply-adds.
+template <int NC>
+__device__ __forceinline__ float dist2(const float (&p)[NC], const float (&q)[NC])
+{
+    float d = __fsub_rn(p[0], q[0]);
+    float s = __fmul_rn(d, d);
+#pragma unroll
+    for (int j = 1; j < NC; ++j) {
+        float dj = __fsub_rn(p[j], q[j]);
+        s = __fadd_rn(s, __fmul_rn(dj, dj));
+    }
+    return s;
+}
+
+// (d2, id) packed so that unsigned 64-bit order is the lexicographic order:
+// d2 >= +0 or NaN, whose float bits order like unsigned integers.
+__device__ __forceinline__ unsigned long long pack_key(float d2, uint32_t id)
+{
+    return ((unsigned long long)__float_as_uint(d2) << 32) | id;
+}
+__device__ __forceinline__ float key_d2(unsigned long long k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+constexpr uint32_t EMPTY_ID = 0xffffffffu;
+
+// Register-resident sorted k-best list of capacity K.  A query for k <= K
+// neighbours fills the first K-k slots with key 0 (below every real key), so
+// they never move, and the k real slots start at (r2, EMPTY_ID): a candidate
+// is accepted iff its key is below the last slot, which is exactly
+// "d2 <= r2 and (list not full or (d2, id) < worst)"; the last slot's d2 is
+// the shrinking cull radius (r2 until k points are held).
+template <int K>
+struct RegList {
+    unsigned long long L[K];
+    __device__ __forceinline__ void init(int k, float r2)
+    {
+        unsigned long long s = pack_key(r2, EMPTY_ID);
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            L[i] = i < K - k ? 0ull : s;
+    }
+    __device__ __forceinline__ float cull() const { return key_d2(L[K - 1]); }
+    __device__ __forceinline__ unsigned long long worst() const { return L[K - 1]; }
+    __device__ __forceinline__ void insert(unsigned long long c)
+    {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            unsigned long long a = L[i];
+            bool sw = c < a;
+            L[i] = sw ? c : a;
+            c = sw ? a : c;
+        }
+    }
+    __device__ __forceinline__ void store(int k, int32_t *ids, float *d2) const
+    {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            int o = i - (K - k);
+            if (o >= 0) {
+                uint32_t id = (uint32_t)L[i];
+                bool empty = id == EMPTY_ID;
+                ids[o] = empty ? -1 : (int32_t)id;
+                d2[o] = empty ? __int_as_float(0x7f800000) : key_d2(L[i]);
+            }
+        }
+    }
+    __device__ __forceinline__ bool full(int) const { return (uint32_t)L[K - 1] != EMPTY_ID; }
+};
+
+// Shared-memory sorted k-best list for 16 < k <= 64, one column per thread
+// (slot i of thread t at s[i * stride + t]: consecutive threads hit
+// consecutive banks).  The worst key is mirrored in a register.
+struct SmemList {
+    unsigned long long *s;
+    int stride;
+    int k;
+    unsigned long long w;
+    __device__ __forceinline__ void init(int k_, float r2)
+    {
+        k = k_;
+        w = pack_key(r2, EMPTY_ID);
+        for (int i = 0; i < k; ++i)
+            s[i * stride] = w;
+    }
+    __device__ __forceinline__ float cull() const { return key_d2(w); }
+    __device__ __forceinline__ unsigned long long worst() const { return w; }
+    __device__ __forceinline__ void insert(unsigned long long c)
+    {
+        int pos = k - 1;
+        while (pos > 0) {
+            unsigned long long a = s[(pos - 1) * stride];
+            if (!(c < a))
+                break;
+            s[pos * stride] = a;
+            --pos;
+        }
+        s[pos * stride] = c;
+        w = s[(k - 1) * stride];
+    }
+    __device__ __forceinline__ void store(int, int32_t *ids, float *d2) const
+    {
+        for (int i = 0; i < k; ++i) {
+            unsigned long long key = s[i * stride];
+            uint32_t id = (uint32_t)key;
+            bool empty = id == EMPTY_ID;
+            ids[i] = empty ? -1 : (int32_t)id;
+            d2[i] = empty ? __int_as_float(0x7f800000) : key_d2(key);
+        }
+    }
+    __device__ __forceinline__ bool full(int) const { return (uint32_t)w != EMPTY_ID; }
+};
+
+// One query through the stack-free state machine (Sec. 3.2).  Invalid children
+// are never stepped into: stepping into a missing child and straight back only
+// returns to the same node with prev = that child, so the machine continues
+// as if the child had been visited; the sequence of valid nodes, and hence
+// every processNode call, is unchanged.  Returns the number of first visits,
+// or -1 if the step bound 3N+3 was exceeded (impossible for a valid tree).
+template <int LAYOUT, bool ORDERED, class List>
+__device__ __forceinline__ int traverse(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
+                                        const float4 *s_nodes, int staged, int N, int D,
+                                        const float (&q)[LayoutTraits<LAYOUT>::NC], List &list)
+{
+    constexpr int NC = LayoutTraits<LAYOUT>::NC;
+    int curr = 0, prev = -1, dim = 0, visits = 0;
+    const long long cap = 3ll * N + 3;
+    for (long long step = 0;; ++step) {
+        if (step > cap)
+            return -1;
+        NodeVal<LAYOUT> nd = fetch<LAYOUT>(nodes, s_nodes, staged, curr);
+        const bool from_parent = prev < curr;
+        if (from_parent) {
+            ++visits;
+            float d2 = dist2<NC>(nd.c, q);
+            if (d2 <= key_d2(list.worst())) {
+                uint32_t id = LAYOUT == 0 ? nd.id : (uint32_t)__ldg(ids + curr);
+                unsigned long long key = pack_key(d2, id);
+                if (key < list.worst())
+                    list.insert(key);
+            }
+        }
+        const float cull = list.cull();
+        const float sd = __fsub_rn(select_dim<NC>(q, dim), select_dim<NC>(nd.c, dim));
+        const float sd2 = __fmul_rn(sd, sd);
+        const int lc = 2 * curr + 1;
+        const int parent = (curr - 1) >> 1;  // -1 for the root
+        int next;
+        if constexpr (ORDERED) {
+            const int close_side = sd > 0.f;
+            const int close_child = lc + close_side;
+            const int far_child = lc + 1 - close_side;
+            const bool far_ok = sd2 <= cull && far_child < N;
+            if (from_parent)
+                next = close_child < N ? close_child : (far_ok ? far_child : parent);
+            else if (prev == close_child)
+                next = far_ok ? far_child : parent;
+            else
+                next = parent;
+        } else {
+            const int rc = lc + 1;
+            const bool left_ok = (sd <= 0.f || sd2 <= cull) && lc < N;
+            const bool right_ok = (sd > 0.f || sd2 <= cull) && rc < N;
+            if (from_parent)
+                next = left_ok ? lc : (right_ok ? rc : parent);
+            else if (prev == lc)
+                next = right_ok ? rc : parent;
+            else
+                next = parent;
+        }
+        if (next < 0)
+            return visits;
+        if (next == parent)
+            dim = dim == 0 ? D - 1 : dim - 1;
+        else
+            dim = dim + 1 == D ? 0 : dim + 1;
+        prev = curr;
+        curr = next;
+    }
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ void load_query(const float *__restrict__ queries, int64_t qi, int D,
+                                           float (&q)[LayoutTraits<LAYOUT>::NC])
+{
+    constexpr int NC = LayoutTraits<LAYOUT>::NC;
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+        q[j] = j < D ? __ldg(queries + qi * D + j) : 0.f;
+}
+
+// stage the first `staged` nodes of a tree into shared memory (whole block)
+template <int LAYOUT>
+__device__ __forceinline__ void stage_nodes(const float4 *__restrict__ nodes, float4 *s_nodes, int staged)
+{
+    constexpr int NF = LayoutTraits<LAYOUT>::NF;
+    for (int i = threadIdx.x; i < staged * NF; i += blockDim.x)
+        s_nodes[i] = ldg_f4(nodes + i);
+}
+
+}  // namespace kdt

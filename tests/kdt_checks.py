@@ -1,0 +1,45 @@
+"""Test-side checks that hold at any size (no oracle arithmetic)."""
+import numpy as np
+
+
+def float_key(x: np.ndarray) -> np.ndarray:
+    """Order-preserving uint64 key of float32 values (-0 sorts as +0)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = np.where(u == 0x80000000, 0, u)
+    neg = (u & 0x80000000) != 0
+    return np.where(neg, (~u) & 0xFFFFFFFF, u | 0x80000000)
+
+
+def check_tree(points: np.ndarray, node_ids: np.ndarray, node_coords: np.ndarray | None = None) -> None:
+    """Assert that node_ids is the level-order left-balanced k-d tree of the
+    points with split dimension (level mod D) and (coordinate, index) order:
+    the ids form a permutation, and every node's key in its split dimension is
+    above every key of its left subtree and below every key of its right
+    subtree.  Those conditions determine the tree uniquely."""
+    N, D = points.shape
+    ids = np.asarray(node_ids, dtype=np.int64)
+    assert ids.shape == (N,)
+    assert np.array_equal(np.sort(ids), np.arange(N)), "ids are not a permutation"
+    if node_coords is not None:
+        assert np.array_equal(np.asarray(node_coords).view(np.uint32), points[ids].view(np.uint32))
+    H = int(np.floor(np.log2(N)))
+    lvl_start = [(1 << l) - 1 for l in range(H + 2)]
+    for d in range(D):
+        key = (float_key(points[ids, d]) << np.uint64(32)) | ids.astype(np.uint64)
+        mn = key.copy()
+        mx = key.copy()
+        for l in range(H - 1, -1, -1):
+            t = np.arange(lvl_start[l], min(lvl_start[l + 1], N))
+            for c in (2 * t + 1, 2 * t + 2):
+                ok = c < N
+                tt, cc = t[ok], c[ok]
+                mn[tt] = np.minimum(mn[tt], mn[cc])
+                mx[tt] = np.maximum(mx[tt], mx[cc])
+        for l in range(0, H + 1):
+            if l % D != d:
+                continue
+            t = np.arange(lvl_start[l], min(lvl_start[l + 1], N))
+            lc, rc = 2 * t + 1, 2 * t + 2
+            okl, okr = lc < N, rc < N
+            assert (mx[lc[okl]] < key[t[okl]]).all(), f"left subtree not below its node (level {l})"
+            assert (key[t[okr]] < mn[rc[okr]]).all(), f"right subtree not above its node (level {l})"
