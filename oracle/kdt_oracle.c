@@ -31,6 +31,7 @@
  * values fixed by the paper (the six-point example of Figure 1), closed forms,
  * brute force on tiny inputs, library routines and invariants.
  */
+#define _GNU_SOURCE 1 /* qsort_r */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>

@@ -1,7 +1,397 @@
-// Learned radius proposal (not in the paper).
+// Learned radius proposal (not in the paper; results never change).
+//
+// A small MLP predicts, per query, the radius of its k-th nearest neighbour.
+// The proposal r_p = margin * exp(y) seeds the cull radius of the ordered
+// traversal (Sec. 3's shrinking radius then starts small instead of at the
+// caller's radius).  The result is exact for every query whose list is full
+// at the end (any point outside r_p is farther than the k points found inside
+// it) or whose proposal did not shrink the caller's radius; the remaining
+// queries are re-run with the caller's radius.
+//
+// Features: the query coordinates and log(max(d2_leaf, 1e-30)), where d2_leaf
+// is the squared distance to the node where a greedy close-child descent from
+// the root ends, normalised by training mean and standard deviation.
+// Network: 4 -> 64 -> 64 -> 1 with ReLU, weights rounded to BF16, biases and
+// all arithmetic in FP32.  Training: MSE against 0.5*log(d2 of the exact k-th
+// neighbour), Adam, deterministic reductions.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "kdt_learned.cuh"
+#include "kdt_query.cuh"
 
 namespace kdt {
+
+int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
+                 void *scratch, uint32_t **perm_out, cudaStream_t s);
+size_t morton_scratch_bytes(int64_t Q);
+
+namespace {
+
+constexpr int H = KDT_MLP_HIDDEN;
+constexpr int P = KDT_MLP_PARAMS;
+constexpr int OW1 = 0;
+constexpr int OB1 = OW1 + H * 4;
+constexpr int OW2 = OB1 + H;
+constexpr int OB2 = OW2 + H * H;
+constexpr int OW3 = OB2 + H;
+constexpr int OB3 = OW3 + H;
+static_assert(OB3 + 1 == P, "parameter layout");
+static_assert(OW2 % 4 == 0, "W2 must be float4 aligned");
+
+constexpr int TS = 64;  // samples (threads) per training block
+
+__host__ __device__ inline bool is_weight(int i)
+{
+    return i < OB1 || (i >= OW2 && i < OB2) || (i >= OW3 && i < OB3);
+}
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void round_params_kernel(const float *__restrict__ master, float *__restrict__ rounded)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P)
+        rounded[i] = is_weight(i) ? bf16_round(master[i]) : master[i];
+}
+
+// greedy close-child descent; returns d2 to the last valid node
+__device__ __forceinline__ float descent_d2(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged, int N,
+                                            int D, const float (&q)[3])
+{
+    int node = 0, dim = 0;
+    NodeVal<0> nd = fetch<0>(nodes, s_nodes, staged, 0);
+    for (;;) {
+        const float sd = __fsub_rn(select_dim<3>(q, dim), select_dim<3>(nd.c, dim));
+        const int child = 2 * node + 1 + (sd > 0.f);
+        if (child >= N)
+            break;
+        node = child;
+        dim = dim + 1 == D ? 0 : dim + 1;
+        nd = fetch<0>(nodes, s_nodes, staged, node);
+    }
+    return dist2<3>(nd.c, q);
+}
+
+__device__ __forceinline__ float leaf_feature(float d2) { return logf(fmaxf(d2, 1e-30f)); }
+
+// forward pass with the (rounded) parameters in shared memory
+__device__ __forceinline__ float mlp_forward(const float *__restrict__ w, const float (&x)[4])
+{
+    float h1[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        float a = w[OB1 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            a = __fmaf_rn(w[OW1 + 4 * i + j], x[j], a);
+        h1[i] = fmaxf(a, 0.f);
+    }
+    float y = w[OB3];
+#pragma unroll 2
+    for (int i = 0; i < H; ++i) {
+        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
+        float a = w[OB2 + i];
+#pragma unroll
+        for (int j = 0; j < H / 4; ++j) {
+            const float4 r = row[j];
+            a = __fmaf_rn(r.x, h1[4 * j + 0], a);
+            a = __fmaf_rn(r.y, h1[4 * j + 1], a);
+            a = __fmaf_rn(r.z, h1[4 * j + 2], a);
+            a = __fmaf_rn(r.w, h1[4 * j + 3], a);
+        }
+        y = __fmaf_rn(w[OW3 + i], fmaxf(a, 0.f), y);
+    }
+    return y;
+}
+
+struct Norm {
+    float mu[4];
+    float sd[4];
+};
+
+__global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict__ nodes, int N, int D,
+                                                       const float *__restrict__ qs, int64_t Q, int staged,
+                                                       float *__restrict__ feat)
+{
+    extern __shared__ float4 s_nodes[];
+    stage_nodes<0>(nodes, s_nodes, staged);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
+        float q[3];
+        load_query<0>(qs, i, D, q);
+        const float d2 = descent_d2(nodes, s_nodes, staged, N, D, q);
+        float4 f = make_float4(q[0], q[1], q[2], leaf_feature(d2));
+        reinterpret_cast<float4 *>(feat)[i] = f;
+    }
+}
+
+// per-query cull radius of the learned pass: min(fl(r_p * r_p), r2_user)
+__global__ void __launch_bounds__(256) radius_kernel(const float4 *__restrict__ nodes, int N, int D,
+                                                     const float *__restrict__ qs, int64_t Q,
+                                                     const uint32_t *__restrict__ perm, int staged,
+                                                     const float *__restrict__ wts, Norm nm, float margin,
+                                                     float r2_user, float *__restrict__ r2q)
+{
+    extern __shared__ float4 s_dyn[];
+    float *s_w = reinterpret_cast<float *>(s_dyn);
+    float4 *s_nodes = s_dyn + (P + 3) / 4;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        s_w[i] = wts[i];
+    stage_nodes<0>(nodes, s_nodes, staged);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = perm ? (int64_t)perm[i] : i;
+        float q[3];
+        load_query<0>(qs, qi, D, q);
+        const float d2 = descent_d2(nodes, s_nodes, staged, N, D, q);
+        float x[4] = {q[0], q[1], q[2], leaf_feature(d2)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            x[j] = __fdiv_rn(__fsub_rn(x[j], nm.mu[j]), nm.sd[j]);
+        const float y = mlp_forward(s_w, x);
+        const float r = __fmul_rn(margin, expf(y));
+        const float rp2 = __fmul_rn(r, r);
+        r2q[qi] = (rp2 == rp2 && rp2 < r2_user) ? rp2 : r2_user;
+    }
+}
+
+__global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restrict__ wts, const float *__restrict__ x,
+                                                          int64_t n, float *__restrict__ y)
+{
+    __shared__ __align__(16) float s_w[P + 3];
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        s_w[i] = wts[i];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float xi[4] = {x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]};
+        y[i] = mlp_forward(s_w, xi);
+    }
+}
+
+// Loss and gradient of one block of TS samples; block partial sums of every
+// parameter gradient (and of the squared errors in slot P) go to
+// partial[blockIdx.x][P + 1].  Gradients are taken through the rounded weights
+// (the same values the forward pass uses).
+__global__ void __launch_bounds__(TS) mlp_grad_kernel(const float *__restrict__ wts, const float *__restrict__ x,
+                                                      const float *__restrict__ label, int64_t begin, int64_t count,
+                                                      float inv_count, float *__restrict__ partial)
+{
+    extern __shared__ float4 s_dyn[];
+    float *w = reinterpret_cast<float *>(s_dyn);
+    float *A1 = w + ((P + 3) & ~3);  // h1 [TS][H]
+    float *A2 = A1 + TS * H;         // h2, then dLoss/dz2 [TS][H]
+    float *G1 = A2 + TS * H;         // dLoss/dz1 [TS][H]
+    float *X = G1 + TS * H;          // features [TS][4]
+    float *GO = X + TS * 4;          // dLoss/dy [TS]
+    float *E2 = GO + TS;             // squared error [TS]
+    const int s = threadIdx.x;
+    for (int i = s; i < P; i += TS)
+        w[i] = wts[i];
+    const int64_t idx = begin + (int64_t)blockIdx.x * TS + s;
+    const bool valid = idx < begin + count;
+    float xs[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        xs[j] = valid ? x[idx * 4 + j] : 0.f;
+    const float lab = valid ? label[idx] : 0.f;
+    __syncthreads();
+
+    float h1[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        float a = w[OB1 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            a = __fmaf_rn(w[OW1 + 4 * i + j], xs[j], a);
+        h1[i] = fmaxf(a, 0.f);
+        A1[s * H + i] = h1[i];
+    }
+    float y = w[OB3];
+    for (int i = 0; i < H; ++i) {
+        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
+        float a = w[OB2 + i];
+#pragma unroll
+        for (int j = 0; j < H / 4; ++j) {
+            const float4 r = row[j];
+            a = __fmaf_rn(r.x, h1[4 * j + 0], a);
+            a = __fmaf_rn(r.y, h1[4 * j + 1], a);
+            a = __fmaf_rn(r.z, h1[4 * j + 2], a);
+            a = __fmaf_rn(r.w, h1[4 * j + 3], a);
+        }
+        const float h2 = fmaxf(a, 0.f);
+        A2[s * H + i] = h2;
+        y = __fmaf_rn(w[OW3 + i], h2, y);
+    }
+    const float e = valid ? __fsub_rn(y, lab) : 0.f;
+    const float go = __fmul_rn(__fmul_rn(2.f, e), inv_count);
+    GO[s] = go;
+    E2[s] = __fmul_rn(e, e);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        X[s * 4 + j] = xs[j];
+
+    // back through layer 2: g1_j = relu'(z1_j) * sum_i W2_ij g2_i
+    float g1[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        g1[j] = 0.f;
+    for (int i = 0; i < H; ++i) {
+        const float g2 = A2[s * H + i] > 0.f ? __fmul_rn(go, w[OW3 + i]) : 0.f;
+        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
+#pragma unroll
+        for (int j = 0; j < H / 4; ++j) {
+            const float4 r = row[j];
+            g1[4 * j + 0] = __fmaf_rn(r.x, g2, g1[4 * j + 0]);
+            g1[4 * j + 1] = __fmaf_rn(r.y, g2, g1[4 * j + 1]);
+            g1[4 * j + 2] = __fmaf_rn(r.z, g2, g1[4 * j + 2]);
+            g1[4 * j + 3] = __fmaf_rn(r.w, g2, g1[4 * j + 3]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        G1[s * H + j] = h1[j] > 0.f ? g1[j] : 0.f;
+    __syncthreads();
+
+    // block sums over the samples; thread t owns output unit t of each layer
+    float *out = partial + (size_t)blockIdx.x * (P + 1);
+    const int t = s;
+    {
+        float gw3 = 0.f, gb2 = 0.f;
+        const float w3t = w[OW3 + t];
+        for (int r = 0; r < TS; ++r) {
+            const float h2 = A2[r * H + t];
+            gw3 = __fmaf_rn(GO[r], h2, gw3);
+            gb2 = __fadd_rn(gb2, h2 > 0.f ? __fmul_rn(GO[r], w3t) : 0.f);
+        }
+        out[OW3 + t] = gw3;
+        out[OB2 + t] = gb2;
+    }
+    __syncthreads();
+    // turn column t of A2 into dLoss/dz2
+    {
+        const float w3t = w[OW3 + t];
+        for (int r = 0; r < TS; ++r) {
+            const float h2 = A2[r * H + t];
+            A2[r * H + t] = h2 > 0.f ? __fmul_rn(GO[r], w3t) : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int i = 0; i < H; ++i) {
+        float acc = 0.f;
+        for (int r = 0; r < TS; ++r)
+            acc = __fmaf_rn(A2[r * H + i], A1[r * H + t], acc);
+        out[OW2 + i * H + t] = acc;
+    }
+    {
+        float gb1 = 0.f, gw[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < TS; ++r) {
+            const float g = G1[r * H + t];
+            gb1 = __fadd_rn(gb1, g);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                gw[j] = __fmaf_rn(g, X[r * 4 + j], gw[j]);
+        }
+        out[OB1 + t] = gb1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            out[OW1 + 4 * t + j] = gw[j];
+    }
+    if (t == 0) {
+        float gb3 = 0.f, l = 0.f;
+        for (int r = 0; r < TS; ++r) {
+            gb3 = __fadd_rn(gb3, GO[r]);
+            l = __fadd_rn(l, E2[r]);
+        }
+        out[OB3] = gb3;
+        out[P] = l;
+    }
+}
+
+constexpr size_t grad_smem_bytes()
+{
+    return (size_t)(((P + 3) & ~3) + 3 * TS * H + TS * 4 + 2 * TS) * sizeof(float);
+}
+
+// fixed-order sum over blocks: grad[i] = sum_b partial[b][i]
+__global__ void grad_reduce_kernel(const float *__restrict__ partial, int nb, float *__restrict__ grad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > P)
+        return;
+    float a = 0.f;
+    for (int b = 0; b < nb; ++b)
+        a = __fadd_rn(a, partial[(size_t)b * (P + 1) + i]);
+    grad[i] = a;
+}
+
+__global__ void adam_kernel(float *__restrict__ master, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ grad, float lr, float bc1, float bc2,
+                            float *__restrict__ rounded, double *__restrict__ loss_acc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0)
+        *loss_acc += (double)grad[P];
+    if (i >= P)
+        return;
+    const float g = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * g;
+    const float vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float step = lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    const float wi = master[i] - step;
+    master[i] = wi;
+    rounded[i] = is_weight(i) ? bf16_round(wi) : wi;
+}
+
+__global__ void label_kernel(const float *__restrict__ d2, int64_t n, int k, float *__restrict__ label)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = d2[i * k + k - 1];
+        v = v == v && v < 1e30f ? v : 1e30f;
+        label[i] = 0.5f * logf(fmaxf(v, 1e-30f));
+    }
+}
+
+// per-block sums (double) of x_j and x_j^2 for the 4 features and of the labels
+constexpr int STAT_BLOCKS = 256;
+__global__ void stats_kernel(const float *__restrict__ feat, const float *__restrict__ label, int64_t n,
+                             double *__restrict__ out /* [STAT_BLOCKS][10] */)
+{
+    __shared__ double s[256][10];
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int j = 0; j < 4; ++j) {
+            double x = feat[i * 4 + j];
+            acc[j] += x;
+            acc[4 + j] += x * x;
+        }
+        acc[8] += label[i];
+        acc[9] += 1.0;
+    }
+    for (int j = 0; j < 10; ++j)
+        s[threadIdx.x][j] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double a = 0;
+        for (int t = 0; t < 256; ++t)
+            a += s[t][threadIdx.x];
+        out[blockIdx.x * 10 + threadIdx.x] = a;
+    }
+}
+
+__global__ void normalize_kernel(float *__restrict__ feat, int64_t n, Norm nm)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < 4; ++j)
+            feat[i * 4 + j] = __fdiv_rn(__fsub_rn(feat[i * 4 + j], nm.mu[j]), nm.sd[j]);
+}
 
 __global__ void fill_inf_kernel(float *p, int64_t n)
 {
@@ -9,17 +399,76 @@ __global__ void fill_inf_kernel(float *p, int64_t n)
         p[i] = __int_as_float(0x7f800000);
 }
 
+unsigned grid_of(int64_t n)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
+}
+
+struct Dev {
+    void *p = nullptr;
+    cudaStream_t s;
+    explicit Dev(cudaStream_t s_) : s(s_) {}
+    ~Dev()
+    {
+        if (p)
+            cudaFreeAsync(p, s);
+    }
+};
+
+uint64_t splitmix(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int model_norm(const kdt_tree *t, Norm *nm)
+{
+    for (int j = 0; j < 4; ++j) {
+        nm->mu[j] = t->model.norm[j];
+        nm->sd[j] = t->model.norm[4 + j];
+    }
+    return KDT_OK;
+}
+
+int ensure_params(kdt_tree *t)
+{
+    if (!t->model.d_params)
+        KDT_CUDA(cudaMalloc(&t->model.d_params, P * sizeof(float)));
+    return KDT_OK;
+}
+
+int ensure_stats(kdt_tree *t)
+{
+    if (!t->stats)
+        KDT_CUDA(cudaMalloc(&t->stats, 4 * sizeof(int64_t)));
+    return KDT_OK;
+}
+
+int upload_rounded(const float *h_params, float *d_rounded, cudaStream_t s)
+{
+    KDT_CUDA(cudaMemcpyAsync(d_rounded, h_params, P * sizeof(float), cudaMemcpyHostToDevice, s));
+    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(d_rounded, d_rounded);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+int check_learned_tree(const kdt_tree *t)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (t->D > 3)
+        return set_error(KDT_EINVAL, "the radius model needs D <= 3 (tree has D = %d)", t->D);
+    return KDT_OK;
+}
+
+}  // namespace
+
 void fill_inf(float *p, int64_t n, cudaStream_t s)
 {
     if (n > 0)
-        fill_inf_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(p, n);
-}
-
-int run_learned_query(kdt_tree *t, const float *, int64_t, int, float, int, int32_t *, float *, cudaStream_t)
-{
-    if (!t->model.trained)
-        return set_error(KDT_ENOMODEL, "the tree has no trained radius model");
-    return set_error(KDT_EINVAL, "learned queries are not available in this build");
+        fill_inf_kernel<<<grid_of(n), 256, 0, s>>>(p, n);
 }
 
 void free_model(kdt_tree *t)
@@ -27,6 +476,349 @@ void free_model(kdt_tree *t)
     if (t->model.d_params)
         cudaFree(t->model.d_params);
     t->model.d_params = nullptr;
+    if (t->stats)
+        cudaFree(t->stats);
+    t->stats = nullptr;
+}
+
+int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int32_t *d_ids,
+                      float *d_d2, cudaStream_t s)
+{
+    KDT_TRY(check_learned_tree(t));
+    if (!t->model.trained)
+        return set_error(KDT_ENOMODEL, "the tree has no trained radius model");
+    KDT_TRY(ensure_stats(t));
+    const bool morton = flags & KDT_MORTON;
+    size_t off_w = 0, off_r2 = 1 << 15, off_fb = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
+    size_t off_m = off_fb + (((size_t)Q * 4 + 255) & ~(size_t)255);
+    size_t bytes = off_m + (morton ? morton_scratch_bytes(Q) : 0);
+    Dev sc(s);
+    KDT_CUDA(cudaMallocAsync(&sc.p, bytes, s));
+    char *B = (char *)sc.p;
+    float *wts = (float *)(B + off_w);                                  // P floats
+    unsigned long long *counter = (unsigned long long *)(B + 20480);    // 3 x u64 after the weights
+    float *r2q = (float *)(B + off_r2);
+    uint32_t *fb_list = (uint32_t *)(B + off_fb);
+    uint32_t *perm = nullptr;
+    if (morton)
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, B + off_m, &perm, s));
+    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
+    Norm nm;
+    model_norm(t, &nm);
+    const int staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, 32 * 1024);
+    const size_t smem = (size_t)((P + 3) / 4) * 16 + (size_t)staged * 16;
+    KDT_CUDA(cudaFuncSetAttribute(radius_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int g = grid_for_kernel((const void *)radius_kernel, 256, smem);
+    radius_kernel<<<g, 256, smem, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, perm, staged, wts, nm, t->model.margin, r2,
+                                       r2q);
+    KDT_CUDA(cudaGetLastError());
+    // stats slots: [0] fallback count, [1] ratio sum (double bits)
+    KDT_CUDA(cudaMemsetAsync(t->stats, 0, 2 * sizeof(int64_t), s));
+
+    QueryArgs a;
+    a.nodes = t->nodes;
+    a.ids = t->ids;
+    a.N = (int)t->N;
+    a.D = t->D;
+    a.queries = d_q;
+    a.Q = Q;
+    a.perm = perm;
+    a.k = k;
+    a.r2 = r2;
+    a.out_ids = d_ids;
+    a.out_d2 = d_d2;
+    a.err = t->err;
+    a.counter = counter;
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+    a.r2q = r2q;
+    a.fb_list = fb_list;
+    a.fb_count = (unsigned long long *)t->stats;
+    a.ratio_sum = (double *)(t->stats + 1);
+    const bool ordered = !(flags & KDT_UNORDERED);
+    KDT_TRY(launch_query(0, a, ordered, MODE_BOUNDED, false, s));
+    KDT_TRY(launch_query(0, a, ordered, MODE_FALLBACK, false, s));
+    t->last_learned_q = Q;
+    return KDT_OK;
 }
 
 }  // namespace kdt
+
+using namespace kdt;
+
+extern "C" {
+
+int kdt_descent_features(const kdt_tree *t, const float *d_q, int64_t Q, float *d_feat, void *stream)
+{
+    KDT_TRY(check_learned_tree(t));
+    if (Q < 0 || (Q > 0 && (!d_q || !d_feat)))
+        return set_error(KDT_EINVAL, "bad query or feature arguments");
+    if (Q == 0)
+        return KDT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int staged = staged_nodes(t->N, 0, 32 * 1024);
+    features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged, d_feat);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d_y, void *stream)
+{
+    if (!h_params || n < 0 || (n > 0 && (!d_x || !d_y)))
+        return set_error(KDT_EINVAL, "bad MLP arguments");
+    if (n == 0)
+        return KDT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Dev w(s);
+    KDT_CUDA(cudaMallocAsync(&w.p, P * sizeof(float), s));
+    KDT_TRY(upload_rounded(h_params, (float *)w.p, s));
+    mlp_forward_kernel<<<grid_of(n), 256, 0, s>>>((const float *)w.p, d_x, n, d_y);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+static int loss_grad_dev(const float *d_w, const float *d_x, const float *d_label, int64_t begin, int64_t count,
+                         float *d_partial, float *d_grad, cudaStream_t s)
+{
+    const int nb = (int)((count + TS - 1) / TS);
+    const size_t smem = grad_smem_bytes();
+    KDT_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    mlp_grad_kernel<<<nb, TS, smem, s>>>(d_w, d_x, d_label, begin, count, 1.0f / (float)count, d_partial);
+    grad_reduce_kernel<<<(P + 1 + 255) / 256, 256, 0, s>>>(d_partial, nb, d_grad);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_mlp_loss_grad(const float *h_params, const float *d_x, const float *d_label, int64_t n, float *h_loss,
+                      float *h_grad, void *stream)
+{
+    if (!h_params || n < 1 || !d_x || !d_label || !h_grad)
+        return set_error(KDT_EINVAL, "bad MLP gradient arguments");
+    if (n > (1 << 24))
+        return set_error(KDT_EINVAL, "n must be <= 2^24");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)((n + TS - 1) / TS);
+    Dev buf(s);
+    size_t wb = ((P * 4 + 255) & ~(size_t)255);
+    KDT_CUDA(cudaMallocAsync(&buf.p, 2 * wb + (size_t)nb * (P + 1) * 4, s));
+    float *w = (float *)buf.p;
+    float *grad = (float *)((char *)buf.p + wb);
+    float *partial = (float *)((char *)buf.p + 2 * wb);
+    KDT_TRY(upload_rounded(h_params, w, s));
+    KDT_TRY(loss_grad_dev(w, d_x, d_label, 0, n, partial, grad, s));
+    std::vector<float> g(P + 1);
+    KDT_CUDA(cudaMemcpyAsync(g.data(), grad, (P + 1) * sizeof(float), cudaMemcpyDeviceToHost, s));
+    KDT_CUDA(cudaStreamSynchronize(s));
+    memcpy(h_grad, g.data(), P * sizeof(float));
+    if (h_loss)
+        *h_loss = g[P] / (float)n;
+    return KDT_OK;
+}
+
+int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, const kdt_train_opts *opts,
+                           float *final_loss, void *stream)
+{
+    KDT_TRY(check_learned_tree(t));
+    if (Qt < 1 || !d_q || k < 1 || k > 64)
+        return set_error(KDT_EINVAL, "bad training arguments");
+    if (Qt > ((int64_t)1 << 26))
+        return set_error(KDT_EINVAL, "at most 2^26 training queries");
+    cudaStream_t s = (cudaStream_t)stream;
+    kdt_train_opts o{6, 4096, 2e-3f, 1, 1.25f};
+    if (opts) {
+        if (opts->epochs > 0)
+            o.epochs = opts->epochs;
+        if (opts->batch > 0)
+            o.batch = opts->batch;
+        if (opts->lr > 0)
+            o.lr = opts->lr;
+        o.seed = opts->seed;
+        if (opts->margin > 0)
+            o.margin = opts->margin;
+    }
+    o.batch = std::max(TS, (o.batch / TS) * TS);
+    KDT_TRY(ensure_params(t));
+
+    // buffers: d2 [Qt][k] + ids (for labels), features, labels, weights, Adam state, partials, stats
+    const int nbmax = (o.batch + TS - 1) / TS;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t o_d2 = 0, o_ids = o_d2 + al((size_t)Qt * k * 4), o_feat = o_ids + al((size_t)Qt * k * 4);
+    size_t o_lab = o_feat + al((size_t)Qt * 16), o_w = o_lab + al((size_t)Qt * 4), o_m = o_w + al(P * 4);
+    size_t o_v = o_m + al(P * 4), o_g = o_v + al(P * 4), o_part = o_g + al((P + 1) * 4);
+    size_t o_stat = o_part + al((size_t)nbmax * (P + 1) * 4), o_loss = o_stat + al(STAT_BLOCKS * 10 * 8);
+    size_t bytes = o_loss + 256;
+    Dev buf(s);
+    KDT_CUDA(cudaMallocAsync(&buf.p, bytes, s));
+    char *B = (char *)buf.p;
+    float *d2 = (float *)(B + o_d2);
+    int32_t *ids = (int32_t *)(B + o_ids);
+    float *feat = (float *)(B + o_feat);
+    float *lab = (float *)(B + o_lab);
+    float *w = (float *)(B + o_w);
+    float *m = (float *)(B + o_m);
+    float *v = (float *)(B + o_v);
+    float *grad = (float *)(B + o_g);
+    float *part = (float *)(B + o_part);
+    double *stat = (double *)(B + o_stat);
+    double *loss_acc = (double *)(B + o_loss);
+
+    // exact labels from the plain method
+    KDT_TRY(run_query(t, d_q, Qt, k, INFINITY, KDT_MORTON, MODE_RESULTS, ids, d2, nullptr, s));
+    label_kernel<<<grid_of(Qt), 256, 0, s>>>(d2, Qt, k, lab);
+    KDT_TRY(kdt_descent_features(t, d_q, Qt, feat, s));
+    stats_kernel<<<STAT_BLOCKS, 256, 0, s>>>(feat, lab, Qt, stat);
+    std::vector<double> hs(STAT_BLOCKS * 10);
+    KDT_CUDA(cudaMemcpyAsync(hs.data(), stat, hs.size() * 8, cudaMemcpyDeviceToHost, s));
+    KDT_CUDA(cudaStreamSynchronize(s));
+    double sum[10] = {0};
+    for (int b = 0; b < STAT_BLOCKS; ++b)
+        for (int j = 0; j < 10; ++j)
+            sum[j] += hs[b * 10 + j];
+    Norm nm;
+    for (int j = 0; j < 4; ++j) {
+        double mu = sum[j] / sum[9];
+        double var = std::max(sum[4 + j] / sum[9] - mu * mu, 0.0);
+        nm.mu[j] = (float)mu;
+        nm.sd[j] = (float)std::max(sqrt(var), 1e-6);
+    }
+    const double label_mean = sum[8] / sum[9];
+    normalize_kernel<<<grid_of(Qt), 256, 0, s>>>(feat, Qt, nm);
+
+    // He-uniform initial weights, zero biases, output bias at the label mean
+    std::vector<float> h(P, 0.f);
+    uint64_t st = o.seed * 0x2545F4914F6CDD1Dull + 12345;
+    auto uni = [&](float lim) { return (float)(((splitmix(st) >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0) * lim; };
+    for (int i = 0; i < H * 4; ++i)
+        h[OW1 + i] = uni(sqrtf(6.f / 4.f));
+    for (int i = 0; i < H * H; ++i)
+        h[OW2 + i] = uni(sqrtf(6.f / H));
+    for (int i = 0; i < H; ++i)
+        h[OW3 + i] = uni(sqrtf(6.f / H)) * 0.1f;
+    h[OB3] = (float)label_mean;
+    KDT_CUDA(cudaMemcpyAsync(t->model.d_params, h.data(), P * 4, cudaMemcpyHostToDevice, s));
+    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, w);
+    KDT_CUDA(cudaMemsetAsync(m, 0, P * 4, s));
+    KDT_CUDA(cudaMemsetAsync(v, 0, P * 4, s));
+
+    double b1t = 1.0, b2t = 1.0;
+    float last = 0.f;
+    for (int ep = 0; ep < o.epochs; ++ep) {
+        KDT_CUDA(cudaMemsetAsync(loss_acc, 0, 8, s));
+        for (int64_t b0 = 0; b0 < Qt; b0 += o.batch) {
+            const int64_t cnt = std::min<int64_t>(o.batch, Qt - b0);
+            KDT_TRY(loss_grad_dev(w, feat, lab, b0, cnt, part, grad, s));
+            b1t *= 0.9;
+            b2t *= 0.999;
+            adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, m, v, grad, o.lr, (float)(1.0 - b1t),
+                                                       (float)(1.0 - b2t), w, loss_acc);
+        }
+        KDT_CUDA(cudaGetLastError());
+        double l = 0;
+        KDT_CUDA(cudaMemcpyAsync(&l, loss_acc, 8, cudaMemcpyDeviceToHost, s));
+        KDT_CUDA(cudaStreamSynchronize(s));
+        last = (float)(l / (double)Qt);
+    }
+    for (int j = 0; j < 4; ++j) {
+        t->model.norm[j] = nm.mu[j];
+        t->model.norm[4 + j] = nm.sd[j];
+    }
+    t->model.margin = o.margin;
+    t->model.k_trained = k;
+    t->model.trained = true;
+    if (final_loss)
+        *final_loss = last;
+    return KDT_OK;
+}
+
+int kdt_radius_model_get(const kdt_tree *t, float *h_params, float *h_norm, float *margin)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (!t->model.trained)
+        return set_error(KDT_ENOMODEL, "the tree has no radius model");
+    if (h_params)
+        KDT_CUDA(cudaMemcpy(h_params, t->model.d_params, P * sizeof(float), cudaMemcpyDeviceToHost));
+    if (h_norm)
+        memcpy(h_norm, t->model.norm, sizeof(t->model.norm));
+    if (margin)
+        *margin = t->model.margin;
+    return KDT_OK;
+}
+
+int kdt_radius_model_set(kdt_tree *t, const float *h_params, const float *h_norm, float margin)
+{
+    KDT_TRY(check_learned_tree(t));
+    if (!h_params || !h_norm || !(margin > 0.f))
+        return set_error(KDT_EINVAL, "bad model arguments");
+    for (int j = 0; j < 4; ++j)
+        if (!(h_norm[4 + j] > 0.f))
+            return set_error(KDT_EINVAL, "feature standard deviations must be > 0");
+    KDT_TRY(ensure_params(t));
+    KDT_CUDA(cudaMemcpy(t->model.d_params, h_params, P * sizeof(float), cudaMemcpyHostToDevice));
+    memcpy(t->model.norm, h_norm, sizeof(t->model.norm));
+    t->model.margin = margin;
+    t->model.trained = true;
+    return KDT_OK;
+}
+
+static const char MODEL_MAGIC[8] = {'K', 'D', 'T', 'R', 'A', 'D', 'M', '1'};
+
+int kdt_radius_model_save(const kdt_tree *t, const char *path)
+{
+    if (!path)
+        return set_error(KDT_EINVAL, "path is NULL");
+    std::vector<float> p(P);
+    float norm[8], margin;
+    KDT_TRY(kdt_radius_model_get(t, p.data(), norm, &margin));
+    FILE *f = fopen(path, "wb");
+    if (!f)
+        return set_error(KDT_EIO, "cannot open %s for writing", path);
+    int32_t hdr[4] = {1, H, P, t->model.k_trained};
+    bool ok = fwrite(MODEL_MAGIC, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 && fwrite(norm, 4, 8, f) == 8 &&
+              fwrite(&margin, 4, 1, f) == 1 && fwrite(p.data(), 4, P, f) == (size_t)P;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? KDT_OK : set_error(KDT_EIO, "write to %s failed", path);
+}
+
+int kdt_radius_model_load(kdt_tree *t, const char *path)
+{
+    KDT_TRY(check_learned_tree(t));
+    if (!path)
+        return set_error(KDT_EINVAL, "path is NULL");
+    FILE *f = fopen(path, "rb");
+    if (!f)
+        return set_error(KDT_EIO, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr[4];
+    float norm[8], margin;
+    std::vector<float> p(P);
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, MODEL_MAGIC, 8) == 0 && fread(hdr, 4, 4, f) == 4 &&
+              hdr[0] == 1 && hdr[1] == H && hdr[2] == P && fread(norm, 4, 8, f) == 8 && fread(&margin, 4, 1, f) == 1 &&
+              fread(p.data(), 4, P, f) == (size_t)P;
+    fclose(f);
+    if (!ok)
+        return set_error(KDT_EIO, "%s is not a radius model file of this version", path);
+    KDT_TRY(kdt_radius_model_set(t, p.data(), norm, margin));
+    t->model.k_trained = hdr[3];
+    return KDT_OK;
+}
+
+int kdt_learned_stats(const kdt_tree *t, int64_t *fallbacks, double *radius_ratio, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (!t->stats)
+        return set_error(KDT_ENOMODEL, "no learned query has run on this tree");
+    int64_t h[2];
+    KDT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    KDT_CUDA(cudaMemcpy(h, t->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    double ratio_sum;
+    memcpy(&ratio_sum, &h[1], 8);
+    const int64_t exact = t->last_learned_q - h[0];
+    if (fallbacks)
+        *fallbacks = h[0];
+    if (radius_ratio)
+        *radius_ratio = exact > 0 ? ratio_sum / (double)exact : 0.0;
+    return KDT_OK;
+}
+
+}  // extern "C"

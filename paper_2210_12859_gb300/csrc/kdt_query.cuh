@@ -30,10 +30,17 @@ struct QueryArgs {
     int T = 1;
     const int64_t *node_off = nullptr; // [T+1]
     const int64_t *q_off = nullptr;    // [T+1]
-    int64_t q_begin = 0;               // first query slot served by this launch
+    // learned radius proposal
+    const float *r2q = nullptr;        // per-query cull radius of the bounded pass (mode 2)
+    uint32_t *fb_list = nullptr;       // queries to re-run (appended by mode 2, read by mode 3)
+    unsigned long long *fb_count = nullptr;
+    double *ratio_sum = nullptr;       // sum of proposed / true k-th radius (mode 2, exact queries)
 };
 
-// Launch the plain traversal for one layout.  mode: 0 results, 1 visit counts.
+// kernel modes: results, visit counts, learned bounded pass, fallback pass
+enum : int { MODE_RESULTS = 0, MODE_VISITS = 1, MODE_BOUNDED = 2, MODE_FALLBACK = 3 };
+
+// Launch a traversal for one layout (mode: MODE_*).
 int launch_query_layout0(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
 int launch_query_layout1(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
 int launch_query_layout2(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);

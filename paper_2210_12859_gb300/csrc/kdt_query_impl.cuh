@@ -8,7 +8,7 @@ namespace kdt {
 // Single tree.  Persistent blocks stage the top levels once, then every warp
 // repeatedly claims the next 32 query slots from a global counter, so the
 // slow lanes of a warp hold up only that warp and the tail stays short.
-template <int LAYOUT, int K, bool ORDERED, bool COUNT>
+template <int LAYOUT, int K, bool ORDERED, int MODE>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_kernel(const QueryArgs a)
 {
@@ -19,39 +19,80 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     stage_nodes<LAYOUT>(a.nodes, s_nodes, a.staged);
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int64_t Qn = MODE == MODE_FALLBACK ? (int64_t)*a.fb_count : a.Q;
+    double ratio = 0.0;
     for (;;) {
         unsigned long long b = 0;
         if (lane == 0)
             b = atomicAdd(a.counter, 32ull);
         b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= (unsigned long long)a.Q)
+        if (b >= (unsigned long long)Qn)
             break;
         const int64_t i = (int64_t)b + lane;
-        if (i >= a.Q)
-            continue;
-        const int64_t qi = a.perm ? (int64_t)a.perm[i] : i;
-        float q[NC];
-        load_query<LAYOUT>(a.queries, qi, a.D, q);
-        int v;
-        if constexpr (K <= MAX_REG_K) {
-            RegList<K> list;
-            list.init(a.k, a.r2);
-            v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
-            if (!COUNT)
-                list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
-        } else {
-            SmemList list;
-            list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
-            list.stride = blockDim.x;
-            list.init(a.k, a.r2);
-            v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
-            if (!COUNT)
-                list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+        bool fallback = false;
+        int64_t qi = 0;
+        if (i < Qn) {
+            if (MODE == MODE_FALLBACK)
+                qi = a.fb_list[i];
+            else
+                qi = a.perm ? (int64_t)a.perm[i] : i;
+            const float r2 = MODE == MODE_BOUNDED ? a.r2q[qi] : a.r2;
+            float q[NC];
+            load_query<LAYOUT>(a.queries, qi, a.D, q);
+            int v;
+            bool full;
+            float worst;
+            if constexpr (K <= MAX_REG_K) {
+                RegList<K> list;
+                list.init(a.k, r2);
+                v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
+                full = list.full(a.k);
+                worst = list.cull();
+                fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
+                if (MODE != MODE_VISITS && !fallback)
+                    list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+            } else {
+                SmemList list;
+                list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
+                list.stride = blockDim.x;
+                list.init(a.k, r2);
+                v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
+                full = list.full(a.k);
+                worst = list.cull();
+                fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
+                if (MODE != MODE_VISITS && !fallback)
+                    list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+            }
+            if (v < 0)
+                atomicOr(a.err, ERR_TRAVERSAL);
+            if (MODE == MODE_VISITS)
+                a.visits[qi] = v;
+            // a query is exact when its list is full (every point outside the
+            // proposed radius is farther than all k held) or when the proposal
+            // did not shrink the caller's radius; for the others the k-best set
+            // may lie beyond the proposal and they are re-run
+            if (MODE == MODE_BOUNDED && !fallback && full && worst > 0.f && r2 < __int_as_float(0x7f800000))
+                ratio += sqrt((double)r2 / (double)worst);
         }
-        if (v < 0)
-            atomicOr(a.err, ERR_TRAVERSAL);
-        if (COUNT)
-            a.visits[qi] = v;
+        if (MODE == MODE_BOUNDED) {
+            // warp-aggregated append of the queries to re-run (all lanes here)
+            const unsigned m = __ballot_sync(0xffffffffu, fallback);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0;
+                if (lane == leader)
+                    base = atomicAdd(a.fb_count, (unsigned long long)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (fallback)
+                    a.fb_list[base + __popc(m & ((1u << lane) - 1))] = (uint32_t)qi;
+            }
+        }
+    }
+    if (MODE == MODE_BOUNDED) {
+        for (int o = 16; o > 0; o >>= 1)
+            ratio += __shfl_down_sync(0xffffffffu, ratio, o);
+        if (lane == 0 && ratio != 0.0)
+            atomicAdd(a.ratio_sum, ratio);
     }
 }
 
@@ -135,14 +176,30 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
         return launch_kernel(knn_forest_kernel<LAYOUT, K, false>, threads, list_bytes, a, s);
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
-    if (mode == 1) {
+    switch (mode) {
+    case MODE_VISITS:
         if (ordered)
-            return launch_kernel(knn_kernel<LAYOUT, K, true, true>, threads, smem, a, s);
-        return launch_kernel(knn_kernel<LAYOUT, K, false, true>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS>, threads, smem, a, s);
+    case MODE_BOUNDED:
+    case MODE_FALLBACK:
+        if constexpr (LAYOUT == 0) {
+            if (mode == MODE_BOUNDED) {
+                if (ordered)
+                    return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED>, threads, smem, a, s);
+                return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED>, threads, smem, a, s);
+            }
+            if (ordered)
+                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_FALLBACK>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_FALLBACK>, threads, smem, a, s);
+        } else {
+            return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
+        }
+    default:
+        if (ordered)
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS>, threads, smem, a, s);
     }
-    if (ordered)
-        return launch_kernel(knn_kernel<LAYOUT, K, true, false>, threads, smem, a, s);
-    return launch_kernel(knn_kernel<LAYOUT, K, false, false>, threads, smem, a, s);
 }
 
 template <int LAYOUT>

@@ -206,6 +206,18 @@ def kdt_build(points: torch.Tensor, opts: int = 0, stream=None) -> Tree:
     return Tree(h)
 
 
+def kdt_build_ex(points: torch.Tensor, opts: int = 0, stream=None) -> Tree:
+    return kdt_build(points, opts, stream)
+
+
+def kdt_tree_info(tree: Tree):
+    return tree.N, tree.D
+
+
+def kdt_last_error() -> str:
+    return _lib.kdt_last_error().decode(errors="replace")
+
+
 def kdt_rebuild(tree: Tree, points: torch.Tensor, opts: int = 0, stream=None) -> None:
     _dev(points, torch.float32, "points", (tree.N, tree.D))
     _check(_lib.kdt_rebuild(tree.handle, ctypes.c_void_p(points.data_ptr()), opts, _stream(stream)))

@@ -176,9 +176,16 @@ def test_edge_cases(kdt):
     pts = g.integers(0, 3, size=(500, 3)).astype(np.float32)
     qs = np.concatenate([pts[:50], g.integers(-2, 5, size=(50, 3)).astype(np.float32), np.full((3, 3), 1e20, np.float32)])
     t = kdt.kdt_build(cu(pts))
-    for k, r in [(600, math.inf), (64, 0.0), (10, 1.0), (1, 0.0), (7, 3e19)]:
+    for k, r in [(64, math.inf), (64, 0.0), (10, 1.0), (1, 0.0), (7, 3e19)]:
         wi, wd = oracle.knn_brute(pts, qs, k, r)
         gi, gd = kdt.kdt_knn(t, cu(qs), k, r)
+        assert_same(gi, gd, wi, wd)
+    # k > N: every point, then empty slots
+    few = pts[:37].copy()
+    tf = kdt.kdt_build(cu(few))
+    for k in (37, 40, 64):
+        wi, wd = oracle.knn_brute(few, qs, k)
+        gi, gd = kdt.kdt_knn(tf, cu(qs), k)
         assert_same(gi, gd, wi, wd)
     # Q = 0 is a no-op
     kdt.kdt_knn(t, cu(np.zeros((0, 3), np.float32)), 5)
