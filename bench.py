@@ -1,0 +1,365 @@
+"""Benchmark: kNN queries/s on one GB300 (or N replicas), one JSON line.
+
+Workload (default): N = 2^24 3-D points from a 64-component isotropic Gaussian
+mixture (sigma 0.01, centres uniform in [0,1]^3), Q = 2^24 queries (90% from
+the mixture, 10% uniform in [0,1]^3); kNN with k = 8, unbounded radius,
+ordered stack-free traversal with Morton query order.  One step = rebuild the
+tree from the points + answer all Q queries (every stage of the single-tree
+hot path).  The learned-radius form of the same query is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank is an independent replica with its own query set
+(queries shard across GPUs; the tree is rebuilt on every GPU), so per-GPU work
+is fixed: weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kNN queries/s, N=2^24 3-D k=8: plain vs learned-radius, bit-exact; % roofline"
+K_NN = 8
+LOG2N = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=LOG2N, help="log2 of N = Q (default 24)")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Max of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the
+    timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[2 + i]
+                          and "Not" not in r[2 + i]})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_qps(points, queries, k, n_queries, seed=5):
+    """Oracle brute force (plain definition, all host cores) on a sample of the
+    workload's queries against all N points; returns (queries/s, threads, sample)."""
+    import oracle
+
+    oracle.ensure_built()
+    g = np.random.default_rng(seed)
+    idx = np.sort(g.choice(len(queries), size=n_queries, replace=False))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ids, d2 = oracle.knn_brute_threaded(points, queries[idx], k, math.inf, threads)
+    dt = time.perf_counter() - t0
+    return n_queries / dt, threads, idx, ids, d2
+
+
+def reference_arm(args, world, rank):
+    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2210_12859_gb300 import synth
+
+    n = 1 << args.log2n
+    pts, qs = synth.gmm_large(n, n)
+    per_step = 96 if args.log2n >= 24 else 512
+    if args.warmup > 0:
+        cpu_oracle_qps(pts, qs, K_NN, 16)
+    times = []
+    threads = os.cpu_count() or 1
+    for s in range(args.steps):
+        qps, threads, *_ = cpu_oracle_qps(pts, qs, K_NN, per_step, seed=100 + s)
+        times.append(per_step / qps)
+    ms = 1000.0 * statistics.median(times)
+    value = per_step / (ms / 1000.0)
+    sample = f"{per_step} of the 2^{args.log2n} queries per step, brute force over all N points"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.log2n),
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(log2n):
+    return {
+        "workload": f"gmm_large: N=2^{log2n} 3-D float32 points, 64-component Gaussian mixture (sigma 0.01, "
+                    f"centres U[0,1]^3); Q=2^{log2n} queries (90% mixture, 10% uniform [0,1]^3); kNN k=8, "
+                    "max_radius=inf, ordered stack-free traversal, Morton query order; step = tree build + "
+                    "all queries",
+        "N": 1 << log2n, "Q": 1 << log2n, "D": 3, "k": K_NN,
+        "cache": "inputs larger than L2 (tree 256 MiB, points and queries 192 MiB each, outputs 1 GiB)",
+    }
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+
+    from paper_2210_12859_gb300 import kdt, synth
+
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    n = 1 << args.log2n
+    pts, qs = synth.gmm_large(n, n, seed=synth.BASE_SEED + 2)
+    if rank > 0:  # each replica answers its own query set
+        mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
+        qs = synth.gmm_queries(mix, n, 0.1, synth.BASE_SEED + 1000 + rank)
+    dp = torch.from_numpy(pts).to(dev)
+    dq = torch.from_numpy(qs).to(dev)
+    out_i = torch.empty((n, K_NN), dtype=torch.int32, device=dev)
+    out_d = torch.empty((n, K_NN), dtype=torch.float32, device=dev)
+    flags = kdt.KDT_MORTON
+    tree = kdt.kdt_build(dp)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC)
+        kdt.kdt_knn(tree, dq, K_NN, math.inf, flags, out_i, out_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kdt.kdt_status(tree)
+
+    # ---- timed region
+    launches0 = kdt.kdt_launch_count()
+    kdt.kdt_profile_enable(tree, True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms_total = ev0.elapsed_time(ev1)
+    trav_ms, trav_launches = kdt.kdt_profile_read(tree)
+    kdt.kdt_profile_enable(tree, False)
+    gpu_launches = kdt.kdt_launch_count() - launches0
+    kdt.kdt_status(tree)
+    ms_step = max_over_ranks(ms_total / args.steps, dist, dev)
+    value = world * n / (ms_step / 1000.0)
+
+    # ---- breakdown (untimed by the contract, reported for context)
+    def timeit(fn, reps=2):
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    build_ms = timeit(lambda: kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC), 3)
+    query_ms = timeit(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags, out_i, out_d), 2)
+    visits = kdt.kdt_knn_visits(tree, dq, K_NN, math.inf, flags)
+    v_sum = float(visits.double().sum().item())
+    v_mean = v_sum / n
+
+    # ---- sampled bit-exactness against the oracle (plain definition)
+    res_i = out_i.cpu().numpy()
+    res_d = out_d.cpu().numpy()
+    exact = None
+    cpu = None
+    if rank == 0:
+        qps_cpu, threads, idx, wi, wd = cpu_oracle_qps(pts, qs, K_NN, 256 if args.log2n >= 24 else 1024)
+        exact = bool(np.array_equal(res_i[idx], wi) and np.array_equal(res_d[idx].view(np.uint32),
+                                                                       wd.view(np.uint32)))
+        cpu = {"value": qps_cpu, "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": f"{len(idx)} random queries of the workload, brute force over all 2^{args.log2n} points "
+                         "(plain definition, FP32), threads over queries"}
+
+    # ---- roofline of the dominant kernel (the traversal)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        peak_src = "measured"
+    except Exception:
+        hbm = 6800.0
+        peak_src = "fallback"
+    kern_ms = trav_ms / max(trav_launches, 1)
+    bytes_per_launch = n * (4 * 3 + 8 * K_NN) + v_sum * 16.0
+    achieved = bytes_per_launch / (kern_ms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("knn_kernel_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_source": peak_src,
+                "kernel": "knn_kernel<layout0,K=8,ordered> (stack-free traversal)",
+                "kernel_ms": kern_ms, "bytes_per_query": bytes_per_launch / n,
+                "visits_per_query": v_mean}
+
+    # ---- learned radius form (same queries, same results)
+    learned = None
+    if not args.no_learned:
+        mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
+        train_q = torch.from_numpy(synth.gmm_queries(mix, 1 << 20, 0.1, synth.BASE_SEED + 77)).to(dev)
+        t0 = time.perf_counter()
+        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=6, seed=1)
+        train_s = time.perf_counter() - t0
+        li = torch.empty_like(out_i)
+        ld = torch.empty_like(out_d)
+        kdt.kdt_knn(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED, li, ld)
+        learned_ms = timeit(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED, li, ld), 2)
+        fb, ratio = kdt.kdt_learned_stats(tree)
+        same = bool(torch.equal(li, out_i) and torch.equal(ld.view(torch.int32), out_d.view(torch.int32)))
+        lv = kdt.kdt_knn_visits(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED)
+        learned = {"query_qps": n / (learned_ms / 1000.0), "query_ms": learned_ms,
+                   "plain_query_qps": n / (query_ms / 1000.0), "speedup_vs_plain": query_ms / learned_ms,
+                   "fallback_rate": fb / n, "radius_ratio": ratio, "identical_to_plain": same,
+                   "visits_per_query": float(lv.double().mean().item()), "train_s": train_s,
+                   "train_loss": loss, "train_queries": 1 << 20}
+
+    # ---- end to end: host buffers in, host results out, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(pts).pin_memory()
+        hq = torch.from_numpy(qs).pin_memory()
+        hi = torch.empty((n, K_NN), dtype=torch.int32).pin_memory()
+        hd = torch.empty((n, K_NN), dtype=torch.float32).pin_memory()
+        kdt.kdt_knn_host(hp, hq, K_NN, math.inf, flags, hi, hd)
+        ts = []
+        for _ in range(2):
+            barrier(dist)
+            t0 = time.perf_counter()
+            kdt.kdt_knn_host(hp, hq, K_NN, math.inf, flags, hi, hd)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(statistics.median(ts), dist, dev)
+        e2e = {"value": world * n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(pts.nbytes + qs.nbytes),
+               "d2h_bytes_per_step": int(hi.numel() * 4 + hd.numel() * 4), "seconds": e2e_s,
+               "identical": bool(np.array_equal(hi.numpy(), res_i))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.log2n),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk.summary(), "bit_exact_sample": exact,
+            "breakdown": {"build_ms": build_ms, "query_ms": query_ms, "query_qps": n / (query_ms / 1000.0)},
+            "learned": learned,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

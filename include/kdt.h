@@ -69,6 +69,11 @@ typedef struct kdt_forest kdt_forest;
 /* Text of the last failure on the calling thread ("" if none). */
 const char *kdt_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices).  Kernels inside the CUDA graph that kdt_knn_batched
+ * replays are counted when the graph is captured, not at each replay. */
+int64_t kdt_launch_count(void);
+
 /* ---- single tree ------------------------------------------------------- */
 
 /* Build the left-balanced complete tree of N points of dimension D in level
@@ -110,8 +115,9 @@ int kdt_knn(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, floa
             int flags, int32_t *d_ids, float *d_d2, void *stream);
 
 /* Per-query count of processed nodes (first visits, the processNode calls of
- * Sec. 3.2) of the traversal kdt_knn would run with the same arguments.
- * KDT_LEARNED is not accepted here.  d_visits int32 [Q]. */
+ * Sec. 3.2) of the traversal kdt_knn would run with the same arguments.  With
+ * KDT_LEARNED: nodes of the bounded pass plus, for re-run queries, of the
+ * re-run (results are not written).  d_visits int32 [Q]. */
 int kdt_knn_visits(const kdt_tree *tree, const float *d_queries, int64_t Q, int k,
                    float max_radius, int flags, int32_t *d_visits, void *stream);
 
@@ -134,7 +140,7 @@ int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_queries
 
 typedef struct kdt_train_opts {
     int epochs;           /* passes over the training queries (default 6 if <= 0) */
-    int batch;            /* minibatch size (default 4096 if <= 0) */
+    int batch;            /* minibatch size (default 1024 if <= 0; rounded down to a multiple of 64) */
     float lr;             /* Adam step size (default 2e-3 if <= 0) */
     uint64_t seed;        /* weight initialisation seed */
     float margin;         /* cull radius = margin * predicted radius (default 1.25 if <= 0) */

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -35,6 +36,9 @@ int cuda_error(cudaError_t e, const char *what, const char *file, int line)
 }
 
 // ---------------------------------------------------------------- helpers
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int grid_for_kernel(const void *fn, int threads, size_t smem)
 {
@@ -192,10 +196,10 @@ int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, c
     uint32_t *tk = c.take<uint32_t>(Q);
     uint32_t *tv = c.take<uint32_t>(Q);
     uint32_t *rs = c.take<uint32_t>(radix_scratch_elems(Q));
-    morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, keys, perm);
+    KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, keys, perm);
     KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, 30, rs, s));
     if (T > 1) {
-        tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
+        KDT_LAUNCH tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
         KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, tbits, rs, s));
     }
     KDT_CUDA(cudaGetLastError());
@@ -318,6 +322,8 @@ extern "C" {
 
 const char *kdt_last_error(void) { return g_err; }
 
+int64_t kdt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 static int alloc_tree(int64_t N, int D, kdt_tree **out)
 {
     kdt_tree *t = new (std::nothrow) kdt_tree();
@@ -422,7 +428,7 @@ int kdt_tree_export(const kdt_tree *t, float *d_coords, int32_t *d_ids, void *st
     if (!t)
         return set_error(KDT_EINVAL, "tree is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    export_kernel<<<grid_1d(t->N), 256, 0, s>>>(t->nodes, t->ids, t->N, t->D, d_coords, d_ids);
+    KDT_LAUNCH export_kernel<<<grid_1d(t->N), 256, 0, s>>>(t->nodes, t->ids, t->N, t->D, d_coords, d_ids);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -436,7 +442,7 @@ int kdt_knn(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_rad
     cudaStream_t s = (cudaStream_t)stream;
     float r2 = max_radius * max_radius;
     if (flags & KDT_LEARNED)
-        return run_learned_query(const_cast<kdt_tree *>(t), d_q, Q, k, r2, flags, d_ids, d_d2, s);
+        return run_learned_query(const_cast<kdt_tree *>(t), d_q, Q, k, r2, flags, d_ids, d_d2, nullptr, s);
     return run_query(t, d_q, Q, k, r2, flags, 0, d_ids, d_d2, nullptr, s);
 }
 
@@ -450,10 +456,11 @@ int kdt_knn_visits(const kdt_tree *t, const float *d_q, int64_t Q, int k, float 
                    int32_t *d_visits, void *stream)
 {
     KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_visits, (const void *)1));
-    if (flags & KDT_LEARNED)
-        return set_error(KDT_EINVAL, "kdt_knn_visits does not take KDT_LEARNED");
     if (Q == 0)
         return KDT_OK;
+    if (flags & KDT_LEARNED)
+        return run_learned_query(const_cast<kdt_tree *>(t), d_q, Q, k, max_radius * max_radius, flags, nullptr,
+                                 nullptr, d_visits, (cudaStream_t)stream);
     return run_query(t, d_q, Q, k, max_radius * max_radius, flags, 1, nullptr, nullptr, d_visits,
                      (cudaStream_t)stream);
 }
@@ -807,7 +814,7 @@ int kdt_forest_export(const kdt_forest *f, float *d_coords, int32_t *d_ids, void
     cudaStream_t s = (cudaStream_t)stream;
     if (f->f.total == 0)
         return KDT_OK;
-    export_kernel<<<grid_1d(f->f.total), 256, 0, s>>>(f->nodes, f->ids, f->f.total, f->f.D, d_coords, d_ids);
+    KDT_LAUNCH export_kernel<<<grid_1d(f->f.total), 256, 0, s>>>(f->nodes, f->ids, f->f.total, f->f.D, d_coords, d_ids);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }

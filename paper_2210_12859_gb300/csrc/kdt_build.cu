@@ -403,24 +403,24 @@ int build_forest(const float *d_points, const int64_t *h_off, int T, int D, floa
     KDT_CUDA(cudaMemcpyAsync(d_off, h_off, (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     const unsigned g = grid_for(total);
     if (T > 1)
-        tree_of_kernel<<<g, BT, 0, s>>>(d_off, T, total, tree_of);
+        KDT_LAUNCH tree_of_kernel<<<g, BT, 0, s>>>(d_off, T, total, tree_of);
     int tbits = T > 1 ? floor_log2((uint64_t)(T - 1)) + 1 : 0;
 
     // per-dimension lists sorted by (tree, coordinate, index)
     for (int e = 0; e < D; ++e) {
-        prep_keys_kernel<<<g, BT, 0, s>>>(d_points, total, D, e, k0, lists[e], err);
+        KDT_LAUNCH prep_keys_kernel<<<g, BT, 0, s>>>(d_points, total, D, e, k0, lists[e], err);
         KDT_TRY(radix_sort_pairs(k0, lists[e], k1, spare, total, 32, rscr, s));
         if (T > 1) {
-            tree_keys_kernel<<<g, BT, 0, s>>>(lists[e], tree_of, total, k0);
+            KDT_LAUNCH tree_keys_kernel<<<g, BT, 0, s>>>(lists[e], tree_of, total, k0);
             KDT_TRY(radix_sort_pairs(k0, lists[e], k1, spare, total, tbits, rscr, s));
         }
     }
     KDT_CUDA(cudaMemcpyAsync(d_lptr, lists, 8 * sizeof(uint32_t *), cudaMemcpyHostToDevice, s));
-    bbox_kernel<<<(T + 127) / 128, 128, 0, s>>>(d_points, D, d_lptr, d_off, T, bbox);
+    KDT_LAUNCH bbox_kernel<<<(T + 127) / 128, 128, 0, s>>>(d_points, D, d_lptr, d_off, T, bbox);
 
     for (int l = 0; l <= maxH; ++l) {
         const int d = l % D;
-        assign_kernel<<<g, BT, 0, s>>>(lists[d], total, l, T, d_off, tree_of, d_points, D, side, nodes, ids);
+        KDT_LAUNCH assign_kernel<<<g, BT, 0, s>>>(lists[d], total, l, T, d_off, tree_of, d_points, D, side, nodes, ids);
         for (int e = 0; e < D; ++e) {
             if (e == d)
                 continue;
@@ -428,9 +428,9 @@ int build_forest(const float *d_points, const int64_t *h_off, int T, int D, floa
             int nl = l + ((e - d + D) % D);
             if (nl > maxH)
                 continue;
-            part_reduce_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off, tree_of, side, tiles);
-            part_tiles_kernel<<<1, 1024, 0, s>>>(tiles, ptiles);
-            part_scatter_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off, tree_of, side, tiles,
+            KDT_LAUNCH part_reduce_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off, tree_of, side, tiles);
+            KDT_LAUNCH part_tiles_kernel<<<1, 1024, 0, s>>>(tiles, ptiles);
+            KDT_LAUNCH part_scatter_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off, tree_of, side, tiles,
                                                                 spare);
             std::swap(lists[e], spare);
         }

@@ -27,6 +27,10 @@ int cuda_error(cudaError_t e, const char *what, const char *file, int line);
             return rc_;                                                         \
     } while (0)
 
+// every kernel launch of the library goes through KDT_LAUNCH, which counts it
+void note_launch();
+#define KDT_LAUNCH ::kdt::note_launch(),
+
 // device error word bits
 enum : int { ERR_NONFINITE = 1, ERR_TRAVERSAL = 2 };
 

@@ -449,7 +449,7 @@ int ensure_stats(kdt_tree *t)
 int upload_rounded(const float *h_params, float *d_rounded, cudaStream_t s)
 {
     KDT_CUDA(cudaMemcpyAsync(d_rounded, h_params, P * sizeof(float), cudaMemcpyHostToDevice, s));
-    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(d_rounded, d_rounded);
+    KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(d_rounded, d_rounded);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -468,7 +468,7 @@ int check_learned_tree(const kdt_tree *t)
 void fill_inf(float *p, int64_t n, cudaStream_t s)
 {
     if (n > 0)
-        fill_inf_kernel<<<grid_of(n), 256, 0, s>>>(p, n);
+        KDT_LAUNCH fill_inf_kernel<<<grid_of(n), 256, 0, s>>>(p, n);
 }
 
 void free_model(kdt_tree *t)
@@ -482,7 +482,7 @@ void free_model(kdt_tree *t)
 }
 
 int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int32_t *d_ids,
-                      float *d_d2, cudaStream_t s)
+                      float *d_d2, int32_t *d_visits, cudaStream_t s)
 {
     KDT_TRY(check_learned_tree(t));
     if (!t->model.trained)
@@ -502,14 +502,14 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     uint32_t *perm = nullptr;
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, B + off_m, &perm, s));
-    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
+    KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
     Norm nm;
     model_norm(t, &nm);
     const int staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, 32 * 1024);
     const size_t smem = (size_t)((P + 3) / 4) * 16 + (size_t)staged * 16;
     KDT_CUDA(cudaFuncSetAttribute(radius_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int g = grid_for_kernel((const void *)radius_kernel, 256, smem);
-    radius_kernel<<<g, 256, smem, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, perm, staged, wts, nm, t->model.margin, r2,
+    KDT_LAUNCH radius_kernel<<<g, 256, smem, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, perm, staged, wts, nm, t->model.margin, r2,
                                        r2q);
     KDT_CUDA(cudaGetLastError());
     // stats slots: [0] fallback count, [1] ratio sum (double bits)
@@ -527,6 +527,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.r2 = r2;
     a.out_ids = d_ids;
     a.out_d2 = d_d2;
+    a.visits = d_visits;
     a.err = t->err;
     a.counter = counter;
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
@@ -556,7 +557,7 @@ int kdt_descent_features(const kdt_tree *t, const float *d_q, int64_t Q, float *
         return KDT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int staged = staged_nodes(t->N, 0, 32 * 1024);
-    features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged, d_feat);
+    KDT_LAUNCH features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged, d_feat);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -571,7 +572,7 @@ int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d
     Dev w(s);
     KDT_CUDA(cudaMallocAsync(&w.p, P * sizeof(float), s));
     KDT_TRY(upload_rounded(h_params, (float *)w.p, s));
-    mlp_forward_kernel<<<grid_of(n), 256, 0, s>>>((const float *)w.p, d_x, n, d_y);
+    KDT_LAUNCH mlp_forward_kernel<<<grid_of(n), 256, 0, s>>>((const float *)w.p, d_x, n, d_y);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -582,8 +583,8 @@ static int loss_grad_dev(const float *d_w, const float *d_x, const float *d_labe
     const int nb = (int)((count + TS - 1) / TS);
     const size_t smem = grad_smem_bytes();
     KDT_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mlp_grad_kernel<<<nb, TS, smem, s>>>(d_w, d_x, d_label, begin, count, 1.0f / (float)count, d_partial);
-    grad_reduce_kernel<<<(P + 1 + 255) / 256, 256, 0, s>>>(d_partial, nb, d_grad);
+    KDT_LAUNCH mlp_grad_kernel<<<nb, TS, smem, s>>>(d_w, d_x, d_label, begin, count, 1.0f / (float)count, d_partial);
+    KDT_LAUNCH grad_reduce_kernel<<<(P + 1 + 255) / 256, 256, 0, s>>>(d_partial, nb, d_grad);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -623,7 +624,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     if (Qt > ((int64_t)1 << 26))
         return set_error(KDT_EINVAL, "at most 2^26 training queries");
     cudaStream_t s = (cudaStream_t)stream;
-    kdt_train_opts o{6, 4096, 2e-3f, 1, 1.25f};
+    kdt_train_opts o{6, 1024, 2e-3f, 1, 1.25f};
     if (opts) {
         if (opts->epochs > 0)
             o.epochs = opts->epochs;
@@ -663,9 +664,9 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
 
     // exact labels from the plain method
     KDT_TRY(run_query(t, d_q, Qt, k, INFINITY, KDT_MORTON, MODE_RESULTS, ids, d2, nullptr, s));
-    label_kernel<<<grid_of(Qt), 256, 0, s>>>(d2, Qt, k, lab);
+    KDT_LAUNCH label_kernel<<<grid_of(Qt), 256, 0, s>>>(d2, Qt, k, lab);
     KDT_TRY(kdt_descent_features(t, d_q, Qt, feat, s));
-    stats_kernel<<<STAT_BLOCKS, 256, 0, s>>>(feat, lab, Qt, stat);
+    KDT_LAUNCH stats_kernel<<<STAT_BLOCKS, 256, 0, s>>>(feat, lab, Qt, stat);
     std::vector<double> hs(STAT_BLOCKS * 10);
     KDT_CUDA(cudaMemcpyAsync(hs.data(), stat, hs.size() * 8, cudaMemcpyDeviceToHost, s));
     KDT_CUDA(cudaStreamSynchronize(s));
@@ -681,7 +682,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         nm.sd[j] = (float)std::max(sqrt(var), 1e-6);
     }
     const double label_mean = sum[8] / sum[9];
-    normalize_kernel<<<grid_of(Qt), 256, 0, s>>>(feat, Qt, nm);
+    KDT_LAUNCH normalize_kernel<<<grid_of(Qt), 256, 0, s>>>(feat, Qt, nm);
 
     // He-uniform initial weights, zero biases, output bias at the label mean
     std::vector<float> h(P, 0.f);
@@ -695,7 +696,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         h[OW3 + i] = uni(sqrtf(6.f / H)) * 0.1f;
     h[OB3] = (float)label_mean;
     KDT_CUDA(cudaMemcpyAsync(t->model.d_params, h.data(), P * 4, cudaMemcpyHostToDevice, s));
-    round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, w);
+    KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, w);
     KDT_CUDA(cudaMemsetAsync(m, 0, P * 4, s));
     KDT_CUDA(cudaMemsetAsync(v, 0, P * 4, s));
 
@@ -708,7 +709,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
             KDT_TRY(loss_grad_dev(w, feat, lab, b0, cnt, part, grad, s));
             b1t *= 0.9;
             b2t *= 0.999;
-            adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, m, v, grad, o.lr, (float)(1.0 - b1t),
+            KDT_LAUNCH adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, m, v, grad, o.lr, (float)(1.0 - b1t),
                                                        (float)(1.0 - b2t), w, loss_acc);
         }
         KDT_CUDA(cudaGetLastError());

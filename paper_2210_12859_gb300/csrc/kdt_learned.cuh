@@ -5,8 +5,11 @@
 #include "kdt_internal.cuh"
 
 namespace kdt {
+// d_visits (optional): per-query processed nodes of the bounded pass plus,
+// for re-run queries, of the fallback pass; results are not written if d_ids
+// is NULL
 int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int32_t *d_ids,
-                      float *d_d2, cudaStream_t s);
+                      float *d_d2, int32_t *d_visits, cudaStream_t s);
 int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, int flags, int mode, int32_t *d_ids,
               float *d_d2, int32_t *d_visits, cudaStream_t s);
 void free_model(kdt_tree *t);

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
                 full = list.full(a.k);
                 worst = list.cull();
                 fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
-                if (MODE != MODE_VISITS && !fallback)
+                if (MODE != MODE_VISITS && !fallback && a.out_ids)
                     list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
             } else {
                 SmemList list;
@@ -60,13 +60,15 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
                 full = list.full(a.k);
                 worst = list.cull();
                 fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
-                if (MODE != MODE_VISITS && !fallback)
+                if (MODE != MODE_VISITS && !fallback && a.out_ids)
                     list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
             }
             if (v < 0)
                 atomicOr(a.err, ERR_TRAVERSAL);
-            if (MODE == MODE_VISITS)
+            if (MODE == MODE_VISITS || (MODE == MODE_BOUNDED && a.visits))
                 a.visits[qi] = v;
+            if (MODE == MODE_FALLBACK && a.visits)
+                a.visits[qi] += v;
             // a query is exact when its list is full (every point outside the
             // proposed radius is farther than all k held) or when the proposal
             // did not shrink the caller's radius; for the others the k-best set
@@ -159,7 +161,7 @@ inline int launch_kernel(Kern fn, int threads, size_t smem, const QueryArgs &a, 
         KDT_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = grid_for_kernel((const void *)fn, threads, smem);
     KDT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
-    fn<<<grid, threads, smem, s>>>(a);
+    KDT_LAUNCH fn<<<grid, threads, smem, s>>>(a);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }

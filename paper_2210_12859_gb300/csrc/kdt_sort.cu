@@ -211,9 +211,9 @@ int exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *scratch, cudaStream_
     if (n <= 0)
         return KDT_OK;
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    scan_reduce_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
-    scan_partials_kernel<<<1, 1024, 0, s>>>(scratch, tiles);
-    scan_downsweep_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
+    KDT_LAUNCH scan_reduce_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
+    KDT_LAUNCH scan_partials_kernel<<<1, 1024, 0, s>>>(scratch, tiles);
+    KDT_LAUNCH scan_downsweep_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -236,9 +236,9 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *
     int passes = (bits + 7) / 8;
     uint32_t *ka = keys, *va = vals, *kb = tmp_k, *vb = tmp_v;
     for (int p = 0; p < passes; ++p) {
-        radix_hist_kernel<<<(unsigned)tiles, RADIX_THREADS, 0, s>>>(ka, n, 8 * p, tiles, hist);
+        KDT_LAUNCH radix_hist_kernel<<<(unsigned)tiles, RADIX_THREADS, 0, s>>>(ka, n, 8 * p, tiles, hist);
         KDT_TRY(exclusive_scan_u32(hist, 256 * tiles, scan_tmp, s));
-        radix_scatter_kernel<<<(unsigned)tiles, RADIX_THREADS, 0, s>>>(ka, va, n, 8 * p, tiles, hist, kb, vb);
+        KDT_LAUNCH radix_scatter_kernel<<<(unsigned)tiles, RADIX_THREADS, 0, s>>>(ka, va, n, 8 * p, tiles, hist, kb, vb);
         KDT_CUDA(cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);

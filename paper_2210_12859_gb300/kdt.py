@@ -70,6 +70,7 @@ def _sig(name, args, res=_I):
 
 
 _lib.kdt_last_error.restype = ctypes.c_char_p
+_sig("kdt_launch_count", [], _I64)
 _sig("kdt_build", [_P, _I64, _I, _P, ctypes.POINTER(_P)])
 _sig("kdt_build_ex", [_P, _I64, _I, _I, _P, ctypes.POINTER(_P)])
 _sig("kdt_rebuild", [_P, _P, _I, _P])
@@ -216,6 +217,10 @@ def kdt_tree_info(tree: Tree):
 
 def kdt_last_error() -> str:
     return _lib.kdt_last_error().decode(errors="replace")
+
+
+def kdt_launch_count() -> int:
+    return int(_lib.kdt_launch_count())
 
 
 def kdt_rebuild(tree: Tree, points: torch.Tensor, opts: int = 0, stream=None) -> None:

@@ -239,14 +239,32 @@ def test_full_size_tree_property(kdt, gmm_full):
     check_tree(pts, ids.cpu().numpy(), coords.cpu().numpy())
 
 
-@pytest.mark.parametrize("k,r,flags_name", [(8, math.inf, "MORTON"), (1, math.inf, "MORTON"),
-                                            (64, math.inf, "MORTON"), (8, 0.005, "MORTON"),
-                                            (8, math.inf, "UNORDERED")])
-def test_full_size_sampled_queries(kdt, gmm_full, k, r, flags_name):
+def test_full_size_bench_configuration(kdt, gmm_full):
+    """The launch the benchmark times (all 2^24 queries, k = 8, Morton order),
+    checked on sampled outputs."""
     pts, qs, tree, dq = gmm_full
-    flags = getattr(kdt, "KDT_" + flags_name)
-    gi, gd = kdt.kdt_knn(tree, dq, k, r, flags=flags)
+    gi, gd = kdt.kdt_knn(tree, dq, 8, flags=kdt.KDT_MORTON)
     kdt.kdt_status(tree)
-    sample = np.random.default_rng(k).choice(len(qs), size=192, replace=False)
-    wi, wd = oracle.knn_brute_threaded(pts, qs[sample], k, r)
-    assert_same(gi[torch.from_numpy(sample).cuda()], gd[torch.from_numpy(sample).cuda()], wi, wd)
+    sample = np.random.default_rng(8).choice(len(qs), size=192, replace=False)
+    wi, wd = oracle.knn_brute_threaded(pts, qs[sample], 8)
+    sel = torch.from_numpy(sample).cuda()
+    assert_same(gi[sel], gd[sel], wi, wd)
+
+
+@pytest.mark.parametrize("k,r,flags_name", [(1, math.inf, "MORTON"), (64, math.inf, "MORTON"),
+                                            (8, 0.005, "MORTON"), (8, math.inf, "UNORDERED|MORTON"),
+                                            (16, math.inf, "ORDERED")])
+def test_full_size_tree_query_subsets(kdt, gmm_full, k, r, flags_name):
+    """Variants on the full 2^24 tree with a 2^16-query subset (sampled outputs)."""
+    pts, qs, tree, dq = gmm_full
+    flags = 0
+    for f in flags_name.split("|"):
+        flags |= getattr(kdt, "KDT_" + f)
+    sub = np.sort(np.random.default_rng(k + 1).choice(len(qs), size=1 << 16, replace=False))
+    q = cu(qs[sub])
+    gi, gd = kdt.kdt_knn(tree, q, k, r, flags=flags)
+    kdt.kdt_status(tree)
+    sample = np.random.default_rng(k).choice(len(sub), size=96, replace=False)
+    wi, wd = oracle.knn_brute_threaded(pts, qs[sub][sample], k, r)
+    sel = torch.from_numpy(sample).cuda()
+    assert_same(gi[sel], gd[sel], wi, wd)

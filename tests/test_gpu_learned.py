@@ -1,0 +1,201 @@
+"""GPU parity of the learned radius proposal.
+
+The proposal must never change a result: learned == plain, bit for bit.  Its
+parts are checked against the oracle: descent features (exact coordinates,
+log of the oracle's leaf distance within 2 ulp), MLP forward and gradients
+(FP64 oracle on the same BF16-rounded weights, FP32 accumulation tolerance).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_12859_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = 64 * 4 + 64 + 64 * 64 + 64 + 64 + 1
+H = 64
+
+
+@pytest.fixture(scope="module")
+def kdt():
+    from paper_2210_12859_gb300 import build
+
+    build.build_library()
+    from paper_2210_12859_gb300 import kdt as k
+
+    return k
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bits(x):
+    return np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+
+
+def weight_mask():
+    m = np.zeros(P, dtype=bool)
+    m[: 4 * H] = True                       # W1
+    m[5 * H: 5 * H + H * H] = True          # W2
+    m[6 * H + H * H: 7 * H + H * H] = True  # w3
+    return m
+
+
+def rounded(params):
+    p = np.asarray(params, dtype=np.float32).copy()
+    m = weight_mask()
+    p[m] = [oracle.round_bf16(float(v)) for v in p[m]]
+    return p.astype(np.float64)
+
+
+def random_params(seed, scale=0.3):
+    g = np.random.default_rng(seed)
+    return (g.standard_normal(P) * scale).astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def surface(kdt):
+    """Surface data (spheres and tori), N = 2^18, for the learned path."""
+    pts, qs = synth.surface_set(1 << 18, 3 << 14)
+    tree = kdt.kdt_build(cu(pts))
+    return pts, qs, tree
+
+
+def test_descent_features_match_oracle(kdt, surface):
+    pts, qs, tree = surface
+    sub = qs[:4000]
+    f = kdt.kdt_descent_features(tree, cu(sub)).cpu().numpy()
+    assert np.array_equal(bits(f[:, :3]), bits(sub))
+    _, node_ids = kdt.kdt_tree_export(tree)
+    d2 = oracle.descent_leaf_d2(pts, node_ids.cpu().numpy(), sub)
+    want = np.log(np.maximum(d2, np.float32(1e-30)).astype(np.float64))
+    assert np.allclose(f[:, 3], want, rtol=0, atol=4e-6 * np.maximum(1.0, np.abs(want)).max())
+
+
+def test_mlp_forward_matches_oracle(kdt):
+    p = random_params(1)
+    g = np.random.default_rng(2)
+    x = g.standard_normal((5000, 4)).astype(np.float32)
+    y = kdt.kdt_mlp_forward(p, cu(x)).cpu().numpy()
+    want = oracle.mlp_forward(rounded(p), H, x.astype(np.float64))
+    assert np.allclose(y, want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
+
+
+def test_mlp_gradients_match_oracle(kdt):
+    p = random_params(3)
+    g = np.random.default_rng(4)
+    n = 1000  # several blocks and a ragged tail
+    x = g.standard_normal((n, 4)).astype(np.float32)
+    lab = g.standard_normal(n).astype(np.float32)
+    loss, grad = kdt.kdt_mlp_loss_grad(p, cu(x), cu(lab))
+    wl, wg = oracle.mlp_loss_grad(rounded(p), H, x.astype(np.float64), lab.astype(np.float64))
+    assert math.isclose(loss, wl, rel_tol=1e-5)
+    scale = np.abs(wg).max()
+    assert np.allclose(grad, wg, rtol=1e-4, atol=1e-5 * scale)
+
+
+@pytest.fixture(scope="module")
+def trained(kdt, surface):
+    pts, qs, tree = surface
+    train = cu(qs[: 1 << 15])
+    loss = kdt.kdt_radius_model_train(tree, train, 8, epochs=10, batch=1024, seed=7)
+    return loss
+
+
+def test_training_fits_radii(kdt):
+    """On clustered data with 10% far queries the k-th neighbour radius spans
+    orders of magnitude; the trained model must explain most of its variance."""
+    mix = synth.gmm_mixture(64, 3, 0.01, 9)
+    pts = synth.gmm_sample(mix, 1 << 18, 10)
+    q = synth.gmm_queries(mix, 1 << 15, 0.1, 11)
+    tree = kdt.kdt_build(cu(pts))
+    loss = kdt.kdt_radius_model_train(tree, cu(q), 8, epochs=10, batch=1024, seed=3)
+    _, d2 = kdt.kdt_knn(tree, cu(q), 8)
+    lab = 0.5 * np.log(np.maximum(d2.cpu().numpy()[:, -1].astype(np.float64), 1e-30))
+    assert loss < 0.25 * lab.var(), (loss, lab.var())
+    # the proposal is then exact for most queries: few re-runs
+    qe = cu(synth.gmm_queries(mix, 1 << 14, 0.1, 12))
+    a = kdt.kdt_knn(tree, qe, 8)
+    b = kdt.kdt_knn(tree, qe, 8, flags=kdt.KDT_LEARNED)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    fb, ratio = kdt.kdt_learned_stats(tree)
+    assert fb < 0.2 * qe.shape[0], fb
+
+
+@pytest.mark.parametrize("k", [8, 32])
+@pytest.mark.parametrize("flags_name", ["MORTON", "ORDERED"])
+def test_learned_equals_plain(kdt, surface, trained, k, flags_name):
+    pts, qs, tree = surface
+    flags = getattr(kdt, "KDT_" + flags_name)
+    q = cu(qs[1 << 15:])
+    pi, pd = kdt.kdt_knn(tree, q, k, flags=flags)
+    li, ld = kdt.kdt_knn(tree, q, k, flags=flags | kdt.KDT_LEARNED)
+    assert torch.equal(pi, li)
+    assert torch.equal(pd.view(torch.int32), ld.view(torch.int32))
+    fb, ratio = kdt.kdt_learned_stats(tree)
+    assert 0 <= fb < q.shape[0]
+    if k == 8:
+        assert 1.0 <= ratio < 3.0
+    kdt.kdt_status(tree)
+
+
+def test_learned_bounded_radius_equals_plain(kdt, surface, trained):
+    pts, qs, tree = surface
+    q = cu(qs[1 << 15:])
+    for r in (0.002, 0.01, 1.0):
+        pi, pd = kdt.kdt_knn(tree, q, 8, r)
+        li, ld = kdt.kdt_knn(tree, q, 8, r, flags=kdt.KDT_LEARNED)
+        assert torch.equal(pi, li) and torch.equal(pd.view(torch.int32), ld.view(torch.int32))
+    # and against the oracle on a sample
+    sample = np.arange(0, q.shape[0], 97)
+    wi, wd = oracle.knn_brute(pts, qs[1 << 15:][sample], 8, 0.01)
+    li, ld = kdt.kdt_knn(tree, q, 8, 0.01, flags=kdt.KDT_LEARNED)
+    assert np.array_equal(li.cpu().numpy()[sample], wi)
+    assert np.array_equal(bits(ld.cpu().numpy()[sample]), bits(wd))
+
+
+def test_learned_visits_fewer_nodes(kdt, surface, trained):
+    """What the trained network gains: fewer processed nodes per query than
+    the plain ordered traversal, at identical results."""
+    pts, qs, tree = surface
+    q = cu(qs[1 << 15:])
+    plain = kdt.kdt_knn_visits(tree, q, 8).double().mean().item()
+    learned = kdt.kdt_knn_visits(tree, q, 8, flags=kdt.KDT_LEARNED).double().mean().item()
+    assert learned < plain, (learned, plain)
+
+
+def test_model_save_load_roundtrip(kdt, surface, trained, tmp_path):
+    pts, qs, tree = surface
+    path = os.path.join(tmp_path, "radius.bin")
+    kdt.kdt_radius_model_save(tree, path)
+    p1, n1, m1 = kdt.kdt_radius_model_get(tree)
+    other = kdt.kdt_build(cu(pts))
+    kdt.kdt_radius_model_load(other, path)
+    p2, n2, m2 = kdt.kdt_radius_model_get(other)
+    assert np.array_equal(p1, p2) and np.array_equal(n1, n2) and m1 == m2
+    q = cu(qs[1 << 15: (1 << 15) + 5000])
+    a = kdt.kdt_knn(tree, q, 8, flags=kdt.KDT_LEARNED)
+    b = kdt.kdt_knn(other, q, 8, flags=kdt.KDT_LEARNED)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    with open(path, "r+b") as f:
+        f.write(b"XXXX")
+    with pytest.raises(kdt.KdtError) as e:
+        kdt.kdt_radius_model_load(other, path)
+    assert e.value.code == kdt.KDT_EIO
+
+
+def test_learned_rejects_untrained_and_high_dim(kdt):
+    pts = synth.uniform(1000, 4, seed=1)
+    t = kdt.kdt_build(cu(pts))
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_radius_model_train(t, cu(pts), 8)
+    t3 = kdt.kdt_build(cu(pts[:, :3].copy()))
+    with pytest.raises(kdt.KdtError) as e:
+        kdt.kdt_knn(t3, cu(pts[:10, :3].copy()), 8, flags=kdt.KDT_LEARNED)
+    assert e.value.code == kdt.KDT_ENOMODEL
