@@ -189,6 +189,36 @@ def workload_config(log2n):
     }
 
 
+# ---------------------------------------------------------------- profile data
+
+KERNEL_SOURCES = ("kdt_traverse.cuh", "kdt_query_impl.cuh", "kdt_query.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2210_12859_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the traversal kernel from the committed ncu
+    summary, or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "knn_kernel_gmm2p24_dram.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    if kv.get("source_sha256_16", "").strip() != kernel_source_hash():
+        return None
+    try:
+        return int(kv["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------- our arm
 
 def main():
@@ -293,13 +323,7 @@ def main():
     kern_ms = trav_ms / max(trav_launches, 1)
     bytes_per_launch = n * (4 * 3 + 8 * K_NN) + v_sum * 16.0
     achieved = bytes_per_launch / (kern_ms / 1000.0) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("knn_kernel_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_source": peak_src,
                 "kernel": "knn_kernel<layout0,K=8,ordered> (stack-free traversal)",
