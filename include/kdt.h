@@ -143,7 +143,10 @@ typedef struct kdt_train_opts {
     int batch;            /* minibatch size (default 1024 if <= 0; rounded down to a multiple of 64) */
     float lr;             /* Adam step size (default 2e-3 if <= 0) */
     uint64_t seed;        /* weight initialisation seed */
-    float margin;         /* cull radius = margin * predicted radius (default 1.25 if <= 0) */
+    float margin;         /* cull radius = margin * predicted radius; if <= 0 the margin is
+                             calibrated after training so that a fraction fallback_target of
+                             the training queries would fall back */
+    float fallback_target;/* see margin (default 0.02 if <= 0) */
 } kdt_train_opts;
 
 /* Width of the two hidden layers of the radius model. */

@@ -624,7 +624,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     if (Qt > ((int64_t)1 << 26))
         return set_error(KDT_EINVAL, "at most 2^26 training queries");
     cudaStream_t s = (cudaStream_t)stream;
-    kdt_train_opts o{6, 1024, 2e-3f, 1, 1.25f};
+    kdt_train_opts o{6, 1024, 2e-3f, 1, 0.f, 0.02f};
     if (opts) {
         if (opts->epochs > 0)
             o.epochs = opts->epochs;
@@ -635,6 +635,8 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         o.seed = opts->seed;
         if (opts->margin > 0)
             o.margin = opts->margin;
+        if (opts->fallback_target > 0)
+            o.fallback_target = std::min(opts->fallback_target, 0.5f);
     }
     o.batch = std::max(TS, (o.batch / TS) * TS);
     KDT_TRY(ensure_params(t));
@@ -718,11 +720,29 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         KDT_CUDA(cudaStreamSynchronize(s));
         last = (float)(l / (double)Qt);
     }
+    float margin = o.margin;
+    if (!(margin > 0.f)) {
+        // calibrate: the proposal falls short for a query iff its residual
+        // label - prediction exceeds log(margin); take the (1 - target)
+        // quantile of the training residuals
+        float *pred = d2;  // reuse: Qt floats
+        KDT_LAUNCH mlp_forward_kernel<<<grid_of(Qt), 256, 0, s>>>(w, feat, Qt, pred);
+        KDT_CUDA(cudaGetLastError());
+        std::vector<float> hp(Qt), hl(Qt);
+        KDT_CUDA(cudaMemcpyAsync(hp.data(), pred, Qt * 4, cudaMemcpyDeviceToHost, s));
+        KDT_CUDA(cudaMemcpyAsync(hl.data(), lab, Qt * 4, cudaMemcpyDeviceToHost, s));
+        KDT_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < Qt; ++i)
+            hp[i] = hl[i] - hp[i];
+        int64_t at = std::min<int64_t>(Qt - 1, (int64_t)((1.0 - o.fallback_target) * (double)Qt));
+        std::nth_element(hp.begin(), hp.begin() + at, hp.end());
+        margin = expf(std::min(std::max(hp[at], -0.7f), 2.8f));
+    }
     for (int j = 0; j < 4; ++j) {
         t->model.norm[j] = nm.mu[j];
         t->model.norm[4 + j] = nm.sd[j];
     }
-    t->model.margin = o.margin;
+    t->model.margin = margin;
     t->model.k_trained = k;
     t->model.trained = true;
     if (final_loss)

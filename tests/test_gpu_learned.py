@@ -125,7 +125,10 @@ def test_training_fits_radii(kdt):
     b = kdt.kdt_knn(tree, qe, 8, flags=kdt.KDT_LEARNED)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     fb, ratio = kdt.kdt_learned_stats(tree)
-    assert fb < 0.2 * qe.shape[0], fb
+    # the margin is calibrated for 2% fallbacks on the training queries
+    assert fb < 0.06 * qe.shape[0], fb
+    _, _, margin = kdt.kdt_radius_model_get(tree)
+    assert 1.0 < margin < 16.0
 
 
 @pytest.mark.parametrize("k", [8, 32])
