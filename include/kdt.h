@@ -136,6 +136,23 @@ void kdt_free(kdt_tree *tree);
 int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_queries, int64_t Q,
                  int k, float max_radius, int flags, int32_t *h_ids, float *h_d2);
 
+/* kdt_knn without any device allocation.  The paper has no counterpart: this
+ * serves callers that must not enter the CUDA allocator while they query
+ * (an application whose own pool owns all device memory, a real-time loop
+ * that cannot afford the synchronisation of cudaMalloc / cudaFree, a plugin
+ * host that forbids library allocations).  Scratch lives in one fixed device
+ * array inside the library (about 4.3 MB per GPU that loads it, held until the
+ * process exits), so Q is limited to KDT_STATIC_MAX_Q per call; larger Q gives
+ * KDT_EINVAL.  KDT_LEARNED is not accepted.  Same arguments, results and
+ * flags as kdt_knn otherwise.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array: calls whose GPU work overlaps (other streams,
+ * other host threads) race and must be serialised. */
+#define KDT_STATIC_MAX_Q (1 << 18)
+int kdt_knn_static(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, float max_radius,
+                   int flags, int32_t *d_ids, float *d_d2, void *stream);
+
 /* ---- learned radius proposal (not in the paper) ------------------------- */
 
 typedef struct kdt_train_opts {

@@ -1,0 +1,115 @@
+// kdt_knn_static: kdt_knn for callers that cannot allocate device memory.
+//
+// Some callers are not allowed to enter the CUDA allocator while they query:
+// an application that hands all device memory to its own pool at start-up
+// and leaves nothing for a library's cudaMalloc; a real-time loop in which
+// the implicit synchronisation of cudaMalloc / cudaFree would stall other
+// work; a plugin whose host forbids device allocations from inside a frame.
+// For them this entry point keeps its scratch (the warp work counter and the
+// Morton keys, permutation and radix-sort temporaries) in one file-scope
+// device array of fixed size instead of allocating it per call.  The array
+// lives in every GPU that loads the library until the process exits.
+//
+// The array is shared by all calls: a call clears what must start at zero (the
+// work counter) and overwrites the rest before reading it.  Two calls whose
+// work overlaps on the GPU (different streams, or host threads racing) use
+// the same bytes and race; serialise them.
+#include <mutex>
+
+#include "kdt_query.cuh"
+
+namespace kdt {
+
+int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
+                 void *scratch, uint32_t **perm_out, cudaStream_t s);
+size_t morton_scratch_bytes(int64_t Q);
+
+namespace {
+
+constexpr int64_t STATIC_MAX_Q = KDT_STATIC_MAX_Q;
+constexpr size_t STATIC_COUNTER_BYTES = 256;
+// four u32 arrays of Q entries (keys, permutation, two sort temporaries) plus
+// the radix histograms (256 per 2048-key tile) and their scan partials, each
+// piece rounded up to 256 bytes, plus the counter block
+constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t STATIC_TILES = (size_t)(STATIC_MAX_Q + 2047) / 2048;
+constexpr size_t STATIC_BYTES =
+    STATIC_COUNTER_BYTES + 4 * round256((size_t)STATIC_MAX_Q * 4) +
+    round256((256 * STATIC_TILES + (256 * STATIC_TILES + 2047) / 2048 + 1) * 4) + 256;
+
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
+
+std::mutex g_mu;
+void *g_addr[64] = {nullptr};
+
+// Device address of g_static_scratch on the current device.  In host code the
+// symbol name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int static_scratch(void **out)
+{
+    int dev = 0;
+    KDT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64)
+        return set_error(KDT_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return KDT_OK;
+}
+
+}  // namespace
+}  // namespace kdt
+
+using namespace kdt;
+
+extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, int flags,
+                              int32_t *d_ids, float *d_d2, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (Q < 0)
+        return set_error(KDT_EINVAL, "Q must be >= 0 (got %lld)", (long long)Q);
+    if (Q > STATIC_MAX_Q)
+        return set_error(KDT_EINVAL, "kdt_knn_static serves at most %lld queries per call (got %lld)",
+                         (long long)STATIC_MAX_Q, (long long)Q);
+    if (k < 1 || k > 64)
+        return set_error(KDT_EINVAL, "k must be in [1, 64] (got %d)", k);
+    if (!(max_radius >= 0.f))
+        return set_error(KDT_EINVAL, "max_radius must be >= 0 (got %g)", (double)max_radius);
+    if (flags & KDT_LEARNED)
+        return set_error(KDT_EINVAL, "kdt_knn_static does not take KDT_LEARNED");
+    if (Q > 0 && (!d_q || !d_ids || !d_d2))
+        return set_error(KDT_EINVAL, "NULL query or output pointer");
+    if (Q == 0)
+        return KDT_OK;
+    if (STATIC_COUNTER_BYTES + morton_scratch_bytes(Q) > STATIC_BYTES)
+        return set_error(KDT_EINVAL, "static scratch too small for %lld queries", (long long)Q);
+    void *base = nullptr;
+    KDT_TRY(static_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    QueryArgs a;
+    a.counter = (unsigned long long *)base;  // zeroed by the launch
+    if (flags & KDT_MORTON)
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (char *)base + STATIC_COUNTER_BYTES,
+                             const_cast<uint32_t **>(&a.perm), s));
+    a.nodes = t->nodes;
+    a.ids = t->ids;
+    a.N = (int)t->N;
+    a.D = t->D;
+    a.queries = d_q;
+    a.Q = Q;
+    a.k = k;
+    a.r2 = max_radius * max_radius;
+    a.out_ids = d_ids;
+    a.out_d2 = d_d2;
+    a.err = t->err;
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, t->layout, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+    return launch_query(t->layout, a, !(flags & KDT_UNORDERED), MODE_RESULTS, false, s);
+}

@@ -79,6 +79,7 @@ _sig("kdt_tree_export", [_P, _P, _P, _P])
 _sig("kdt_fcp", [_P, _P, _I64, _F, _I, _P, _P, _P])
 _sig("kdt_knn", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
 _sig("kdt_knn_visits", [_P, _P, _I64, _I, _F, _I, _P, _P])
+_sig("kdt_knn_static", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
 _sig("kdt_status", [_P, _P])
 _sig("kdt_free", [_P], None)
 _sig("kdt_knn_host", [_P, _I64, _I, _P, _I64, _I, _F, _I, _P, _P])
@@ -251,6 +252,21 @@ def kdt_knn(tree: Tree, queries: torch.Tensor, k: int, max_radius: float = math.
     _check(_lib.kdt_knn(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, k, float(max_radius),
                         flags, _dev(out_ids, torch.int32, "out_ids", (Q, k)),
                         _dev(out_d2, torch.float32, "out_d2", (Q, k)), _stream(stream)))
+    return out_ids, out_d2
+
+
+KDT_STATIC_MAX_Q = 1 << 18
+
+
+def kdt_knn_static(tree: Tree, queries: torch.Tensor, k: int, max_radius: float = math.inf, flags: int = 0,
+                   out_ids=None, out_d2=None, stream=None):
+    """kdt_knn with its scratch in the library's fixed device array (no
+    device allocation inside the call; Q <= KDT_STATIC_MAX_Q)."""
+    Q = queries.shape[0]
+    out_ids, out_d2 = _outputs(Q, k, out_ids, out_d2, queries.device)
+    _check(_lib.kdt_knn_static(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, k,
+                               float(max_radius), flags, _dev(out_ids, torch.int32, "out_ids", (Q, k)),
+                               _dev(out_d2, torch.float32, "out_d2", (Q, k)), _stream(stream)))
     return out_ids, out_d2
 
 
