@@ -237,6 +237,29 @@ int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids,
 
 void kdt_forest_free(kdt_forest *forest);
 
+/* ---- launch tuning -------------------------------------------------------- */
+
+/* The traversal kernels copy the top `levels` levels of the tree (2^levels - 1
+ * nodes) into shared memory once per block.  Staging trades L1 capacity (the
+ * same on-chip array) for the latency of the top-level loads; the best depth
+ * depends on the tree and the queries.  -1 restores the automatic choice (the
+ * tuned value for this tree's shape if kdt_autotune or kdt_tuning_load set
+ * one, else 0: no staging).  levels in [-1, 16]. */
+int kdt_set_stage_levels(kdt_tree *tree, int levels);
+
+/* Time the plain traversal of up to 2^20 of the given queries for each
+ * staging depth in {0, 4, 6, 8, 10, 11, 12} (within 64 KB of shared memory)
+ * and remember the fastest for this tree's shape (GPU name, D, k bucket,
+ * floor(log2 N)); later queries on trees of that shape use it unless
+ * kdt_set_stage_levels overrides.  Synchronous.  *best_levels and *best_ms
+ * (may be NULL) receive the choice and its time per launch. */
+int kdt_autotune(kdt_tree *tree, const float *d_queries, int64_t Q, int k, int flags, int *best_levels,
+                 float *best_ms, void *stream);
+
+/* Write / read the remembered tuning choices as a small JSON file. */
+int kdt_tuning_save(const char *path);
+int kdt_tuning_load(const char *path);
+
 /* ---- profiling ----------------------------------------------------------- */
 
 /* Accumulate device time of the traversal kernels launched by kdt_knn /

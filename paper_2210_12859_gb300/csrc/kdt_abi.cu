@@ -262,8 +262,7 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.visits = d_visits;
     a.err = t->err;
     a.counter = counter;
-    int budget = k <= MAX_REG_K ? 32 * 1024 : 16 * 1024;
-    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, t->layout, budget);
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     cudaEvent_t stop;
     KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
     KDT_TRY(launch_query(t->layout, a, !(flags & KDT_UNORDERED), mode, false, s));
@@ -334,7 +333,9 @@ static int alloc_tree(int64_t N, int D, kdt_tree **out)
     t->layout = layout_of(D);
     cudaGetDevice(&t->device);
     t->prof = new Prof();
-    cudaError_t e = cudaMalloc(&t->nodes, (size_t)N * float4_per_node(D) * sizeof(float4));
+    const int nf = float4_per_node(D);
+    cudaError_t e = cudaMalloc(&t->nodes_alloc, ((size_t)N * nf + (nf == 1 ? 1 : 0)) * sizeof(float4));
+    t->nodes = t->nodes_alloc + (nf == 1 ? 1 : 0);
     if (e == cudaSuccess && t->layout > 0)
         e = cudaMalloc(&t->ids, (size_t)N * sizeof(int32_t));
     if (e == cudaSuccess)
@@ -485,7 +486,7 @@ void kdt_free(kdt_tree *t)
 {
     if (!t)
         return;
-    cudaFree(t->nodes);
+    cudaFree(t->nodes_alloc);
     cudaFree(t->ids);
     cudaFree(t->bbox);
     cudaFree(t->err);
@@ -742,7 +743,7 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
             a.out_d2 = d_d2 + h_qoff[i] * k;
             a.err = f->err;
             a.counter = counter;
-            a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(n, layout, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+            a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(n, 6);
             KDT_TRY(launch_query(layout, a, !(flags & KDT_UNORDERED), 0, false, s));
         }
         return KDT_OK;

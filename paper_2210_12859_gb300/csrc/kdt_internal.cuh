@@ -133,12 +133,7 @@ __host__ __device__ __forceinline__ int float4_per_node(int D) { return D <= 4 ?
 // ---------------------------------------------------------------- primitives
 // Stable LSD radix sort of (u32 key, u32 value) pairs on bits [0, bits).
 // keys/vals hold the input and receive the output; tmp_k / tmp_v are scratch of
-// n elements each.
-struct SortScratch {
-    uint32_t *hist = nullptr;      // 256 * tiles
-    uint32_t *partials = nullptr;  // scan partials
-    size_t hist_elems = 0;
-};
+// n elements each, `scratch` holds radix_scratch_elems(n) elements.
 size_t radix_scratch_elems(int64_t n);
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *tmp_v, int64_t n,
                      int bits, uint32_t *scratch, cudaStream_t s);
@@ -165,8 +160,6 @@ struct ForestDesc {
     int D = 3;
     int64_t total = 0;
     int64_t *d_offsets = nullptr;  // [T+1] node offsets of each tree
-    int32_t *d_tree_of = nullptr;  // [total] tree index per node position (T > 1 only)
-    int maxH = 0;
 };
 
 }  // namespace kdt
@@ -176,15 +169,19 @@ struct kdt_tree {
     int D = 0;
     int layout = 0;
     int device = 0;
-    float4 *nodes = nullptr;       // N * float4_per_node(D)
+    float4 *nodes = nullptr;       // N * float4_per_node(D), node t at nodes[t * float4_per_node(D)]
+    float4 *nodes_alloc = nullptr; // allocation; 16-byte nodes start one slot in, so that the siblings
+                                   // 2c+1 and 2c+2 share one 32-byte sector
     int32_t *ids = nullptr;        // layout > 0
     float *bbox = nullptr;         // device [2][3]: lo, hi of the first min(D,3) dims
     int *err = nullptr;            // device error word
     kdt::Model model;
     // learned-path statistics of the last learned query
-    int64_t *stats = nullptr;      // device [2]: fallback count, ratio sum as fixed-point
-    double *ratio_sum = nullptr;   // device
+    int64_t *stats = nullptr;      // device [2]: fallback count, sum of radius ratios (double bits)
     int64_t last_learned_q = 0;
+    // top tree levels staged in shared memory by the traversal kernels
+    // (-1: the tuned or default depth for this tree's shape)
+    int stage_levels = -1;
     // profiling
     bool profiling = false;
     void *prof = nullptr;
@@ -201,6 +198,9 @@ struct kdt_forest {
 };
 
 namespace kdt {
+// staging depth (levels) for a query on tree t with k neighbours: the tree's
+// own setting, else the tuned value for its shape, else the default
+int stage_levels_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 int build_forest(const float *d_points, const int64_t *h_offsets, int T, int D, float4 *nodes,
                  int32_t *ids, float *bbox, int *err, cudaStream_t s);

@@ -505,7 +505,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
     Norm nm;
     model_norm(t, &nm);
-    const int staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, 32 * 1024);
+    const int staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     const size_t smem = (size_t)((P + 3) / 4) * 16 + (size_t)staged * 16;
     KDT_CUDA(cudaFuncSetAttribute(radius_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int g = grid_for_kernel((const void *)radius_kernel, 256, smem);
@@ -530,7 +530,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.visits = d_visits;
     a.err = t->err;
     a.counter = counter;
-    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, 0, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.r2q = r2q;
     a.fb_list = fb_list;
     a.fb_count = (unsigned long long *)t->stats;
@@ -556,7 +556,7 @@ int kdt_descent_features(const kdt_tree *t, const float *d_q, int64_t Q, float *
     if (Q == 0)
         return KDT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int staged = staged_nodes(t->N, 0, 32 * 1024);
+    const int staged = staged_for_levels(t->N, stage_levels_for(t, 8));
     KDT_LAUNCH features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged, d_feat);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;

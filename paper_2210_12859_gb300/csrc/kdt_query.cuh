@@ -6,9 +6,10 @@
 
 namespace kdt {
 
-constexpr int REG_THREADS = 256;   // block size of the register-list kernels
+constexpr int REG_THREADS = 128;   // block size of the register-list kernels
 constexpr int SMEM_THREADS = 128;  // block size of the shared-memory-list kernels
 constexpr int MAX_REG_K = 16;
+constexpr int STEPS_PER_CLAIM = 16; // traversal steps between two query claims of a warp
 
 struct QueryArgs {
     const float4 *nodes = nullptr;     // single tree: its nodes; batched: all nodes
@@ -54,14 +55,12 @@ inline int launch_query(int layout, const QueryArgs &a, bool ordered, int mode, 
     }
 }
 
-// number of nodes to stage for a tree of n nodes and a shared-memory budget
-inline int staged_nodes(int64_t n, int layout, int budget_bytes)
+// nodes staged in shared memory for `levels` top levels of a tree of n nodes
+inline int staged_for_levels(int64_t n, int levels)
 {
-    int per = layout == 2 ? 32 : 16;
-    int64_t lv = 0;
-    while ((((int64_t)2 << lv) - 1) * per <= budget_bytes && lv < 20)
-        ++lv;
-    int64_t cap = ((int64_t)1 << lv) - 1;
+    if (levels <= 0)
+        return 0;
+    int64_t cap = ((int64_t)1 << levels) - 1;
     return (int)(n < cap ? n : cap);
 }
 

@@ -1,156 +1,188 @@
 // Query kernels, instantiated once per node layout by kdt_query_l{0,1,2}.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "kdt_query.cuh"
 
 namespace kdt {
 
-// Single tree.  Persistent blocks stage the top levels once, then every warp
-// repeatedly claims the next 32 query slots from a global counter, so the
-// slow lanes of a warp hold up only that warp and the tail stays short.
-template <int LAYOUT, int K, bool ORDERED, int MODE>
+// Claim the next queries for the lanes of the warp that need one: one atomic
+// per warp, consecutive slots in lane order.  Returns the slot of this lane
+// (or a value >= limit when the work is exhausted); all 32 lanes must call.
+__device__ __forceinline__ int64_t claim_slot(bool need, unsigned long long *counter)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    int64_t slot = INT64_MAX;
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader)
+            base = atomicAdd(counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need)
+            slot = (int64_t)(base + __popc(m & lane_mask_lt()));
+    }
+    return slot;
+}
+
+// Single tree.  Persistent blocks stage the top levels once; every lane then
+// runs queries back to back: when its query ends it claims the next one
+// (persistent threads with replacement), so a lane never idles while a slow
+// neighbour in its warp is still traversing, until the work runs out.
+template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_kernel(const QueryArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
+    using List = typename std::conditional<(K <= MAX_REG_K), RegList<K <= MAX_REG_K ? K : 1>, SmemList>::type;
     extern __shared__ float4 s_dyn[];
     float4 *s_nodes = s_dyn;
-    stage_nodes<LAYOUT>(a.nodes, s_nodes, a.staged);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
+    if (STAGE) {
+        stage_nodes<LAYOUT>(a.nodes, s_nodes, a.staged);
+        __syncthreads();
+    }
     const int64_t Qn = MODE == MODE_FALLBACK ? (int64_t)*a.fb_count : a.Q;
     double ratio = 0.0;
+    int64_t qi = -1;
+    bool exhausted = false;
+    float q[NC];
+    float r2 = 0.f;
+    int visits = 0;
+    List list;
+    if constexpr (K > MAX_REG_K) {
+        list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
+        list.stride = blockDim.x;
+    }
+    Walker<LAYOUT, ORDERED> w;
     for (;;) {
-        unsigned long long b = 0;
-        if (lane == 0)
-            b = atomicAdd(a.counter, 32ull);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= (unsigned long long)Qn)
-            break;
-        const int64_t i = (int64_t)b + lane;
-        bool fallback = false;
-        int64_t qi = 0;
-        if (i < Qn) {
-            if (MODE == MODE_FALLBACK)
-                qi = a.fb_list[i];
-            else
-                qi = a.perm ? (int64_t)a.perm[i] : i;
-            const float r2 = MODE == MODE_BOUNDED ? a.r2q[qi] : a.r2;
-            float q[NC];
-            load_query<LAYOUT>(a.queries, qi, a.D, q);
-            int v;
-            bool full;
-            float worst;
-            if constexpr (K <= MAX_REG_K) {
-                RegList<K> list;
+        const bool need = qi < 0 && !exhausted;
+        const int64_t slot = claim_slot(need, a.counter);
+        if (need) {
+            if (slot < Qn) {
+                qi = MODE == MODE_FALLBACK ? (int64_t)a.fb_list[slot] : (a.perm ? (int64_t)a.perm[slot] : slot);
+                r2 = MODE == MODE_BOUNDED ? a.r2q[qi] : a.r2;
+                load_query<LAYOUT>(a.queries, qi, a.D, q);
                 list.init(a.k, r2);
-                v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
-                full = list.full(a.k);
-                worst = list.cull();
-                fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
-                if (MODE != MODE_VISITS && !fallback && a.out_ids)
-                    list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+                w.start();
+                visits = 0;
             } else {
-                SmemList list;
-                list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
-                list.stride = blockDim.x;
-                list.init(a.k, r2);
-                v = traverse<LAYOUT, ORDERED>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list);
-                full = list.full(a.k);
-                worst = list.cull();
-                fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
-                if (MODE != MODE_VISITS && !fallback && a.out_ids)
-                    list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+                exhausted = true;
             }
-            if (v < 0)
-                atomicOr(a.err, ERR_TRAVERSAL);
-            if (MODE == MODE_VISITS || (MODE == MODE_BOUNDED && a.visits))
-                a.visits[qi] = v;
-            if (MODE == MODE_FALLBACK && a.visits)
-                a.visits[qi] += v;
-            // a query is exact when its list is full (every point outside the
-            // proposed radius is farther than all k held) or when the proposal
-            // did not shrink the caller's radius; for the others the k-best set
-            // may lie beyond the proposal and they are re-run
-            if (MODE == MODE_BOUNDED && !fallback && full && worst > 0.f && r2 < __int_as_float(0x7f800000))
-                ratio += sqrt((double)r2 / (double)worst);
         }
+        if (__all_sync(0xffffffffu, qi < 0))
+            break;
+        if (qi < 0)
+            continue;
+        // up to STEPS_PER_CLAIM steps between claims: amortises the warp vote
+        bool overflow = false;
+        bool fin = false;
+        for (int s = 0; s < STEPS_PER_CLAIM && !fin; ++s)
+            fin = w.template step<STAGE>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits, overflow);
+        if (!fin)
+            continue;
+        // query finished
+        if (overflow)
+            atomicOr(a.err, ERR_TRAVERSAL);
+        const bool full = list.full(a.k);
+        // a bounded query is exact when its list is full (every point outside
+        // the proposed radius is farther than all k held) or when the proposal
+        // did not shrink the caller's radius; the others are re-run
+        const bool fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
+        if (MODE != MODE_VISITS && !fallback && a.out_ids)
+            list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+        if (MODE == MODE_VISITS || (MODE == MODE_BOUNDED && a.visits))
+            a.visits[qi] = overflow ? -1 : visits;
+        if (MODE == MODE_FALLBACK && a.visits)
+            a.visits[qi] += visits;
         if (MODE == MODE_BOUNDED) {
-            // warp-aggregated append of the queries to re-run (all lanes here)
-            const unsigned m = __ballot_sync(0xffffffffu, fallback);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long base = 0;
-                if (lane == leader)
-                    base = atomicAdd(a.fb_count, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (fallback)
-                    a.fb_list[base + __popc(m & ((1u << lane) - 1))] = (uint32_t)qi;
+            if (fallback) {
+                const unsigned long long at = atomicAdd(a.fb_count, 1ull);
+                a.fb_list[at] = (uint32_t)qi;
+            } else if (full && list.cull() > 0.f && r2 < __int_as_float(0x7f800000)) {
+                ratio += sqrt((double)r2 / (double)list.cull());
             }
         }
+        qi = -1;
     }
     if (MODE == MODE_BOUNDED) {
         for (int o = 16; o > 0; o >>= 1)
             ratio += __shfl_down_sync(0xffffffffu, ratio, o);
-        if (lane == 0 && ratio != 0.0)
+        if ((threadIdx.x & 31) == 0 && ratio != 0.0)
             atomicAdd(a.ratio_sum, ratio);
     }
 }
 
-// Forest: every query slot finds its tree by binary search over the query
-// offsets; no shared-memory staging (trees differ between neighbouring slots).
+// Forest: a lane's query finds its tree by binary search over the query
+// offsets; no shared-memory staging (neighbouring lanes may walk different
+// trees).  Same lane-refill scheme as knn_kernel.
 template <int LAYOUT, int K, bool ORDERED>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_forest_kernel(const QueryArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
+    using List = typename std::conditional<(K <= MAX_REG_K), RegList<K <= MAX_REG_K ? K : 1>, SmemList>::type;
     extern __shared__ float4 s_dyn[];
-    const int lane = threadIdx.x & 31;
+    int64_t qi = -1;
+    bool exhausted = false;
+    float q[NC];
+    int visits = 0;
+    int N = 0;
+    const float4 *nodes = nullptr;
+    const int32_t *ids = nullptr;
+    List list;
+    if constexpr (K > MAX_REG_K) {
+        list.s = reinterpret_cast<unsigned long long *>(s_dyn) + threadIdx.x;
+        list.stride = blockDim.x;
+    }
+    Walker<LAYOUT, ORDERED> w;
     for (;;) {
-        unsigned long long b = 0;
-        if (lane == 0)
-            b = atomicAdd(a.counter, 32ull);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= (unsigned long long)a.Q)
+        const bool need = qi < 0 && !exhausted;
+        const int64_t slot = claim_slot(need, a.counter);
+        if (need) {
+            if (slot < a.Q) {
+                qi = a.perm ? (int64_t)a.perm[slot] : slot;
+                int lo = 0, hi = a.T - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.q_off[mid] <= qi)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const int64_t nb = a.node_off[lo];
+                N = (int)(a.node_off[lo + 1] - nb);
+                nodes = a.nodes + nb * NF;
+                ids = a.ids ? a.ids + nb : nullptr;
+                load_query<LAYOUT>(a.queries, qi, a.D, q);
+                list.init(a.k, a.r2);
+                w.start();
+                visits = 0;
+                if (N == 0) {  // empty cloud: empty result
+                    list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+                    qi = -1;
+                }
+            } else {
+                exhausted = true;
+            }
+        }
+        if (__all_sync(0xffffffffu, qi < 0))
             break;
-        const int64_t i = (int64_t)b + lane;
-        if (i >= a.Q)
+        if (qi < 0)
             continue;
-        const int64_t qi = a.perm ? (int64_t)a.perm[i] : i;
-        int lo = 0, hi = a.T - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (a.q_off[mid] <= qi)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const int64_t nb = a.node_off[lo];
-        const int N = (int)(a.node_off[lo + 1] - nb);
-        float q[NC];
-        load_query<LAYOUT>(a.queries, qi, a.D, q);
-        const float4 *nodes = a.nodes + nb * NF;
-        const int32_t *ids = a.ids ? a.ids + nb : nullptr;
-        int v = 0;
-        if constexpr (K <= MAX_REG_K) {
-            RegList<K> list;
-            list.init(a.k, a.r2);
-            if (N > 0)
-                v = traverse<LAYOUT, ORDERED>(nodes, ids, nullptr, 0, N, a.D, q, list);
-            list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
-        } else {
-            SmemList list;
-            list.s = reinterpret_cast<unsigned long long *>(s_dyn) + threadIdx.x;
-            list.stride = blockDim.x;
-            list.init(a.k, a.r2);
-            if (N > 0)
-                v = traverse<LAYOUT, ORDERED>(nodes, ids, nullptr, 0, N, a.D, q, list);
-            list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
-        }
-        if (v < 0)
+        bool overflow = false;
+        bool fin = false;
+        for (int s = 0; s < STEPS_PER_CLAIM && !fin; ++s)
+            fin = w.template step<false>(nodes, ids, nullptr, 0, N, a.D, q, list, visits, overflow);
+        if (!fin)
+            continue;
+        if (overflow)
             atomicOr(a.err, ERR_TRAVERSAL);
+        list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
+        qi = -1;
     }
 }
 
@@ -166,6 +198,35 @@ inline int launch_kernel(Kern fn, int threads, size_t smem, const QueryArgs &a, 
     return KDT_OK;
 }
 
+template <int LAYOUT, int K, bool STAGE>
+inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, size_t smem, cudaStream_t s)
+{
+    switch (mode) {
+    case MODE_VISITS:
+        if (ordered)
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS, STAGE>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE>, threads, smem, a, s);
+    case MODE_BOUNDED:
+    case MODE_FALLBACK:
+        if constexpr (LAYOUT == 0) {
+            if (mode == MODE_BOUNDED) {
+                if (ordered)
+                    return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE>, threads, smem, a, s);
+                return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE>, threads, smem, a, s);
+            }
+            if (ordered)
+                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_FALLBACK, STAGE>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_FALLBACK, STAGE>, threads, smem, a, s);
+        } else {
+            return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
+        }
+    default:
+        if (ordered)
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, STAGE>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, STAGE>, threads, smem, a, s);
+    }
+}
+
 template <int LAYOUT, int K>
 inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s)
 {
@@ -178,30 +239,9 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
         return launch_kernel(knn_forest_kernel<LAYOUT, K, false>, threads, list_bytes, a, s);
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
-    switch (mode) {
-    case MODE_VISITS:
-        if (ordered)
-            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS>, threads, smem, a, s);
-        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS>, threads, smem, a, s);
-    case MODE_BOUNDED:
-    case MODE_FALLBACK:
-        if constexpr (LAYOUT == 0) {
-            if (mode == MODE_BOUNDED) {
-                if (ordered)
-                    return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED>, threads, smem, a, s);
-                return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED>, threads, smem, a, s);
-            }
-            if (ordered)
-                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_FALLBACK>, threads, smem, a, s);
-            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_FALLBACK>, threads, smem, a, s);
-        } else {
-            return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
-        }
-    default:
-        if (ordered)
-            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS>, threads, smem, a, s);
-        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS>, threads, smem, a, s);
-    }
+    if (a.staged > 0)
+        return launch_mode<LAYOUT, K, true>(a, ordered, mode, threads, smem, s);
+    return launch_mode<LAYOUT, K, false>(a, ordered, mode, threads, smem, s);
 }
 
 template <int LAYOUT>

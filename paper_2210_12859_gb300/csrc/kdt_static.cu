@@ -110,6 +110,6 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     a.out_ids = d_ids;
     a.out_d2 = d_d2;
     a.err = t->err;
-    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_nodes(t->N, t->layout, k <= MAX_REG_K ? 32 * 1024 : 16 * 1024);
+    a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     return launch_query(t->layout, a, !(flags & KDT_UNORDERED), MODE_RESULTS, false, s);
 }

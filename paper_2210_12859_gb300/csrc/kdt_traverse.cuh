@@ -24,14 +24,14 @@ __device__ __forceinline__ float4 ldg_f4(const float4 *p) { return __ldg(p); }
 
 // Fetch node `curr` (from shared memory when it is among the `staged` first
 // nodes).  nodes: the tree's node array (already offset to the tree's base).
-template <int LAYOUT>
+template <int LAYOUT, bool STAGE = true>
 __device__ __forceinline__ NodeVal<LAYOUT> fetch(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged,
                                                  int curr)
 {
     NodeVal<LAYOUT> v;
     if constexpr (LAYOUT == 2) {
         float4 a, b;
-        if (curr < staged) {
+        if (STAGE && curr < staged) {
             a = s_nodes[2 * curr];
             b = s_nodes[2 * curr + 1];
         } else {
@@ -42,7 +42,7 @@ __device__ __forceinline__ NodeVal<LAYOUT> fetch(const float4 *__restrict__ node
         v.c[4] = b.x; v.c[5] = b.y; v.c[6] = b.z; v.c[7] = b.w;
         v.id = 0;
     } else {
-        float4 a = curr < staged ? s_nodes[curr] : ldg_f4(nodes + curr);
+        float4 a = (STAGE && curr < staged) ? s_nodes[curr] : ldg_f4(nodes + curr);
         v.c[0] = a.x; v.c[1] = a.y; v.c[2] = a.z;
         if constexpr (LAYOUT == 1) {
             v.c[3] = a.w;
@@ -176,72 +176,146 @@ struct SmemList {
     __device__ __forceinline__ bool full(int) const { return (uint32_t)w != EMPTY_ID; }
 };
 
-// One query through the stack-free state machine (Sec. 3.2).  Invalid children
-// are never stepped into: stepping into a missing child and straight back only
-// returns to the same node with prev = that child, so the machine continues
-// as if the child had been visited; the sequence of valid nodes, and hence
-// every processNode call, is unchanged.  Returns the number of first visits,
-// or -1 if the step bound 3N+3 was exceeded (impossible for a valid tree).
-template <int LAYOUT, bool ORDERED, class List>
-__device__ __forceinline__ int traverse(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
-                                        const float4 *s_nodes, int staged, int N, int D,
+// processNode of fcp / kNN for node `n` (values nd)
+template <int LAYOUT, class List>
+__device__ __forceinline__ void process(const NodeVal<LAYOUT> &nd, int n, const int32_t *__restrict__ ids,
                                         const float (&q)[LayoutTraits<LAYOUT>::NC], List &list)
 {
-    constexpr int NC = LayoutTraits<LAYOUT>::NC;
-    int curr = 0, prev = -1, dim = 0, visits = 0;
-    const long long cap = 3ll * N + 3;
-    for (long long step = 0;; ++step) {
-        if (step > cap)
-            return -1;
-        NodeVal<LAYOUT> nd = fetch<LAYOUT>(nodes, s_nodes, staged, curr);
+    const float d2 = dist2<LayoutTraits<LAYOUT>::NC>(nd.c, q);
+    if (d2 <= key_d2(list.worst())) {
+        const uint32_t id = LAYOUT == 0 ? nd.id : (uint32_t)__ldg(ids + n);
+        const unsigned long long key = pack_key(d2, id);
+        if (key < list.worst())
+            list.insert(key);
+    }
+}
+
+// The stack-free state machine of Sec. 3.2 for one query, advanced one step
+// at a time so that a persistent lane can interleave queries.
+//
+// Two shortcuts leave the sequence of processed nodes unchanged:
+//  * a missing child is never stepped into: stepping into it and straight back
+//    only sets prev to that child, so the machine continues as if it had been
+//    visited;
+//  * when a node's children are leaves (or missing), they are processed in the
+//    node's own step, in the order the machine would visit them (close child,
+//    then far child if the plane is still within the cull radius; unordered:
+//    left then right, each if in range), and the step returns to the parent -
+//    exactly the four steps into and out of the leaves, without them.
+template <int LAYOUT, bool ORDERED>
+struct Walker {
+    static constexpr int NC = LayoutTraits<LAYOUT>::NC;
+    int curr, prev, dim;
+    uint32_t steps;
+
+    __device__ __forceinline__ void start()
+    {
+        curr = 0;
+        prev = -1;
+        dim = 0;
+        steps = 0;
+    }
+
+    // one step; returns true when the traversal has finished (or exceeded
+    // its step bound, reported through *overflow).  STAGE: the first
+    // `staged` nodes are read from shared memory.
+    template <bool STAGE, class List>
+    __device__ __forceinline__ bool step(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
+                                         const float4 *s_nodes, int staged, int N, int D, const float (&q)[NC],
+                                         List &list, int &visits, bool &overflow)
+    {
+        if (++steps > 3u * (uint32_t)N + 3u) {
+            overflow = true;
+            return true;
+        }
+        const NodeVal<LAYOUT> nd = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, curr);
         const bool from_parent = prev < curr;
         if (from_parent) {
             ++visits;
-            float d2 = dist2<NC>(nd.c, q);
-            if (d2 <= key_d2(list.worst())) {
-                uint32_t id = LAYOUT == 0 ? nd.id : (uint32_t)__ldg(ids + curr);
-                unsigned long long key = pack_key(d2, id);
-                if (key < list.worst())
-                    list.insert(key);
-            }
+            process<LAYOUT>(nd, curr, ids, q, list);
         }
-        const float cull = list.cull();
         const float sd = __fsub_rn(select_dim<NC>(q, dim), select_dim<NC>(nd.c, dim));
         const float sd2 = __fmul_rn(sd, sd);
         const int lc = 2 * curr + 1;
         const int parent = (curr - 1) >> 1;  // -1 for the root
         int next;
-        if constexpr (ORDERED) {
-            const int close_side = sd > 0.f;
-            const int close_child = lc + close_side;
-            const int far_child = lc + 1 - close_side;
-            const bool far_ok = sd2 <= cull && far_child < N;
-            if (from_parent)
-                next = close_child < N ? close_child : (far_ok ? far_child : parent);
-            else if (prev == close_child)
-                next = far_ok ? far_child : parent;
-            else
-                next = parent;
-        } else {
+        if (from_parent && lc < N && 2 * lc + 1 >= N) {
+            // both children are leaves (the right one may be missing)
             const int rc = lc + 1;
-            const bool left_ok = (sd <= 0.f || sd2 <= cull) && lc < N;
-            const bool right_ok = (sd > 0.f || sd2 <= cull) && rc < N;
-            if (from_parent)
-                next = left_ok ? lc : (right_ok ? rc : parent);
-            else if (prev == lc)
-                next = right_ok ? rc : parent;
-            else
-                next = parent;
+            if constexpr (ORDERED) {
+                const int close_side = sd > 0.f;
+                const int close_child = lc + close_side;
+                const int far_child = lc + 1 - close_side;
+                if (close_child < N) {
+                    ++visits;
+                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, close_child), close_child, ids, q, list);
+                }
+                if (far_child < N && sd2 <= list.cull()) {
+                    ++visits;
+                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, far_child), far_child, ids, q, list);
+                }
+            } else {
+                if (sd <= 0.f || sd2 <= list.cull()) {
+                    ++visits;
+                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc), lc, ids, q, list);
+                }
+                if (rc < N && (sd > 0.f || sd2 <= list.cull())) {
+                    ++visits;
+                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, rc), rc, ids, q, list);
+                }
+            }
+            next = parent;
+        } else {
+            const float cull = list.cull();
+            if constexpr (ORDERED) {
+                const int close_side = sd > 0.f;
+                const int close_child = lc + close_side;
+                const int far_child = lc + 1 - close_side;
+                const bool far_ok = sd2 <= cull && far_child < N;
+                if (from_parent)
+                    next = close_child < N ? close_child : (far_ok ? far_child : parent);
+                else if (prev == close_child)
+                    next = far_ok ? far_child : parent;
+                else
+                    next = parent;
+            } else {
+                const int rc = lc + 1;
+                const bool left_ok = (sd <= 0.f || sd2 <= cull) && lc < N;
+                const bool right_ok = (sd > 0.f || sd2 <= cull) && rc < N;
+                if (from_parent)
+                    next = left_ok ? lc : (right_ok ? rc : parent);
+                else if (prev == lc)
+                    next = right_ok ? rc : parent;
+                else
+                    next = parent;
+            }
         }
         if (next < 0)
-            return visits;
+            return true;
         if (next == parent)
             dim = dim == 0 ? D - 1 : dim - 1;
         else
             dim = dim + 1 == D ? 0 : dim + 1;
         prev = curr;
         curr = next;
+        return false;
     }
+};
+
+// Whole traversal of one query; returns the number of processed nodes (first
+// visits), or -1 if the step bound was exceeded (impossible for a valid tree).
+template <int LAYOUT, bool ORDERED, class List>
+__device__ __forceinline__ int traverse(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
+                                        const float4 *s_nodes, int staged, int N, int D,
+                                        const float (&q)[LayoutTraits<LAYOUT>::NC], List &list)
+{
+    Walker<LAYOUT, ORDERED> w;
+    w.start();
+    int visits = 0;
+    bool overflow = false;
+    while (!w.template step<true>(nodes, ids, s_nodes, staged, N, D, q, list, visits, overflow)) {
+    }
+    return overflow ? -1 : visits;
 }
 
 template <int LAYOUT>
@@ -261,6 +335,13 @@ __device__ __forceinline__ void stage_nodes(const float4 *__restrict__ nodes, fl
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
     for (int i = threadIdx.x; i < staged * NF; i += blockDim.x)
         s_nodes[i] = ldg_f4(nodes + i);
+}
+
+__device__ __forceinline__ uint32_t lane_mask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
 }
 
 }  // namespace kdt

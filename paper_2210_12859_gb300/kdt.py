@@ -88,6 +88,10 @@ _sig("kdt_knn_batched", [_P, _P, _P, _I, _F, _I, _P, _P, _P])
 _sig("kdt_forest_export", [_P, _P, _P, _P])
 _sig("kdt_forest_free", [_P], None)
 _sig("kdt_profile_enable", [_P, _I])
+_sig("kdt_set_stage_levels", [_P, _I])
+_sig("kdt_autotune", [_P, _P, _I64, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
+_sig("kdt_tuning_save", [ctypes.c_char_p])
+_sig("kdt_tuning_load", [ctypes.c_char_p])
 _sig("kdt_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
 
 _OPTIONAL = {}
@@ -314,6 +318,28 @@ def kdt_knn_host(points, queries, k: int, max_radius: float = math.inf, flags: i
     dp, _ = _host(out_d2, np.float32, "out_d2")
     _check(_lib.kdt_knn_host(pp, N, D, qp, Q, k, float(max_radius), flags, ip, dp))
     return out_ids, out_d2
+
+
+def kdt_set_stage_levels(tree: Tree, levels: int) -> None:
+    _check(_lib.kdt_set_stage_levels(tree.handle, int(levels)))
+
+
+def kdt_autotune(tree: Tree, queries: torch.Tensor, k: int, flags: int = 0, stream=None):
+    """Measure the staging depths on these queries; returns (levels, ms)."""
+    Q = queries.shape[0]
+    lv = _I()
+    ms = _F()
+    _check(_lib.kdt_autotune(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, k, flags,
+                             ctypes.byref(lv), ctypes.byref(ms), _stream(stream)))
+    return lv.value, ms.value
+
+
+def kdt_tuning_save(path: str) -> None:
+    _check(_lib.kdt_tuning_save(os.fsencode(path)))
+
+
+def kdt_tuning_load(path: str) -> None:
+    _check(_lib.kdt_tuning_load(os.fsencode(path)))
 
 
 def kdt_profile_enable(tree: Tree, enable: bool = True) -> None:
