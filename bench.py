@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--log2n", type=int, default=LOG2N, help="log2 of N = Q (default 24)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", default="gmm_large",
+                    choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched"],
+                    help="gmm_large: the contract line; the others print one JSON line per measured form")
     return ap.parse_args()
 
 
@@ -226,6 +229,11 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        return
+    if args.config != "gmm_large":
+        from bench_configs import run_config
+
+        run_config(args)
         return
 
     import torch

@@ -1,0 +1,148 @@
+"""Secondary measurements of bench.py (--config ...): the other workloads,
+each printed as one JSON line per measured form.  The contract line
+(default config) is produced by bench.py itself."""
+from __future__ import annotations
+
+import json
+import math
+import statistics
+import time
+
+import numpy as np
+
+
+def _timer(torch):
+    stream = torch.cuda.current_stream()
+
+    def timeit(fn, reps=3, warm=1):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    return timeit
+
+
+def _exact(oracle, pts, qs, gi, gd, k, r=math.inf, n=64, seed=0):
+    idx = np.sort(np.random.default_rng(seed).choice(len(qs), size=min(n, len(qs)), replace=False))
+    wi, wd = oracle.knn_brute_threaded(pts, qs[idx], k, r)
+    return bool(np.array_equal(gi[idx], wi) and np.array_equal(gd[idx].view(np.uint32), wd.view(np.uint32)))
+
+
+def _emit(**kw):
+    print(json.dumps(kw), flush=True)
+
+
+def run_config(args):
+    import torch
+
+    import oracle
+    from paper_2210_12859_gb300 import kdt, synth
+
+    torch.cuda.set_device(0)
+    timeit = _timer(torch)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+
+    if args.config == "uniform_small":
+        pts, qs = synth.uniform_small()
+        dp, dq = cu(pts), cu(qs)
+        tree = kdt.kdt_build(dp)
+        build_ms = timeit(lambda: kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC), 5)
+        for k in (1, 8):
+            for name, fl in (("ordered", kdt.KDT_MORTON), ("unordered", kdt.KDT_MORTON | kdt.KDT_UNORDERED)):
+                ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, flags=fl), 5)
+                gi, gd = kdt.kdt_knn(tree, dq, k, flags=fl)
+                v = kdt.kdt_knn_visits(tree, dq, k, flags=fl).double().mean().item()
+                wi, wd = oracle.knn_brute(pts, qs, k)
+                _emit(config="uniform_small N=Q=2^14", form=f"{'fcp' if k == 1 else 'kNN k=8'} {name}",
+                      query_qps=len(qs) / (ms / 1e3), query_ms=ms, build_ms=build_ms, visits_per_query=v,
+                      bit_exact_full=bool(np.array_equal(gi.cpu().numpy().reshape(wi.shape), wi) and np.array_equal(
+                          gd.cpu().numpy().reshape(wd.shape).view(np.uint32), wd.view(np.uint32))))
+        return
+
+    if args.config == "dims":
+        n = 1 << 22
+        sets = [(f"uniform D={D}", *synth.uniform_dim(n, n, D)) for D in (2, 4, 8)]
+        sets.append(("surface D=3", *synth.surface_set(n, n)))
+        for name, pts, qs in sets:
+            dp, dq = cu(pts), cu(qs)
+            tree = kdt.kdt_build(dp)
+            build_ms = timeit(lambda: kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC), 3)
+            ms = timeit(lambda: kdt.kdt_knn(tree, dq, 16, flags=kdt.KDT_MORTON), 2)
+            gi, gd = kdt.kdt_knn(tree, dq, 16, flags=kdt.KDT_MORTON)
+            v = kdt.kdt_knn_visits(tree, dq, 16, flags=kdt.KDT_MORTON).double().mean().item()
+            _emit(config="dims N=Q=2^22 kNN k=16 ordered", form=name, query_qps=n / (ms / 1e3), query_ms=ms,
+                  build_ms=build_ms, visits_per_query=v,
+                  bit_exact_sample=_exact(oracle, pts, qs, gi.cpu().numpy(), gd.cpu().numpy(), 16))
+            del tree
+        return
+
+    if args.config == "surface_learned":
+        n = 1 << 24
+        sh = synth.surface_shapes(256, synth.BASE_SEED + 4)
+        pts = synth.surface_sample(sh, n, synth.BASE_SEED + 41)
+        train = synth.surface_sample(sh, 1 << 20, synth.BASE_SEED + 42)
+        qs = synth.surface_sample(sh, n, synth.BASE_SEED + 43)
+        dp, dq, dt = cu(pts), cu(qs), cu(train)
+        tree = kdt.kdt_build(dp)
+        for k in (8, 32):
+            t0 = time.perf_counter()
+            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=6, seed=1)
+            train_s = time.perf_counter() - t0
+            out_i = torch.empty((n, k), dtype=torch.int32, device="cuda")
+            out_d = torch.empty((n, k), dtype=torch.float32, device="cuda")
+            li = torch.empty_like(out_i)
+            ld = torch.empty_like(out_d)
+            plain_ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, kdt.KDT_MORTON, out_i, out_d), 2)
+            learned_ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, kdt.KDT_MORTON | kdt.KDT_LEARNED, li, ld), 2)
+            fb, ratio = kdt.kdt_learned_stats(tree)
+            pv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON).double().mean().item()
+            lv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON | kdt.KDT_LEARNED).double().mean().item()
+            same = bool(torch.equal(li, out_i) and torch.equal(ld.view(torch.int32), out_d.view(torch.int32)))
+            _emit(config="surface_learned N=Q=2^24 (256 spheres/tori)", form=f"kNN k={k} plain vs learned",
+                  plain_qps=n / (plain_ms / 1e3), learned_qps=n / (learned_ms / 1e3),
+                  speedup=plain_ms / learned_ms, fallback_rate=fb / n, radius_ratio=ratio,
+                  plain_visits=pv, learned_visits=lv, identical=same, train_s=train_s, train_loss=loss,
+                  bit_exact_sample=_exact(oracle, pts, qs, out_i.cpu().numpy(), out_d.cpu().numpy(), k))
+        return
+
+    if args.config == "batched":
+        c = synth.clouds(4096, seed=synth.BASE_SEED + 5)
+        dp, dq = cu(c.points), cu(c.queries)
+        Q = len(c.queries)
+        t0 = time.perf_counter()
+        forest = kdt.kdt_build_batched(dp, c.offsets)
+        build_s = time.perf_counter() - t0
+        out_i = torch.empty((Q, 8), dtype=torch.int32, device="cuda")
+        out_d = torch.empty((Q, 8), dtype=torch.float32, device="cuda")
+        res = {}
+        for name, fl in (("one persistent graph launch, Morton order", kdt.KDT_MORTON),
+                         ("one persistent graph launch", 0),
+                         ("one launch per tree", kdt.KDT_PER_TREE)):
+            ms = timeit(lambda: kdt.kdt_knn_batched(forest, dq, c.qoffsets, 8, math.inf, fl, out_i, out_d), 2)
+            res[name] = (ms, out_i.clone(), out_d.clone())
+        same = all(torch.equal(res[a][1], res["one launch per tree"][1]) and
+                   torch.equal(res[a][2], res["one launch per tree"][2]) for a in res)
+        # sampled oracle check on a few clouds
+        gi = out_i.cpu().numpy()
+        gd = out_d.cpu().numpy()
+        ok = True
+        for t in (0, 1000, 4095):
+            p = c.points[c.offsets[t]:c.offsets[t + 1]]
+            q = c.queries[c.qoffsets[t]:c.qoffsets[t + 1]]
+            wi, wd = oracle.knn_brute(p, q[:64], 8)
+            ok &= bool(np.array_equal(gi[c.qoffsets[t]:c.qoffsets[t] + len(wi)], wi))
+        for name, (ms, _, _) in res.items():
+            _emit(config=f"batched: 4096 clouds, {int(c.offsets[-1])} points, {Q} queries, kNN k=8", form=name,
+                  query_qps=Q / (ms / 1e3), query_ms=ms, forest_build_s=build_s, identical_forms=same,
+                  bit_exact_sample=ok)
+        return

@@ -197,11 +197,16 @@ __device__ __forceinline__ void process(const NodeVal<LAYOUT> &nd, int n, const 
 //  * a missing child is never stepped into: stepping into it and straight back
 //    only sets prev to that child, so the machine continues as if it had been
 //    visited;
-//  * when a node's children are leaves (or missing), they are processed in the
-//    node's own step, in the order the machine would visit them (close child,
-//    then far child if the plane is still within the cull radius; unordered:
-//    left then right, each if in range), and the step returns to the parent -
-//    exactly the four steps into and out of the leaves, without them.
+//  * when the subtree below a node is at most INLINE_DEPTH levels deep, it is
+//    processed in the node's own step, in the order the machine would visit
+//    it (close child, its subtree, then the far child and its subtree if the
+//    plane is still within the cull radius; unordered: left then right, each
+//    if in range), and the step returns to the parent - the same processed
+//    nodes in the same order, without the steps into and out of them.
+// Depth of the bottom subtrees processed inside one step (1: a node whose
+// children are leaves; 2: also a node whose grandchildren are leaves).
+constexpr int INLINE_DEPTH = 2;
+
 template <int LAYOUT, bool ORDERED>
 struct Walker {
     static constexpr int NC = LayoutTraits<LAYOUT>::NC;
@@ -214,6 +219,55 @@ struct Walker {
         prev = -1;
         dim = 0;
         steps = 0;
+    }
+
+    // children lc, lc+1 of a node whose split offset is sd are leaves (or
+    // missing): process them in the order the machine visits them
+    template <bool STAGE, class List>
+    __device__ __forceinline__ void leaf_pair(float sd, float sd2, int lc, const float4 *__restrict__ nodes,
+                                              const int32_t *__restrict__ ids, const float4 *s_nodes, int staged,
+                                              int N, const float (&q)[NC], List &list, int &visits)
+    {
+        const int rc = lc + 1;
+        if constexpr (ORDERED) {
+            const int close_side = sd > 0.f;
+            const int close_child = lc + close_side;
+            const int far_child = lc + 1 - close_side;
+            if (close_child < N) {
+                ++visits;
+                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, close_child), close_child, ids, q, list);
+            }
+            if (far_child < N && sd2 <= list.cull()) {
+                ++visits;
+                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, far_child), far_child, ids, q, list);
+            }
+        } else {
+            if (sd <= 0.f || sd2 <= list.cull()) {
+                ++visits;
+                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc), lc, ids, q, list);
+            }
+            if (rc < N && (sd > 0.f || sd2 <= list.cull())) {
+                ++visits;
+                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, rc), rc, ids, q, list);
+            }
+        }
+    }
+
+    // node c (split dimension dimc) whose children are leaves: process it,
+    // then its children
+    template <bool STAGE, class List>
+    __device__ __forceinline__ void inline_pair(int c, int dimc, const float4 *__restrict__ nodes,
+                                                const int32_t *__restrict__ ids, const float4 *s_nodes, int staged,
+                                                int N, const float (&q)[NC], List &list, int &visits)
+    {
+        const NodeVal<LAYOUT> nc = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, c);
+        ++visits;
+        process<LAYOUT>(nc, c, ids, q, list);
+        const int lcc = 2 * c + 1;
+        if (lcc < N) {
+            const float sdc = __fsub_rn(select_dim<NC>(q, dimc), select_dim<NC>(nc.c, dimc));
+            leaf_pair<STAGE>(sdc, __fmul_rn(sdc, sdc), lcc, nodes, ids, s_nodes, staged, N, q, list, visits);
+        }
     }
 
     // one step; returns true when the traversal has finished (or exceeded
@@ -239,31 +293,30 @@ struct Walker {
         const int lc = 2 * curr + 1;
         const int parent = (curr - 1) >> 1;  // -1 for the root
         int next;
-        if (from_parent && lc < N && 2 * lc + 1 >= N) {
-            // both children are leaves (the right one may be missing)
-            const int rc = lc + 1;
+        const int rc = lc + 1;
+        if (INLINE_DEPTH >= 2 && from_parent && lc < N && 2 * lc + 1 < N &&
+            2u * (2u * (uint32_t)lc + 1u) + 1u >= (uint32_t)N) {
+            // the children have only leaves below them: the whole depth-2
+            // subtree, in the machine's order
+            const int dim1 = dim + 1 == D ? 0 : dim + 1;
             if constexpr (ORDERED) {
                 const int close_side = sd > 0.f;
                 const int close_child = lc + close_side;
                 const int far_child = lc + 1 - close_side;
-                if (close_child < N) {
-                    ++visits;
-                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, close_child), close_child, ids, q, list);
-                }
-                if (far_child < N && sd2 <= list.cull()) {
-                    ++visits;
-                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, far_child), far_child, ids, q, list);
-                }
+                if (close_child < N)
+                    inline_pair<STAGE>(close_child, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
+                if (far_child < N && sd2 <= list.cull())
+                    inline_pair<STAGE>(far_child, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
             } else {
-                if (sd <= 0.f || sd2 <= list.cull()) {
-                    ++visits;
-                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc), lc, ids, q, list);
-                }
-                if (rc < N && (sd > 0.f || sd2 <= list.cull())) {
-                    ++visits;
-                    process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, rc), rc, ids, q, list);
-                }
+                if (sd <= 0.f || sd2 <= list.cull())
+                    inline_pair<STAGE>(lc, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
+                if (rc < N && (sd > 0.f || sd2 <= list.cull()))
+                    inline_pair<STAGE>(rc, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
             }
+            next = parent;
+        } else if (from_parent && lc < N && 2 * lc + 1 >= N) {
+            // both children are leaves (the right one may be missing)
+            leaf_pair<STAGE>(sd, sd2, lc, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
         } else {
             const float cull = list.cull();
