@@ -221,52 +221,65 @@ struct Walker {
         steps = 0;
     }
 
-    // children lc, lc+1 of a node whose split offset is sd are leaves (or
-    // missing): process them in the order the machine visits them
-    template <bool STAGE, class List>
-    __device__ __forceinline__ void leaf_pair(float sd, float sd2, int lc, const float4 *__restrict__ nodes,
-                                              const int32_t *__restrict__ ids, const float4 *s_nodes, int staged,
-                                              int N, const float (&q)[NC], List &list, int &visits)
+    template <class T>
+    __device__ __forceinline__ static T pick(bool c, const T &x, const T &y)
+    {
+        T r;
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            r.c[j] = c ? x.c[j] : y.c[j];
+        r.id = c ? x.id : y.id;
+        return r;
+    }
+
+    // Leaves lc (value a) and lc+1 (value b, valid iff lc+1 < N) below a node
+    // whose split offset is sd: process them in the order the machine visits
+    // them.  The values were loaded before, both at once.
+    template <class List>
+    __device__ __forceinline__ void leaf_pair(float sd, float sd2, int lc, const NodeVal<LAYOUT> &a,
+                                              const NodeVal<LAYOUT> &b, const int32_t *__restrict__ ids, int N,
+                                              const float (&q)[NC], List &list, int &visits)
     {
         const int rc = lc + 1;
+        const bool rc_ok = rc < N;
         if constexpr (ORDERED) {
-            const int close_side = sd > 0.f;
-            const int close_child = lc + close_side;
-            const int far_child = lc + 1 - close_side;
-            if (close_child < N) {
+            const bool right_first = sd > 0.f;
+            const NodeVal<LAYOUT> first = pick(right_first, b, a);
+            const NodeVal<LAYOUT> second = pick(right_first, a, b);
+            if (!right_first || rc_ok) {
                 ++visits;
-                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, close_child), close_child, ids, q, list);
+                process<LAYOUT>(first, right_first ? rc : lc, ids, q, list);
             }
-            if (far_child < N && sd2 <= list.cull()) {
+            if ((right_first || rc_ok) && sd2 <= list.cull()) {
                 ++visits;
-                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, far_child), far_child, ids, q, list);
+                process<LAYOUT>(second, right_first ? lc : rc, ids, q, list);
             }
         } else {
             if (sd <= 0.f || sd2 <= list.cull()) {
                 ++visits;
-                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc), lc, ids, q, list);
+                process<LAYOUT>(a, lc, ids, q, list);
             }
-            if (rc < N && (sd > 0.f || sd2 <= list.cull())) {
+            if (rc_ok && (sd > 0.f || sd2 <= list.cull())) {
                 ++visits;
-                process<LAYOUT>(fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, rc), rc, ids, q, list);
+                process<LAYOUT>(b, rc, ids, q, list);
             }
         }
     }
 
-    // node c (split dimension dimc) whose children are leaves: process it,
-    // then its children
-    template <bool STAGE, class List>
-    __device__ __forceinline__ void inline_pair(int c, int dimc, const float4 *__restrict__ nodes,
-                                                const int32_t *__restrict__ ids, const float4 *s_nodes, int staged,
-                                                int N, const float (&q)[NC], List &list, int &visits)
+    // node c (value nc, split dimension dimc) whose children are leaves (values
+    // ga, gb, loaded before): process it, then its children
+    template <class List>
+    __device__ __forceinline__ void leaf_parent(int c, int dimc, const NodeVal<LAYOUT> &nc,
+                                                const NodeVal<LAYOUT> &ga, const NodeVal<LAYOUT> &gb,
+                                                const int32_t *__restrict__ ids, int N, const float (&q)[NC],
+                                                List &list, int &visits)
     {
-        const NodeVal<LAYOUT> nc = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, c);
         ++visits;
         process<LAYOUT>(nc, c, ids, q, list);
         const int lcc = 2 * c + 1;
         if (lcc < N) {
             const float sdc = __fsub_rn(select_dim<NC>(q, dimc), select_dim<NC>(nc.c, dimc));
-            leaf_pair<STAGE>(sdc, __fmul_rn(sdc, sdc), lcc, nodes, ids, s_nodes, staged, N, q, list, visits);
+            leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ga, gb, ids, N, q, list, visits);
         }
     }
 
@@ -297,26 +310,40 @@ struct Walker {
         if (INLINE_DEPTH >= 2 && from_parent && lc < N && 2 * lc + 1 < N &&
             2u * (2u * (uint32_t)lc + 1u) + 1u >= (uint32_t)N) {
             // the children have only leaves below them: the whole depth-2
-            // subtree, in the machine's order
+            // subtree in the machine's order.  Its six node indices are known
+            // from curr alone, so all loads are issued first (indices clamped
+            // to N-1; values of missing nodes are never used).
+            const int last = N - 1;
+            const int g0 = 2 * lc + 1;
+            const NodeVal<LAYOUT> c0 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
+            const NodeVal<LAYOUT> c1 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(rc, last));
+            const NodeVal<LAYOUT> g00 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, g0);
+            const NodeVal<LAYOUT> g01 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 1, last));
+            const NodeVal<LAYOUT> g10 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 2, last));
+            const NodeVal<LAYOUT> g11 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 3, last));
             const int dim1 = dim + 1 == D ? 0 : dim + 1;
+            const bool rc_ok = rc < N;
             if constexpr (ORDERED) {
-                const int close_side = sd > 0.f;
-                const int close_child = lc + close_side;
-                const int far_child = lc + 1 - close_side;
-                if (close_child < N)
-                    inline_pair<STAGE>(close_child, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
-                if (far_child < N && sd2 <= list.cull())
-                    inline_pair<STAGE>(far_child, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
+                const bool right_first = sd > 0.f;
+                if (!right_first || rc_ok)
+                    leaf_parent(right_first ? rc : lc, dim1, pick(right_first, c1, c0), pick(right_first, g10, g00),
+                                pick(right_first, g11, g01), ids, N, q, list, visits);
+                if ((right_first || rc_ok) && sd2 <= list.cull())
+                    leaf_parent(right_first ? lc : rc, dim1, pick(right_first, c0, c1), pick(right_first, g00, g10),
+                                pick(right_first, g01, g11), ids, N, q, list, visits);
             } else {
                 if (sd <= 0.f || sd2 <= list.cull())
-                    inline_pair<STAGE>(lc, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
-                if (rc < N && (sd > 0.f || sd2 <= list.cull()))
-                    inline_pair<STAGE>(rc, dim1, nodes, ids, s_nodes, staged, N, q, list, visits);
+                    leaf_parent(lc, dim1, c0, g00, g01, ids, N, q, list, visits);
+                if (rc_ok && (sd > 0.f || sd2 <= list.cull()))
+                    leaf_parent(rc, dim1, c1, g10, g11, ids, N, q, list, visits);
             }
             next = parent;
         } else if (from_parent && lc < N && 2 * lc + 1 >= N) {
-            // both children are leaves (the right one may be missing)
-            leaf_pair<STAGE>(sd, sd2, lc, nodes, ids, s_nodes, staged, N, q, list, visits);
+            // both children are leaves (the right one may be missing): both
+            // loads first
+            const NodeVal<LAYOUT> a = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
+            const NodeVal<LAYOUT> b = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(rc, N - 1));
+            leaf_pair(sd, sd2, lc, a, b, ids, N, q, list, visits);
             next = parent;
         } else {
             const float cull = list.cull();
