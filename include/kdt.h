@@ -52,8 +52,10 @@ extern "C" {
                               side or the splitting plane is within the cull radius
                               (Sec. 3: unordered traversal as a simplification) */
 #define KDT_MORTON     0x2 /* sort queries along a 30-bit Morton curve before traversal so
-                              that the threads of a warp walk nearby paths; results are
-                              written to the caller's query order */
+                              that the threads of a warp walk nearby paths (single trees with
+                              D <= 3: within four cost classes, most expensive first, judged by
+                              how far the greedy descent ends from its leaf point); results
+                              are written to the caller's query order */
 #define KDT_LEARNED    0x4 /* seed each query's cull radius with the trained radius model
                               and re-run the queries that find fewer than k points with
                               the caller's radius (not in the paper; results unchanged) */

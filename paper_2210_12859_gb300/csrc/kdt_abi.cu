@@ -12,6 +12,7 @@
 
 #include "kdt_learned.cuh"
 #include "kdt_query.cuh"
+#include "kdt_traverse.cuh"
 
 namespace kdt {
 
@@ -125,11 +126,22 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
 }
 
 // 30-bit Morton code of the first min(D,3) coordinates quantised to 10 bits
-// inside the bounding box of the query's tree
+// inside the bounding box of the query's tree.  With `nodes` (a single tree
+// of D <= 3), the two bits above the code hold a cost class, most expensive
+// first: a query whose greedy descent ends far from its leaf point, relative
+// to the tree's mean point spacing, lies outside the data and processes many
+// nodes; starting those first keeps them out of the end of the launch.
 __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, const float *__restrict__ bbox, int T,
-                              const int64_t *__restrict__ q_off, uint32_t *__restrict__ keys,
-                              uint32_t *__restrict__ vals)
+                              const int64_t *__restrict__ q_off, const float4 *__restrict__ nodes, int64_t N,
+                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
+    float spacing2 = 0.f;
+    if (nodes) {
+        float vol = 1.f;
+        for (int j = 0; j < D; ++j)
+            vol *= fmaxf(bbox[3 + j] - bbox[j], 1e-30f);
+        spacing2 = powf(vol / (float)N, 2.f / (float)D);
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
         int t = 0;
         if (T > 1) {
@@ -151,6 +163,13 @@ __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, co
             x = fminf(fmaxf(x, 0.f), 1.f);
             uint32_t c = (uint32_t)fminf(x * 1024.f, 1023.f);
             code |= spread3(c) << (2 - j);
+        }
+        if (nodes) {
+            float q[3];
+            load_query<0>(qs, i, D, q);
+            const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q) / spacing2;
+            const uint32_t cls = r > 64.f ? 0u : (r > 8.f ? 1u : (r > 1.f ? 2u : 3u));  // NaN: 3
+            code |= cls << 30;
         }
         keys[i] = code;
         vals[i] = (uint32_t)i;
@@ -188,7 +207,7 @@ size_t morton_scratch_bytes(int64_t Q)
 // permutation of the queries along the Morton curve (stable: equal codes keep
 // their index order); perm receives traversal order -> query index
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 void *scratch, uint32_t **perm_out, cudaStream_t s)
+                 const float4 *nodes, int64_t N, void *scratch, uint32_t **perm_out, cudaStream_t s)
 {
     Carve c{(char *)scratch};
     uint32_t *keys = c.take<uint32_t>(Q);
@@ -196,8 +215,10 @@ int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, c
     uint32_t *tk = c.take<uint32_t>(Q);
     uint32_t *tv = c.take<uint32_t>(Q);
     uint32_t *rs = c.take<uint32_t>(radix_scratch_elems(Q));
-    KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, keys, perm);
-    KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, 30, rs, s));
+    const bool cost = nodes && D <= 3 && T == 1;
+    KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, cost ? nodes : nullptr, N, keys,
+                                                        perm);
+    KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, cost ? 32 : 30, rs, s));
     if (T > 1) {
         KDT_LAUNCH tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
         KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, tbits, rs, s));
@@ -247,7 +268,8 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     unsigned long long *counter = c.take<unsigned long long>(8);
     QueryArgs a;
     if (morton)
-        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, c.base + c.off, const_cast<uint32_t **>(&a.perm),
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, c.base + c.off,
+                             const_cast<uint32_t **>(&a.perm),
                              s));
     a.nodes = t->nodes;
     a.ids = t->ids;
@@ -667,7 +689,7 @@ static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64
     QueryArgs a;
     if (flags & KDT_MORTON) {
         int tbits = T > 1 ? floor_log2((uint64_t)(T - 1)) + 1 : 0;
-        KDT_TRY(morton_order(d_q, Q, f->f.D, f->bbox, T, d_qoff, tbits, c.base + c.off,
+        KDT_TRY(morton_order(d_q, Q, f->f.D, f->bbox, T, d_qoff, tbits, nullptr, 0, c.base + c.off,
                              const_cast<uint32_t **>(&a.perm), s));
     }
     a.nodes = f->nodes;

@@ -28,7 +28,7 @@
 namespace kdt {
 
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 void *scratch, uint32_t **perm_out, cudaStream_t s);
+                 const float4 *nodes, int64_t N, void *scratch, uint32_t **perm_out, cudaStream_t s);
 size_t morton_scratch_bytes(int64_t Q);
 
 namespace {
@@ -58,24 +58,6 @@ __global__ void round_params_kernel(const float *__restrict__ master, float *__r
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P)
         rounded[i] = is_weight(i) ? bf16_round(master[i]) : master[i];
-}
-
-// greedy close-child descent; returns d2 to the last valid node
-__device__ __forceinline__ float descent_d2(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged, int N,
-                                            int D, const float (&q)[3])
-{
-    int node = 0, dim = 0;
-    NodeVal<0> nd = fetch<0>(nodes, s_nodes, staged, 0);
-    for (;;) {
-        const float sd = __fsub_rn(select_dim<3>(q, dim), select_dim<3>(nd.c, dim));
-        const int child = 2 * node + 1 + (sd > 0.f);
-        if (child >= N)
-            break;
-        node = child;
-        dim = dim + 1 == D ? 0 : dim + 1;
-        nd = fetch<0>(nodes, s_nodes, staged, node);
-    }
-    return dist2<3>(nd.c, q);
 }
 
 __device__ __forceinline__ float leaf_feature(float d2) { return logf(fmaxf(d2, 1e-30f)); }
@@ -125,7 +107,7 @@ __global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict_
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
         float q[3];
         load_query<0>(qs, i, D, q);
-        const float d2 = descent_d2(nodes, s_nodes, staged, N, D, q);
+        const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q);
         float4 f = make_float4(q[0], q[1], q[2], leaf_feature(d2));
         reinterpret_cast<float4 *>(feat)[i] = f;
     }
@@ -149,7 +131,7 @@ __global__ void __launch_bounds__(256) radius_kernel(const float4 *__restrict__ 
         const int64_t qi = perm ? (int64_t)perm[i] : i;
         float q[3];
         load_query<0>(qs, qi, D, q);
-        const float d2 = descent_d2(nodes, s_nodes, staged, N, D, q);
+        const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q);
         float x[4] = {q[0], q[1], q[2], leaf_feature(d2)};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -501,7 +483,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     uint32_t *fb_list = (uint32_t *)(B + off_fb);
     uint32_t *perm = nullptr;
     if (morton)
-        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, B + off_m, &perm, s));
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, B + off_m, &perm, s));
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
     Norm nm;
     model_norm(t, &nm);

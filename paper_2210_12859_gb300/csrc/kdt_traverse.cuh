@@ -417,6 +417,26 @@ __device__ __forceinline__ void stage_nodes(const float4 *__restrict__ nodes, fl
         s_nodes[i] = ldg_f4(nodes + i);
 }
 
+// Greedy close-child descent from the root (Sec. 3.2's closeSide rule at every
+// node) until that child does not exist; returns the FP32 squared distance to
+// the last node reached (layout 0 trees, D <= 3).
+__device__ __forceinline__ float descent_leaf_d2(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged,
+                                                 int N, int D, const float (&q)[3])
+{
+    int node = 0, dim = 0;
+    NodeVal<0> nd = fetch<0>(nodes, s_nodes, staged, 0);
+    for (;;) {
+        const float sd = __fsub_rn(select_dim<3>(q, dim), select_dim<3>(nd.c, dim));
+        const int child = 2 * node + 1 + (sd > 0.f);
+        if (child >= N)
+            break;
+        node = child;
+        dim = dim + 1 == D ? 0 : dim + 1;
+        nd = fetch<0>(nodes, s_nodes, staged, node);
+    }
+    return dist2<3>(nd.c, q);
+}
+
 __device__ __forceinline__ uint32_t lane_mask_lt()
 {
     uint32_t m;
