@@ -133,14 +133,18 @@ struct RegList {
     __device__ __forceinline__ bool full(int) const { return (uint32_t)L[K - 1] != EMPTY_ID; }
 };
 
-// Shared-memory sorted k-best list for 16 < k <= 64, one column per thread
-// (slot i of thread t at s[i * stride + t]: consecutive threads hit
-// consecutive banks).  The worst key is mirrored in a register.
+// Shared-memory k-best set for 16 < k <= 64: a binary max-heap of packed
+// (d2, id) keys per thread (slot i of thread t at s[i * stride + t], so
+// consecutive threads hit consecutive banks).  The root is the worst key, i.e.
+// the cull radius; an accepted key replaces the root and sifts down (log2 k
+// levels instead of k/2 shifts of a sorted list).  The k slots start at
+// (r2, EMPTY_ID) like the register list, which gives the same acceptance rule.
+// store() sorts the heap once (heapsort, ascending).
 struct SmemList {
     unsigned long long *s;
     int stride;
     int k;
-    unsigned long long w;
+    unsigned long long w;  // root (worst key) mirrored in a register
     __device__ __forceinline__ void init(int k_, float r2)
     {
         k = k_;
@@ -150,21 +154,44 @@ struct SmemList {
     }
     __device__ __forceinline__ float cull() const { return key_d2(w); }
     __device__ __forceinline__ unsigned long long worst() const { return w; }
+    // replace the root by c (c < root) and restore the heap on [0, n)
+    __device__ __forceinline__ static void sift(unsigned long long *h, int stride, int n, unsigned long long c)
+    {
+        int i = 0;
+        for (;;) {
+            const int l = 2 * i + 1;
+            if (l >= n)
+                break;
+            unsigned long long big = h[l * stride];
+            int j = l;
+            if (l + 1 < n) {
+                const unsigned long long r = h[(l + 1) * stride];
+                if (r > big) {
+                    big = r;
+                    j = l + 1;
+                }
+            }
+            if (!(big > c))
+                break;
+            h[i * stride] = big;
+            i = j;
+        }
+        h[i * stride] = c;
+    }
     __device__ __forceinline__ void insert(unsigned long long c)
     {
-        int pos = k - 1;
-        while (pos > 0) {
-            unsigned long long a = s[(pos - 1) * stride];
-            if (!(c < a))
-                break;
-            s[pos * stride] = a;
-            --pos;
-        }
-        s[pos * stride] = c;
-        w = s[(k - 1) * stride];
+        sift(s, stride, k, c);
+        w = s[0];
     }
-    __device__ __forceinline__ void store(int, int32_t *ids, float *d2) const
+    __device__ __forceinline__ void store(int, int32_t *ids, float *d2)
     {
+        // heapsort: move the maximum to the end, shrink, repeat
+        for (int n = k; n > 1; --n) {
+            const unsigned long long top = s[0];
+            const unsigned long long last = s[(n - 1) * stride];
+            s[(n - 1) * stride] = top;
+            sift(s, stride, n - 1, last);
+        }
         for (int i = 0; i < k; ++i) {
             unsigned long long key = s[i * stride];
             uint32_t id = (uint32_t)key;
@@ -173,6 +200,7 @@ struct SmemList {
             d2[i] = empty ? __int_as_float(0x7f800000) : key_d2(key);
         }
     }
+    // whether k points are held: the root is a real point
     __device__ __forceinline__ bool full(int) const { return (uint32_t)w != EMPTY_ID; }
 };
 
