@@ -104,6 +104,13 @@ int kdt_tree_info(const kdt_tree *tree, int64_t *N, int *D);
  * point at each node) and d_ids int32 [N] (its input index). */
 int kdt_tree_export(const kdt_tree *tree, float *d_coords, int32_t *d_ids, void *stream);
 
+/* Save a tree as its level-order arrays (coordinates, input indices, bounding
+ * box) with a header and a checksum; load it back as a new tree without
+ * rebuilding (synchronous; KDT_EIO for a missing, foreign or damaged file).
+ * A radius model is not part of the tree file (kdt_radius_model_save). */
+int kdt_tree_save(const kdt_tree *tree, const char *path);
+int kdt_tree_load(const char *path, void *stream, kdt_tree **out);
+
 /* Find-closest-point (Sec. 4, fcp): kNN with k = 1.
  *   d_queries float32 [Q][D]; d_ids int32 [Q]; d_d2 float32 [Q]. */
 int kdt_fcp(const kdt_tree *tree, const float *d_queries, int64_t Q, float max_radius,

@@ -345,7 +345,7 @@ const char *kdt_last_error(void) { return g_err; }
 
 int64_t kdt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-static int alloc_tree(int64_t N, int D, kdt_tree **out)
+__attribute__((visibility("hidden"))) int kdt_tree_alloc_internal(int64_t N, int D, kdt_tree **out)
 {
     kdt_tree *t = new (std::nothrow) kdt_tree();
     if (!t)
@@ -406,7 +406,7 @@ int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream
     pool_setup_once();
     cudaStream_t s = (cudaStream_t)stream;
     kdt_tree *t = nullptr;
-    KDT_TRY(alloc_tree(N, D, &t));
+    KDT_TRY(kdt_tree_alloc_internal(N, D, &t));
     int64_t off[2] = {0, N};
     int rc = build_forest(d_points, off, 1, D, t->nodes, t->ids, t->bbox, t->err, s);
     if (rc == KDT_OK)

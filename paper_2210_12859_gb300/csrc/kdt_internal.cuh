@@ -197,6 +197,9 @@ struct kdt_forest {
     void *graph = nullptr;         // cached graph of the batched query
 };
 
+// allocate an empty tree object with device arrays for N nodes of dimension D
+extern "C" int kdt_tree_alloc_internal(int64_t N, int D, kdt_tree **out);
+
 namespace kdt {
 // staging depth (levels) for a query on tree t with k neighbours: the tree's
 // own setting, else the tuned value for its shape, else the default

@@ -76,6 +76,8 @@ _sig("kdt_build_ex", [_P, _I64, _I, _I, _P, ctypes.POINTER(_P)])
 _sig("kdt_rebuild", [_P, _P, _I, _P])
 _sig("kdt_tree_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I)])
 _sig("kdt_tree_export", [_P, _P, _P, _P])
+_sig("kdt_tree_save", [_P, ctypes.c_char_p])
+_sig("kdt_tree_load", [ctypes.c_char_p, _P, ctypes.POINTER(_P)])
 _sig("kdt_fcp", [_P, _P, _I64, _F, _I, _P, _P, _P])
 _sig("kdt_knn", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
 _sig("kdt_knn_visits", [_P, _P, _I64, _I, _F, _I, _P, _P])
@@ -239,6 +241,16 @@ def kdt_tree_export(tree: Tree, stream=None):
     _check(_lib.kdt_tree_export(tree.handle, ctypes.c_void_p(coords.data_ptr()), ctypes.c_void_p(ids.data_ptr()),
                                 _stream(stream)))
     return coords, ids
+
+
+def kdt_tree_save(tree: Tree, path: str) -> None:
+    _check(_lib.kdt_tree_save(tree.handle, os.fsencode(path)))
+
+
+def kdt_tree_load(path: str, stream=None) -> Tree:
+    h = _P()
+    _check(_lib.kdt_tree_load(os.fsencode(path), _stream(stream), ctypes.byref(h)))
+    return Tree(h)
 
 
 def _outputs(Q, k, out_ids, out_d2, dev):

@@ -84,6 +84,25 @@ def test_rebuild_reuses_tree(kdt):
     assert np.array_equal(ids.cpu().numpy(), oracle.build(b))
 
 
+def test_tree_save_load_roundtrip(kdt, tmp_path):
+    pts, qs = synth.uniform_small(5000, 2000)
+    tree = kdt.kdt_build(cu(pts))
+    path = str(tmp_path / "tree.kdt")
+    kdt.kdt_tree_save(tree, path)
+    back = kdt.kdt_tree_load(path)
+    a, b = kdt.kdt_tree_export(tree), kdt.kdt_tree_export(back)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    ra = kdt.kdt_knn(tree, cu(qs), 8, flags=kdt.KDT_MORTON)
+    rb = kdt.kdt_knn(back, cu(qs), 8, flags=kdt.KDT_MORTON)
+    assert torch.equal(ra[0], rb[0]) and torch.equal(ra[1], rb[1])
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 1
+    open(path, "wb").write(bytes(raw))
+    with pytest.raises(kdt.KdtError) as e:
+        kdt.kdt_tree_load(path)
+    assert e.value.code == kdt.KDT_EIO
+
+
 def test_build_rejects_bad_input(kdt):
     pts = np.zeros((10, 3), dtype=np.float32)
     pts[4, 2] = np.inf
