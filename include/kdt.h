@@ -207,7 +207,10 @@ int kdt_descent_features(const kdt_tree *tree, const float *d_queries, int64_t Q
                          float *d_feat, void *stream);
 
 /* Model forward on normalised features: d_x float32 [n][4] -> d_y float32 [n],
- * using h_params as given (FP32, rounded to BF16 by the kernel). */
+ * the inference path of the learned query: h_params (FP32) with weights
+ * rounded to BF16; layer 1 in FP32, hidden activations rounded to BF16, the
+ * 64 x 64 layer on the tensor cores (tcgen05.mma, FP32 accumulation), output
+ * layer in FP32.  Synchronous. */
 int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d_y, void *stream);
 
 /* Mean squared error of the model on (d_x, d_label) and its gradient with

@@ -69,6 +69,8 @@ def _load():
         lib.orc_round_bf16.restype = f32
         lib.orc_mlp_forward.argtypes = [P, i32, P, i64, P]
         lib.orc_mlp_forward.restype = None
+        lib.orc_mlp_forward_bf16act.argtypes = [P, i32, P, i64, P]
+        lib.orc_mlp_forward_bf16act.restype = None
         lib.orc_mlp_loss_grad.argtypes = [P, i32, P, P, i64, P]
         lib.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
@@ -226,6 +228,16 @@ def mlp_forward(params, H: int, x) -> np.ndarray:
     xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
     y = np.empty(xs.shape[0], dtype=np.float64)
     _load().orc_mlp_forward(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y))
+    return y
+
+
+def mlp_forward_bf16act(params, H: int, x) -> np.ndarray:
+    """Forward of the tensor-core inference path: FP32 fused layer 1, hidden
+    activations rounded to bfloat16, the rest exact (FP64)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    xs = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+    y = np.empty(xs.shape[0], dtype=np.float64)
+    _load().orc_mlp_forward_bf16act(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y))
     return y
 
 

@@ -25,7 +25,9 @@
  *   orc_descent_leaf    greedy close-child descent (feature of the learned
  *                       radius proposal; not in the paper)
  *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
- *                       paper; parity target for the GPU training kernels)
+ *                       paper; parity target for the GPU training kernels),
+ *                       and the forward with BF16 hidden activations (parity
+ *                       target for the tensor-core inference kernel)
  *
  * Parity status: every function above is pinned by tests under tests/ against
  * values fixed by the paper (the six-point example of Figure 1), closed forms,
@@ -598,4 +600,40 @@ double orc_mlp_loss_grad(const double *params, int H, const double *x,
     free(g2);
     free(g1);
     return loss / (double)n;
+}
+
+/* Forward pass of the device inference kernel: layer 1 in FP32 with a fused
+ * multiply-add chain in input order starting from the bias, ReLU, the hidden
+ * activations rounded to bfloat16 (the tensor-core operand type); layer 2 and
+ * the output layer evaluated exactly (FP64) from those values.  params are
+ * float32 values (weights already rounded to bfloat16 by the caller). */
+void orc_mlp_forward_bf16act(const float *params, int H, const float *x, int64_t n, double *y)
+{
+    const float *W1 = params;
+    const float *b1 = W1 + (int64_t)H * 4;
+    const float *W2 = b1 + H;
+    const float *b2 = W2 + (int64_t)H * H;
+    const float *w3 = b2 + H;
+    const float *b3 = w3 + H;
+    double *h1 = (double *)malloc((size_t)H * sizeof(double));
+    for (int64_t s = 0; s < n; ++s) {
+        const float *xs = x + s * 4;
+        for (int i = 0; i < H; ++i) {
+            float a = b1[i];
+            for (int j = 0; j < 4; ++j)
+                a = fmaf(W1[i * 4 + j], xs[j], a);
+            a = a > 0.0f ? a : 0.0f;
+            h1[i] = (double)orc_round_bf16(a);
+        }
+        double o = (double)b3[0];
+        for (int i = 0; i < H; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < H; ++j)
+                acc += (double)W2[(int64_t)i * H + j] * h1[j];
+            acc += (double)b2[i];
+            o += (double)w3[i] * (acc > 0.0 ? acc : 0.0);
+        }
+        y[s] = o;
+    }
+    free(h1);
 }

@@ -62,36 +62,6 @@ __global__ void round_params_kernel(const float *__restrict__ master, float *__r
 
 __device__ __forceinline__ float leaf_feature(float d2) { return logf(fmaxf(d2, 1e-30f)); }
 
-// forward pass with the (rounded) parameters in shared memory
-__device__ __forceinline__ float mlp_forward(const float *__restrict__ w, const float (&x)[4])
-{
-    float h1[H];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        float a = w[OB1 + i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            a = __fmaf_rn(w[OW1 + 4 * i + j], x[j], a);
-        h1[i] = fmaxf(a, 0.f);
-    }
-    float y = w[OB3];
-#pragma unroll 2
-    for (int i = 0; i < H; ++i) {
-        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
-        float a = w[OB2 + i];
-#pragma unroll
-        for (int j = 0; j < H / 4; ++j) {
-            const float4 r = row[j];
-            a = __fmaf_rn(r.x, h1[4 * j + 0], a);
-            a = __fmaf_rn(r.y, h1[4 * j + 1], a);
-            a = __fmaf_rn(r.z, h1[4 * j + 2], a);
-            a = __fmaf_rn(r.w, h1[4 * j + 3], a);
-        }
-        y = __fmaf_rn(w[OW3 + i], fmaxf(a, 0.f), y);
-    }
-    return y;
-}
-
 struct Norm {
     float mu[4];
     float sd[4];
@@ -110,49 +80,6 @@ __global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict_
         const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q);
         float4 f = make_float4(q[0], q[1], q[2], leaf_feature(d2));
         reinterpret_cast<float4 *>(feat)[i] = f;
-    }
-}
-
-// per-query cull radius of the learned pass: min(fl(r_p * r_p), r2_user)
-__global__ void __launch_bounds__(256) radius_kernel(const float4 *__restrict__ nodes, int N, int D,
-                                                     const float *__restrict__ qs, int64_t Q,
-                                                     const uint32_t *__restrict__ perm, int staged,
-                                                     const float *__restrict__ wts, Norm nm, float margin,
-                                                     float r2_user, float *__restrict__ r2q)
-{
-    extern __shared__ float4 s_dyn[];
-    float *s_w = reinterpret_cast<float *>(s_dyn);
-    float4 *s_nodes = s_dyn + (P + 3) / 4;
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        s_w[i] = wts[i];
-    stage_nodes<0>(nodes, s_nodes, staged);
-    __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = perm ? (int64_t)perm[i] : i;
-        float q[3];
-        load_query<0>(qs, qi, D, q);
-        const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q);
-        float x[4] = {q[0], q[1], q[2], leaf_feature(d2)};
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            x[j] = __fdiv_rn(__fsub_rn(x[j], nm.mu[j]), nm.sd[j]);
-        const float y = mlp_forward(s_w, x);
-        const float r = __fmul_rn(margin, expf(y));
-        const float rp2 = __fmul_rn(r, r);
-        r2q[qi] = (rp2 == rp2 && rp2 < r2_user) ? rp2 : r2_user;
-    }
-}
-
-__global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restrict__ wts, const float *__restrict__ x,
-                                                          int64_t n, float *__restrict__ y)
-{
-    __shared__ __align__(16) float s_w[P + 3];
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        s_w[i] = wts[i];
-    __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float xi[4] = {x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]};
-        y[i] = mlp_forward(s_w, xi);
     }
 }
 
@@ -405,15 +332,6 @@ uint64_t splitmix(uint64_t &x)
     return z ^ (z >> 31);
 }
 
-int model_norm(const kdt_tree *t, Norm *nm)
-{
-    for (int j = 0; j < 4; ++j) {
-        nm->mu[j] = t->model.norm[j];
-        nm->sd[j] = t->model.norm[4 + j];
-    }
-    return KDT_OK;
-}
-
 int ensure_params(kdt_tree *t)
 {
     if (!t->model.d_params)
@@ -485,15 +403,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, B + off_m, &perm, s));
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
-    Norm nm;
-    model_norm(t, &nm);
-    const int staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
-    const size_t smem = (size_t)((P + 3) / 4) * 16 + (size_t)staged * 16;
-    KDT_CUDA(cudaFuncSetAttribute(radius_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int g = grid_for_kernel((const void *)radius_kernel, 256, smem);
-    KDT_LAUNCH radius_kernel<<<g, 256, smem, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, perm, staged, wts, nm, t->model.margin, r2,
-                                       r2q);
-    KDT_CUDA(cudaGetLastError());
+    KDT_TRY(tc_radius(t, wts, d_q, Q, perm, r2, r2q, s));
     // stats slots: [0] fallback count, [1] ratio sum (double bits)
     KDT_CUDA(cudaMemsetAsync(t->stats, 0, 2 * sizeof(int64_t), s));
 
@@ -552,10 +462,17 @@ int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d
         return KDT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     Dev w(s);
-    KDT_CUDA(cudaMallocAsync(&w.p, P * sizeof(float), s));
+    const size_t wb = ((P * 4 + 255) & ~(size_t)255);
+    KDT_CUDA(cudaMallocAsync(&w.p, wb + 256, s));
+    int *err = (int *)((char *)w.p + wb);
+    KDT_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     KDT_TRY(upload_rounded(h_params, (float *)w.p, s));
-    KDT_LAUNCH mlp_forward_kernel<<<grid_of(n), 256, 0, s>>>((const float *)w.p, d_x, n, d_y);
-    KDT_CUDA(cudaGetLastError());
+    KDT_TRY(tc_forward((const float *)w.p, d_x, n, d_y, err, s));
+    int h = 0;
+    KDT_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KDT_CUDA(cudaStreamSynchronize(s));
+    if (h)
+        return set_error(KDT_ECUDA, "the tensor-core MMA did not signal completion in time");
     return KDT_OK;
 }
 
@@ -708,8 +625,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         // label - prediction exceeds log(margin); take the (1 - target)
         // quantile of the training residuals
         float *pred = d2;  // reuse: Qt floats
-        KDT_LAUNCH mlp_forward_kernel<<<grid_of(Qt), 256, 0, s>>>(w, feat, Qt, pred);
-        KDT_CUDA(cudaGetLastError());
+        KDT_TRY(tc_forward(w, feat, Qt, pred, t->err, s));
         std::vector<float> hp(Qt), hl(Qt);
         KDT_CUDA(cudaMemcpyAsync(hp.data(), pred, Qt * 4, cudaMemcpyDeviceToHost, s));
         KDT_CUDA(cudaMemcpyAsync(hl.data(), lab, Qt * 4, cudaMemcpyDeviceToHost, s));

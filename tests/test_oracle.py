@@ -360,3 +360,34 @@ def test_mlp_gradient_matches_finite_differences():
         pm[i] -= eps
         fd = (np.mean((_numpy_mlp(pp, H, x) - lab) ** 2) - np.mean((_numpy_mlp(pm, H, x) - lab) ** 2)) / (2 * eps)
         assert abs(fd - grad[i]) <= 1e-5 * max(1.0, abs(fd)), i
+
+
+def test_mlp_bf16_activation_forward_equals_exact_when_nothing_rounds():
+    """With small-integer weights, biases and inputs every hidden activation is
+    an integer below 256 (exact in bfloat16) and the FP32 layer is exact, so
+    the device-path forward must equal the plain FP64 forward."""
+    H = 16
+    g = np.random.default_rng(14)
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[: 4 * H] = g.integers(-2, 3, 4 * H)          # W1
+    p[4 * H: 5 * H] = g.integers(-3, 4, H)         # b1
+    p[5 * H:] = g.standard_normal(len(p) - 5 * H)  # W2, b2, w3, b3 (bf16-exact below)
+    p[5 * H:] = [oracle.round_bf16(float(v)) for v in p[5 * H:]]
+    x = g.integers(-4, 5, size=(50, 4)).astype(np.float64)
+    a = oracle.mlp_forward(p, H, x)
+    b = oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_bf16_activation_forward_rounds_hidden_layer():
+    """A hidden activation of 1 + 2^-10 is not a bfloat16 value: the device-path
+    forward sees 1 (ties to even), the exact forward sees 1 + 2^-10."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0                  # W1[0][0]
+    p[4] = 2.0 ** -10           # b1
+    p[5] = 1.0                  # W2
+    p[7] = 1.0                  # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    assert oracle.mlp_forward(p, H, x)[0] == 1.0 + 2.0 ** -10
+    assert oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0] == 1.0
