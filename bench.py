@@ -185,7 +185,8 @@ def workload_config(log2n):
     return {
         "workload": f"gmm_large: N=2^{log2n} 3-D float32 points, 64-component Gaussian mixture (sigma 0.01, "
                     f"centres U[0,1]^3); Q=2^{log2n} queries (90% mixture, 10% uniform [0,1]^3); kNN k=8, "
-                    "max_radius=inf, ordered stack-free traversal, Morton query order; step = tree build + "
+                    "max_radius=inf, ordered stack-free traversal, Morton query order with expensive queries first; "
+                    "step = tree build + "
                     "all queries",
         "N": 1 << log2n, "Q": 1 << log2n, "D": 3, "k": K_NN,
         "cache": "inputs larger than L2 (tree 256 MiB, points and queries 192 MiB each, outputs 1 GiB)",
@@ -252,7 +253,7 @@ def main():
     dq = torch.from_numpy(qs).to(dev)
     out_i = torch.empty((n, K_NN), dtype=torch.int32, device=dev)
     out_d = torch.empty((n, K_NN), dtype=torch.float32, device=dev)
-    flags = kdt.KDT_MORTON
+    flags = kdt.KDT_MORTON | kdt.KDT_COST_ORDER
     tree = kdt.kdt_build(dp)
     stream = torch.cuda.current_stream()
 

@@ -52,14 +52,18 @@ extern "C" {
                               side or the splitting plane is within the cull radius
                               (Sec. 3: unordered traversal as a simplification) */
 #define KDT_MORTON     0x2 /* sort queries along a 30-bit Morton curve before traversal so
-                              that the threads of a warp walk nearby paths (single trees with
-                              D <= 3: within four cost classes, most expensive first, judged by
-                              how far the greedy descent ends from its leaf point); results
-                              are written to the caller's query order */
+                              that the threads of a warp walk nearby paths; results are
+                              written to the caller's query order */
 #define KDT_LEARNED    0x4 /* seed each query's cull radius with the trained radius model
                               and re-run the queries that find fewer than k points with
                               the caller's radius (not in the paper; results unchanged) */
 #define KDT_NO_STAGE   0x8 /* do not stage the top tree levels in shared memory */
+#define KDT_COST_ORDER 0x20 /* with KDT_MORTON, single trees with D <= 3: run the queries in four
+                              cost classes, most expensive first (judged by how far the greedy
+                              descent ends from its leaf point, relative to the mean point
+                              spacing), Morton order within a class.  Pays when a few queries
+                              cost far more than the rest (queries outside the data); costs one
+                              descent per query */
 
 /* ---- build options ----------------------------------------------------- */
 #define KDT_BUILD_ASYNC 0x1 /* kdt_build_ex: do not synchronise to check the points for

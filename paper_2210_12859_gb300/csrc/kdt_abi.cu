@@ -268,8 +268,8 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     unsigned long long *counter = c.take<unsigned long long>(8);
     QueryArgs a;
     if (morton)
-        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, c.base + c.off,
-                             const_cast<uint32_t **>(&a.perm),
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
+                             t->N, c.base + c.off, const_cast<uint32_t **>(&a.perm),
                              s));
     a.nodes = t->nodes;
     a.ids = t->ids;

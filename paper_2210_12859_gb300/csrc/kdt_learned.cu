@@ -401,7 +401,8 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     uint32_t *fb_list = (uint32_t *)(B + off_fb);
     uint32_t *perm = nullptr;
     if (morton)
-        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, B + off_m, &perm, s));
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
+                             t->N, B + off_m, &perm, s));
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
     KDT_TRY(tc_radius(t, wts, d_q, Q, perm, r2, r2q, s));
     // stats slots: [0] fallback count, [1] ratio sum (double bits)

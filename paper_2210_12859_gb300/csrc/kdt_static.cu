@@ -97,7 +97,8 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     QueryArgs a;
     a.counter = (unsigned long long *)base;  // zeroed by the launch
     if (flags & KDT_MORTON)
-        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, t->nodes, t->N, (char *)base + STATIC_COUNTER_BYTES,
+        KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr, t->N,
+                             (char *)base + STATIC_COUNTER_BYTES,
                              const_cast<uint32_t **>(&a.perm), s));
     a.nodes = t->nodes;
     a.ids = t->ids;

@@ -38,6 +38,7 @@ KDT_MORTON = 0x2
 KDT_LEARNED = 0x4
 KDT_NO_STAGE = 0x8
 KDT_PER_TREE = 0x10
+KDT_COST_ORDER = 0x20
 KDT_BUILD_ASYNC = 0x1
 
 MLP_HIDDEN = 64

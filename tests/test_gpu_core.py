@@ -132,7 +132,8 @@ def small(kdt):
     return pts, qs, tree, cu(qs), oracle.build(pts)
 
 
-@pytest.mark.parametrize("flags_name", ["ORDERED", "UNORDERED", "MORTON", "NO_STAGE", "UNORDERED|MORTON"])
+@pytest.mark.parametrize("flags_name", ["ORDERED", "UNORDERED", "MORTON", "NO_STAGE", "UNORDERED|MORTON",
+                                        "MORTON|COST_ORDER"])
 @pytest.mark.parametrize("k", [1, 8])
 def test_small_uniform_bit_exact(kdt, small, flags_name, k):
     pts, qs, tree, dq, _ = small
@@ -262,7 +263,7 @@ def test_full_size_bench_configuration(kdt, gmm_full):
     """The launch the benchmark times (all 2^24 queries, k = 8, Morton order),
     checked on sampled outputs."""
     pts, qs, tree, dq = gmm_full
-    gi, gd = kdt.kdt_knn(tree, dq, 8, flags=kdt.KDT_MORTON)
+    gi, gd = kdt.kdt_knn(tree, dq, 8, flags=kdt.KDT_MORTON | kdt.KDT_COST_ORDER)
     kdt.kdt_status(tree)
     sample = np.random.default_rng(8).choice(len(qs), size=192, replace=False)
     wi, wd = oracle.knn_brute_threaded(pts, qs[sample], 8)
