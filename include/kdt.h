@@ -251,6 +251,7 @@ int kdt_knn_batched(kdt_forest *forest, const float *d_queries, const int64_t *h
  * d_coords float32 [sum N_i][D], d_ids int32 [sum N_i] (ids within the cloud). */
 int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids, void *stream);
 
+/* Release a forest and its device memory (synchronises the device first). */
 void kdt_forest_free(kdt_forest *forest);
 
 /* ---- launch tuning -------------------------------------------------------- */

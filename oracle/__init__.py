@@ -52,6 +52,10 @@ def _load():
         lib.orc_left_size.restype = i64
         lib.orc_build.argtypes = [P, i64, i32, P]
         lib.orc_build.restype = i32
+        lib.orc_build_widest.argtypes = [P, i64, i32, P, P]
+        lib.orc_build_widest.restype = i32
+        lib.orc_knn_stackfree_batch_dims.argtypes = [P, P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
+        lib.orc_knn_stackfree_batch_dims.restype = i32
         lib.orc_knn_brute.argtypes = [P, i64, i32, P, i64, i32, f32, P, P]
         lib.orc_knn_brute.restype = None
         lib.orc_knn_brute_f64.argtypes = [P, i64, i32, P, i64, i32, P, P]
@@ -98,6 +102,36 @@ def build(points) -> np.ndarray:
     if _load().orc_build(_ptr(pts), N, D, _ptr(out)) != 0:
         raise ValueError("oracle build failed (bad arguments or non-finite point)")
     return out
+
+
+def build_widest(points):
+    """Level-order tree with a stored split dimension per node (widest extent
+    of the node's points): (node -> input index int32[N], dims uint8[N])."""
+    pts = _f32(points)
+    N, D = pts.shape
+    out = np.empty(N, dtype=np.int32)
+    dims = np.empty(N, dtype=np.uint8)
+    if _load().orc_build_widest(_ptr(pts), N, D, _ptr(out), _ptr(dims)) != 0:
+        raise ValueError("oracle build failed (bad arguments or non-finite point)")
+    return out, dims
+
+
+def knn_tree_dims(points, node_pid, node_dim, queries, k, max_radius=float("inf"), ordered=True):
+    """Stack-free traversal of many queries over a tree with stored split
+    dimensions: (ids, d2, first visits per query)."""
+    pts, qs = _f32(points), _f32(queries)
+    node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    node_dim = np.ascontiguousarray(node_dim, dtype=np.uint8)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float32)
+    nv = np.empty(Q, dtype=np.int32)
+    rc = _load().orc_knn_stackfree_batch_dims(_ptr(pts), _ptr(node_pid), _ptr(node_dim), N, D, _ptr(qs), Q, k,
+                                              float(max_radius), int(ordered), _ptr(ids), _ptr(d2), _ptr(nv))
+    if rc != 0:
+        raise RuntimeError("oracle traversal exceeded its step cap")
+    return ids, d2, nv
 
 
 def knn_brute(points, queries, k: int, max_radius: float = float("inf")):

@@ -17,6 +17,8 @@
  *                       assumption; needed by the builder of Sec. 4)
  *   orc_build           recursive median builder (Sec. 4: the tree any serial
  *                       builder produces), round-robin split dimension
+ *   orc_build_widest    the same with a stored per-node split dimension (the
+ *                       other splitDimOf variant Sec. 3 names): widest extent
  *   orc_knn_brute       plain definition of the fcp / kNN result (exact method,
  *                       Sec. 3 "shrinking max radius"), FP32 distances
  *   orc_knn_brute_f64   the same selection with distances in FP64
@@ -97,25 +99,52 @@ static int orc_cmp_coord_idx(const void *a, const void *b, void *vctx)
     return (ia > ib) - (ia < ib);
 }
 
+/* dimension of widest extent (max - min, rounded to float) of the points S,
+ * ties to the lowest dimension index */
+static int orc_widest_dim(const float *pts, int D, const int32_t *S, int64_t n)
+{
+    int best = 0;
+    float best_ext = -1.0f;
+    for (int e = 0; e < D; ++e) {
+        float lo = pts[(int64_t)S[0] * D + e], hi = lo;
+        for (int64_t i = 1; i < n; ++i) {
+            float v = pts[(int64_t)S[i] * D + e];
+            if (v < lo)
+                lo = v;
+            if (v > hi)
+                hi = v;
+        }
+        float ext = hi - lo;
+        if (ext > best_ext) {
+            best_ext = ext;
+            best = e;
+        }
+    }
+    return best;
+}
+
+/* node_dim NULL: split dimension level mod D; else the widest dimension of the
+ * node's points, recorded in node_dim[node] */
 static int orc_build_rec(const float *pts, int64_t N, int D, int32_t *S,
-                         int64_t n, int64_t node, int32_t *node_pid)
+                         int64_t n, int64_t node, int32_t *node_pid, uint8_t *node_dim)
 {
     if (n == 0)
         return 0;
     if (node >= N)
         return -1; /* subtree sizes disagree with the complete tree */
-    orc_sort_ctx ctx = {pts, D, orc_level(node) % D};
+    int dim = node_dim ? orc_widest_dim(pts, D, S, n) : orc_level(node) % D;
+    if (node_dim)
+        node_dim[node] = (uint8_t)dim;
+    orc_sort_ctx ctx = {pts, D, dim};
     qsort_r(S, (size_t)n, sizeof(int32_t), orc_cmp_coord_idx, &ctx);
     int64_t L = orc_left_size(n);
     node_pid[node] = S[L];
-    if (orc_build_rec(pts, N, D, S, L, 2 * node + 1, node_pid))
+    if (orc_build_rec(pts, N, D, S, L, 2 * node + 1, node_pid, node_dim))
         return -1;
-    return orc_build_rec(pts, N, D, S + L + 1, n - L - 1, 2 * node + 2, node_pid);
+    return orc_build_rec(pts, N, D, S + L + 1, n - L - 1, 2 * node + 2, node_pid, node_dim);
 }
 
-/* node_pid[t] = input index of the point stored at level-order node t.
- * Returns 0 on success, -1 on bad arguments or a non-finite coordinate. */
-int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
+static int orc_build_any(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim)
 {
     if (N < 1 || D < 1 || D > 8)
         return -1;
@@ -127,9 +156,26 @@ int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
         return -1;
     for (int64_t i = 0; i < N; ++i)
         S[i] = (int32_t)i;
-    int rc = orc_build_rec(pts, N, D, S, N, 0, node_pid);
+    int rc = orc_build_rec(pts, N, D, S, N, 0, node_pid, node_dim);
     free(S);
     return rc;
+}
+
+/* node_pid[t] = input index of the point stored at level-order node t, split
+ * dimension level mod D.  Returns 0 on success, -1 on bad arguments or a
+ * non-finite coordinate. */
+int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
+{
+    return orc_build_any(pts, N, D, node_pid, NULL);
+}
+
+/* The same builder with the split dimension of every node stored in the node
+ * (Sec. 3 leaves splitDimOf open: stored per node or fixed by level): the
+ * dimension of widest extent of the node's points, ties to the lowest index;
+ * node_dim[t] receives it. */
+int orc_build_widest(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim)
+{
+    return orc_build_any(pts, N, D, node_pid, node_dim);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -279,7 +325,13 @@ typedef struct {
     int32_t *steps;    /* every node the traversal is "at", may be NULL */
     int64_t nsteps;
     int64_t scap;
+    const uint8_t *node_dim; /* stored split dimensions, or NULL: level mod D */
 } orc_trav;
+
+static int orc_split_dim(const orc_trav *T, int64_t node)
+{
+    return T->node_dim ? T->node_dim[node] : orc_level(node) % T->D;
+}
 
 static void orc_log(int32_t *buf, int64_t *n, int64_t cap, int64_t node)
 {
@@ -306,7 +358,7 @@ static void orc_rec(orc_trav *T, int64_t node)
     if (node >= T->N)
         return;
     orc_process(T, node);
-    int dim = orc_level(node) % T->D;
+    int dim = orc_split_dim(T, node);
     float split = T->pts[(int64_t)T->node_pid[node] * T->D + dim];
     float sd = T->q[dim] - split;
     if (T->ordered) {
@@ -351,7 +403,7 @@ static int orc_stackfree(orc_trav *T)
         if (from_parent)
             orc_process(T, curr);
         float cull = orc_list_cull(T->L);
-        int dim = orc_level(curr) % T->D;
+        int dim = orc_split_dim(T, curr);
         float split = T->pts[(int64_t)T->node_pid[curr] * T->D + dim];
         float sd = T->q[dim] - split;
         int64_t next;
@@ -386,7 +438,7 @@ static int orc_stackfree(orc_trav *T)
     return -1; /* step cap exceeded: cannot happen for a correct machine */
 }
 
-static int orc_knn_tree(const float *pts, const int32_t *node_pid, int64_t N, int D,
+static int orc_knn_tree(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
                         const float *q, int k, float max_radius, int ordered,
                         int stackfree, int32_t *ids, float *d2,
                         int32_t *visits, int64_t vcap, int64_t *nvisits,
@@ -395,7 +447,7 @@ static int orc_knn_tree(const float *pts, const int32_t *node_pid, int64_t N, in
     float *ld = (float *)malloc((size_t)k * sizeof(float));
     int32_t *li = (int32_t *)malloc((size_t)k * sizeof(int32_t));
     orc_list L = {k, 0, max_radius * max_radius, ld, li};
-    orc_trav T = {pts, node_pid, N, D, q, ordered, &L, visits, 0, vcap, steps, 0, scap};
+    orc_trav T = {pts, node_pid, N, D, q, ordered, &L, visits, 0, vcap, steps, 0, scap, node_dim};
     int rc = 0;
     if (stackfree)
         rc = orc_stackfree(&T);
@@ -417,7 +469,7 @@ int orc_knn_recursive(const float *pts, const int32_t *node_pid, int64_t N, int 
                       int32_t *ids, float *d2, int32_t *visits, int64_t vcap,
                       int64_t *nvisits, int32_t *steps, int64_t scap, int64_t *nsteps)
 {
-    return orc_knn_tree(pts, node_pid, N, D, q, k, max_radius, ordered, 0, ids, d2,
+    return orc_knn_tree(pts, node_pid, NULL, N, D, q, k, max_radius, ordered, 0, ids, d2,
                         visits, vcap, nvisits, steps, scap, nsteps);
 }
 
@@ -427,25 +479,34 @@ int orc_knn_stackfree(const float *pts, const int32_t *node_pid, int64_t N, int 
                       int32_t *ids, float *d2, int32_t *visits, int64_t vcap,
                       int64_t *nvisits, int32_t *steps, int64_t scap, int64_t *nsteps)
 {
-    return orc_knn_tree(pts, node_pid, N, D, q, k, max_radius, ordered, 1, ids, d2,
+    return orc_knn_tree(pts, node_pid, NULL, N, D, q, k, max_radius, ordered, 1, ids, d2,
                         visits, vcap, nvisits, steps, scap, nsteps);
 }
 
-/* Many queries through the stack-free machine; per-query first-visit counts. */
-int orc_knn_stackfree_batch(const float *pts, const int32_t *node_pid, int64_t N, int D,
-                            const float *qs, int64_t Q, int k, float max_radius,
-                            int ordered, int32_t *ids, float *d2, int32_t *nvisit)
+/* Many queries through the stack-free machine; per-query first-visit counts.
+ * node_dim: stored split dimensions, or NULL for level mod D. */
+int orc_knn_stackfree_batch_dims(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N,
+                                 int D, const float *qs, int64_t Q, int k, float max_radius,
+                                 int ordered, int32_t *ids, float *d2, int32_t *nvisit)
 {
     int rc = 0;
     for (int64_t i = 0; i < Q; ++i) {
         int64_t nv = 0;
-        if (orc_knn_tree(pts, node_pid, N, D, qs + i * D, k, max_radius, ordered, 1,
+        if (orc_knn_tree(pts, node_pid, node_dim, N, D, qs + i * D, k, max_radius, ordered, 1,
                          ids + i * k, d2 + i * k, NULL, 0, &nv, NULL, 0, NULL))
             rc = -1;
         if (nvisit)
             nvisit[i] = (int32_t)nv;
     }
     return rc;
+}
+
+int orc_knn_stackfree_batch(const float *pts, const int32_t *node_pid, int64_t N, int D,
+                            const float *qs, int64_t Q, int k, float max_radius,
+                            int ordered, int32_t *ids, float *d2, int32_t *nvisit)
+{
+    return orc_knn_stackfree_batch_dims(pts, node_pid, NULL, N, D, qs, Q, k, max_radius, ordered, ids, d2,
+                                        nvisit);
 }
 
 /* ------------------------------------------------------------------------ */

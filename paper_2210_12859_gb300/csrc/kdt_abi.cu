@@ -508,6 +508,7 @@ void kdt_free(kdt_tree *t)
 {
     if (!t)
         return;
+    cudaDeviceSynchronize();
     cudaFree(t->nodes_alloc);
     cudaFree(t->ids);
     cudaFree(t->bbox);
@@ -846,6 +847,7 @@ void kdt_forest_free(kdt_forest *f)
 {
     if (!f)
         return;
+    cudaDeviceSynchronize();
     if (f->graph) {
         ForestGraph *g = (ForestGraph *)f->graph;
         if (g->exec)

@@ -391,3 +391,78 @@ def test_mlp_bf16_activation_forward_rounds_hidden_layer():
     x = np.array([[1.0, 0, 0, 0]])
     assert oracle.mlp_forward(p, H, x)[0] == 1.0 + 2.0 ** -10
     assert oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0] == 1.0
+
+
+# ---------------------------------------------------------------- stored split dimension
+
+def _check_widest_tree(pts, node_pid, node_dim):
+    """Every node's stored dimension is the widest extent (max - min in float32,
+    ties to the lowest index) of its subtree's points, and the node separates
+    its subtrees in that dimension under the (coordinate, index) order."""
+    N, D = pts.shape
+    assert sorted(node_pid.tolist()) == list(range(N))
+    c = pts[node_pid]
+    lo, hi = c.copy(), c.copy()
+    ids = node_pid.astype(np.int64)
+    kmin = [((c[:, d].astype(np.float64)), ids.copy()) for d in range(D)]
+    for t in range(N - 1, -1, -1):
+        for ch in (2 * t + 1, 2 * t + 2):
+            if ch < N:
+                lo[t] = np.minimum(lo[t], lo[ch])
+                hi[t] = np.maximum(hi[t], hi[ch])
+    ext = (hi - lo).astype(np.float32)
+    assert np.array_equal(node_dim, np.argmax(ext, axis=1).astype(np.uint8))
+
+    def keys(t, d):
+        # all (coord, id) keys of subtree t in dimension d
+        out, stack = [], [t]
+        while stack:
+            u = stack.pop()
+            if u < N:
+                out.append((float(c[u, d]), int(ids[u])))
+                stack += [2 * u + 1, 2 * u + 2]
+        return out
+
+    for t in range(N):
+        d = int(node_dim[t])
+        me = (float(c[t, d]), int(ids[t]))
+        if 2 * t + 1 < N:
+            assert max(keys(2 * t + 1, d)) < me, t
+        if 2 * t + 2 < N:
+            assert me < min(keys(2 * t + 2, d)), t
+
+
+def test_widest_six_point_example():
+    g = json.load(open(GOLDEN))
+    pts = np.array(g["points"], dtype=np.float32)
+    node_pid, node_dim = oracle.build_widest(pts)
+    # root: x extent 7 > y extent 6; (5,4)'s points: y 4 > x 3; (9,6)'s: y 5 > x 1;
+    # single points have extent 0 everywhere -> dimension 0
+    assert node_dim.tolist() == [0, 1, 1, 0, 0, 0]
+    assert node_pid.tolist() == g["tree_ids"]
+
+
+@pytest.mark.parametrize("N,D,seed", [(1, 3, 0), (2, 2, 1), (9, 3, 2), (130, 3, 3), (300, 2, 4), (257, 1, 5)])
+def test_widest_builder_property(N, D, seed):
+    g = np.random.default_rng(seed)
+    pts = (g.random((N, D)) * np.array([1.0, 3.0, 0.5][:D])).astype(np.float32)
+    if seed % 2:
+        pts = g.integers(0, 5, size=(N, D)).astype(np.float32)  # ties in extents and coordinates
+    node_pid, node_dim = oracle.build_widest(pts)
+    _check_widest_tree(pts, node_pid, node_dim)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_widest_traversal_matches_brute(seed):
+    g = np.random.default_rng(300 + seed)
+    N, D = int(g.integers(1, 300)), int(g.integers(1, 4))
+    pts = (g.random((N, D)) * g.uniform(0.1, 3.0, D)).astype(np.float32)
+    if seed % 2:
+        pts = g.integers(0, 4, size=(N, D)).astype(np.float32)
+    qs = (g.random((60, D)) * 1.2 - 0.1).astype(np.float32)
+    node_pid, node_dim = oracle.build_widest(pts)
+    for k, r in ((1, math.inf), (8, math.inf), (5, 0.3)):
+        want = oracle.knn_brute(pts, qs, k, r)
+        for ordered in (True, False):
+            got = oracle.knn_tree_dims(pts, node_pid, node_dim, qs, k, r, ordered)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
