@@ -360,6 +360,23 @@ def main():
                    "visits_per_query": float(lv.double().mean().item()), "train_s": train_s,
                    "train_loss": loss, "train_queries": 1 << 20}
 
+    # ---- the same queries on a tree with a stored per-node split dimension
+    # (widest extent; the paper's other splitDimOf variant), same results
+    widest = None
+    if rank == 0:
+        wtree = kdt.kdt_build(dp, opts=kdt.KDT_BUILD_WIDEST)
+        wi = torch.empty_like(out_i)
+        wd = torch.empty_like(out_d)
+        w_build_ms = timeit(lambda: kdt.kdt_rebuild(wtree, dp, opts=kdt.KDT_BUILD_ASYNC), 2)
+        w_ms = timeit(lambda: kdt.kdt_knn(wtree, dq, K_NN, math.inf, flags, wi, wd), 2)
+        wv = kdt.kdt_knn_visits(wtree, dq, K_NN, math.inf, flags).double().mean().item()
+        widest = {"query_qps": n / (w_ms / 1000.0), "query_ms": w_ms, "build_ms": w_build_ms,
+                  "visits_per_query": wv, "speedup_vs_level_split": query_ms / w_ms,
+                  "identical_to_plain": bool(torch.equal(wi, out_i) and torch.equal(wd.view(torch.int32),
+                                                                                      out_d.view(torch.int32)))}
+        kdt.kdt_status(wtree)
+        wtree.free()
+
     # ---- end to end: host buffers in, host results out, through the C ABI
     e2e = None
     if not args.no_e2e:
@@ -388,6 +405,7 @@ def main():
             "clocks": clk.summary(), "bit_exact_sample": exact,
             "breakdown": {"build_ms": build_ms, "query_ms": query_ms, "query_qps": n / (query_ms / 1000.0)},
             "learned": learned,
+            "stored_split_dim": widest,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -68,6 +68,11 @@ extern "C" {
 /* ---- build options ----------------------------------------------------- */
 #define KDT_BUILD_ASYNC 0x1 /* kdt_build_ex: do not synchronise to check the points for
                                NaN / inf; the check result is reported by kdt_status */
+#define KDT_BUILD_WIDEST 0x2 /* kdt_build_ex, D <= 3: store a split dimension in every node
+                               instead of using level mod D (Sec. 3 leaves splitDimOf open
+                               between the two): the dimension of widest extent (largest
+                               max - min, rounded to float) of the node's points, ties to the
+                               lowest dimension; otherwise the same median rule */
 
 typedef struct kdt_tree kdt_tree;
 typedef struct kdt_forest kdt_forest;
@@ -100,6 +105,10 @@ int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream
 /* Rebuild `tree` in place from new points with the same N and D, reusing its
  * device memory (a trained radius model is kept).  opts as for kdt_build_ex. */
 int kdt_rebuild(kdt_tree *tree, const float *d_points, int opts, void *stream);
+
+/* Split dimension of every level-order node: d_dims uint8 [N] (level mod D, or
+ * the stored dimension of a KDT_BUILD_WIDEST tree). */
+int kdt_tree_split_dims(const kdt_tree *tree, uint8_t *d_dims, void *stream);
 
 /* N and D of a tree (host values, no synchronisation). */
 int kdt_tree_info(const kdt_tree *tree, int64_t *N, int *D);

@@ -133,7 +133,7 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
 // nodes; starting those first keeps them out of the end of the launch.
 __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, const float *__restrict__ bbox, int T,
                               const int64_t *__restrict__ q_off, const float4 *__restrict__ nodes, int64_t N,
-                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+                              bool stored, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
 {
     float spacing2 = 0.f;
     if (nodes) {
@@ -167,7 +167,7 @@ __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, co
         if (nodes) {
             float q[3];
             load_query<0>(qs, i, D, q);
-            const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q) / spacing2;
+            const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q, stored) / spacing2;
             const uint32_t cls = r > 64.f ? 0u : (r > 8.f ? 1u : (r > 1.f ? 2u : 3u));  // NaN: 3
             code |= cls << 30;
         }
@@ -207,7 +207,7 @@ size_t morton_scratch_bytes(int64_t Q)
 // permutation of the queries along the Morton curve (stable: equal codes keep
 // their index order); perm receives traversal order -> query index
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, void *scratch, uint32_t **perm_out, cudaStream_t s)
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s)
 {
     Carve c{(char *)scratch};
     uint32_t *keys = c.take<uint32_t>(Q);
@@ -216,8 +216,8 @@ int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, c
     uint32_t *tv = c.take<uint32_t>(Q);
     uint32_t *rs = c.take<uint32_t>(radix_scratch_elems(Q));
     const bool cost = nodes && D <= 3 && T == 1;
-    KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, cost ? nodes : nullptr, N, keys,
-                                                        perm);
+    KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, cost ? nodes : nullptr, N, stored,
+                                                        keys, perm);
     KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, cost ? 32 : 30, rs, s));
     if (T > 1) {
         KDT_LAUNCH tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
@@ -269,7 +269,7 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     QueryArgs a;
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
-                             t->N, c.base + c.off, const_cast<uint32_t **>(&a.perm),
+                             t->N, t->layout == 3, c.base + c.off, const_cast<uint32_t **>(&a.perm),
                              s));
     a.nodes = t->nodes;
     a.ids = t->ids;
@@ -329,8 +329,16 @@ __global__ void export_kernel(const float4 *__restrict__ nodes, const int32_t *_
             for (int j = 0; j < D; ++j)
                 coords[t * D + j] = v[j];
         if (out_ids)
-            out_ids[t] = D <= 3 ? __float_as_int(a.w) : ids[t];
+            out_ids[t] = D <= 3 ? (int32_t)(__float_as_uint(a.w) & NODE_ID_MASK) : ids[t];
     }
+}
+
+__global__ void split_dims_kernel(const float4 *__restrict__ nodes, int64_t n, int D, bool stored,
+                                  uint8_t *__restrict__ dims)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dims[t] = stored ? (uint8_t)(__float_as_uint(nodes[t].w) >> NODE_DIM_SHIFT)
+                         : (uint8_t)(Topo::level(t) % D);
 }
 
 }  // namespace kdt
@@ -403,12 +411,17 @@ int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream
         return set_error(KDT_EINVAL, "out is NULL");
     *out = nullptr;
     KDT_TRY(check_build_args(d_points, N, D));
+    const bool widest = opts & KDT_BUILD_WIDEST;
+    if (widest && D > 3)
+        return set_error(KDT_EINVAL, "KDT_BUILD_WIDEST needs D <= 3 (got %d)", D);
     pool_setup_once();
     cudaStream_t s = (cudaStream_t)stream;
     kdt_tree *t = nullptr;
     KDT_TRY(kdt_tree_alloc_internal(N, D, &t));
+    if (widest)
+        t->layout = 3;
     int64_t off[2] = {0, N};
-    int rc = build_forest(d_points, off, 1, D, t->nodes, t->ids, t->bbox, t->err, s);
+    int rc = build_forest(d_points, off, 1, D, t->nodes, t->ids, t->bbox, t->err, s, widest);
     if (rc == KDT_OK)
         rc = finish_build(t, opts, s);
     if (rc != KDT_OK) {
@@ -431,7 +444,7 @@ int kdt_rebuild(kdt_tree *t, const float *d_points, int opts, void *stream)
     KDT_TRY(check_build_args(d_points, t->N, t->D));
     cudaStream_t s = (cudaStream_t)stream;
     int64_t off[2] = {0, t->N};
-    KDT_TRY(build_forest(d_points, off, 1, t->D, t->nodes, t->ids, t->bbox, t->err, s));
+    KDT_TRY(build_forest(d_points, off, 1, t->D, t->nodes, t->ids, t->bbox, t->err, s, t->layout == 3));
     return finish_build(t, opts, s);
 }
 
@@ -452,6 +465,16 @@ int kdt_tree_export(const kdt_tree *t, float *d_coords, int32_t *d_ids, void *st
         return set_error(KDT_EINVAL, "tree is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     KDT_LAUNCH export_kernel<<<grid_1d(t->N), 256, 0, s>>>(t->nodes, t->ids, t->N, t->D, d_coords, d_ids);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
+}
+
+int kdt_tree_split_dims(const kdt_tree *t, uint8_t *d_dims, void *stream)
+{
+    if (!t || !d_dims)
+        return set_error(KDT_EINVAL, "NULL tree or output");
+    KDT_LAUNCH split_dims_kernel<<<grid_1d(t->N), 256, 0, (cudaStream_t)stream>>>(t->nodes, t->N, t->D,
+                                                                                   t->layout == 3, d_dims);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
@@ -690,7 +713,7 @@ static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64
     QueryArgs a;
     if (flags & KDT_MORTON) {
         int tbits = T > 1 ? floor_log2((uint64_t)(T - 1)) + 1 : 0;
-        KDT_TRY(morton_order(d_q, Q, f->f.D, f->bbox, T, d_qoff, tbits, nullptr, 0, c.base + c.off,
+        KDT_TRY(morton_order(d_q, Q, f->f.D, f->bbox, T, d_qoff, tbits, nullptr, 0, false, c.base + c.off,
                              const_cast<uint32_t **>(&a.perm), s));
     }
     a.nodes = f->nodes;

@@ -151,6 +151,69 @@ __global__ void assign_kernel(const uint32_t *__restrict__ list, int64_t total, 
     }
 }
 
+// ---- stored split dimension (widest extent of the node's points)
+
+struct ListPtrs {
+    const uint32_t *p[8];
+};
+
+// split dimension of every node of level l: within the node's segment each
+// list is sorted by its coordinate, so its first and last elements give the
+// extent; the widest dimension wins, ties to the lowest index
+__global__ void widest_kernel(ListPtrs lists, int64_t n, int l, const float *__restrict__ pts, int D,
+                              uint8_t *__restrict__ node_dim)
+{
+    const int64_t first = ((int64_t)1 << l) - 1;
+    const int64_t count = (first + 1 < n - first) ? first + 1 : n - first;
+    const Topo tp(n);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = first + i;
+        const int64_t a = tp.inorder(tp.leftmost(t));
+        const int64_t b = tp.inorder(tp.rightmost(t));
+        int best = 0;
+        float best_ext = -1.f;
+        for (int e = 0; e < D; ++e) {
+            const float lo = pts[(int64_t)lists.p[e][a] * D + e];
+            const float hi = pts[(int64_t)lists.p[e][b] * D + e];
+            const float ext = __fsub_rn(hi, lo);
+            if (ext > best_ext) {
+                best_ext = ext;
+                best = e;
+            }
+        }
+        node_dim[t] = (uint8_t)best;
+    }
+}
+
+// level l with per-node split dimensions: the element at in-order position p
+// of its segment's split list decides the side (single tree, D <= 3)
+__global__ void assign_widest_kernel(ListPtrs lists, int64_t n, int l, const uint8_t *__restrict__ node_dim,
+                                     const float *__restrict__ pts, int D, uint8_t *__restrict__ side,
+                                     float4 *__restrict__ nodes)
+{
+    const Topo tp(n);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (l > tp.H)
+            continue;
+        const int64_t u = tp.node_at(p);
+        const int lu = Topo::level(u);
+        if (lu < l)
+            continue;
+        const int64_t t = Topo::ancestor(u, lu, l);
+        const int e = node_dim[t];
+        const uint32_t pid = lists.p[e][p];
+        if (lu == l) {
+            side[pid] = SIDE_NODE;
+            const float *c = pts + (int64_t)pid * D;
+            const uint32_t word = pid | ((uint32_t)e << NODE_DIM_SHIFT);
+            nodes[u] = make_float4(c[0], D > 1 ? c[1] : 0.f, D > 2 ? c[2] : 0.f, __uint_as_float(word));
+        } else {
+            const int bit = (int)(((u + 1) >> (lu - l - 1)) & 1);
+            side[pid] = bit ? SIDE_RIGHT : SIDE_LEFT;
+        }
+    }
+}
+
 // ---- segmented stable partition of a non-split list
 
 struct Seg {
@@ -353,7 +416,7 @@ struct DevBuf {
 }  // namespace
 
 int build_forest(const float *d_points, const int64_t *h_off, int T, int D, float4 *nodes, int32_t *ids, float *bbox,
-                 int *err, cudaStream_t s)
+                 int *err, cudaStream_t s, bool widest)
 {
     const int64_t total = h_off[T];
     int maxH = 0;
@@ -383,6 +446,7 @@ int build_forest(const float *d_points, const int64_t *h_off, int T, int D, floa
     size_t o_tiles = take((size_t)ptiles * sizeof(Seg));
     size_t o_rs = take(rs * 4);
     size_t o_lptr = take((size_t)8 * sizeof(uint32_t *));
+    size_t o_dim = take(widest ? (size_t)total : 0);
     DevBuf buf;
     buf.s = s;
     KDT_CUDA(cudaMallocAsync(&buf.p, bytes, s));
@@ -399,6 +463,7 @@ int build_forest(const float *d_points, const int64_t *h_off, int T, int D, floa
     Seg *tiles = (Seg *)(B + o_tiles);
     uint32_t *rscr = (uint32_t *)(B + o_rs);
     uint32_t **d_lptr = (uint32_t **)(B + o_lptr);
+    uint8_t *node_dim = (uint8_t *)(B + o_dim);
 
     KDT_CUDA(cudaMemcpyAsync(d_off, h_off, (T + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     const unsigned g = grid_for(total);
@@ -418,6 +483,30 @@ int build_forest(const float *d_points, const int64_t *h_off, int T, int D, floa
     KDT_CUDA(cudaMemcpyAsync(d_lptr, lists, 8 * sizeof(uint32_t *), cudaMemcpyHostToDevice, s));
     KDT_LAUNCH bbox_kernel<<<(T + 127) / 128, 128, 0, s>>>(d_points, D, d_lptr, d_off, T, bbox);
 
+    if (widest) {
+        // per-node split dimensions: every list may be a node's split list,
+        // so every list is partitioned at every level that has a successor
+        for (int l = 0; l <= maxH; ++l) {
+            ListPtrs lp;
+            for (int e = 0; e < 8; ++e)
+                lp.p[e] = e < D ? lists[e] : nullptr;
+            const int64_t level_nodes = std::min<int64_t>((int64_t)1 << l, total - (((int64_t)1 << l) - 1));
+            KDT_LAUNCH widest_kernel<<<grid_for(level_nodes), BT, 0, s>>>(lp, total, l, d_points, D, node_dim);
+            KDT_LAUNCH assign_widest_kernel<<<g, BT, 0, s>>>(lp, total, l, node_dim, d_points, D, side, nodes);
+            if (l < maxH) {
+                for (int e = 0; e < D; ++e) {
+                    KDT_LAUNCH part_reduce_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off, tree_of,
+                                                                                  side, tiles);
+                    KDT_LAUNCH part_tiles_kernel<<<1, 1024, 0, s>>>(tiles, ptiles);
+                    KDT_LAUNCH part_scatter_kernel<<<(unsigned)ptiles, BT, 0, s>>>(lists[e], total, l, T, d_off,
+                                                                                   tree_of, side, tiles, spare);
+                    std::swap(lists[e], spare);
+                }
+            }
+            KDT_CUDA(cudaGetLastError());
+        }
+        return KDT_OK;
+    }
     for (int l = 0; l <= maxH; ++l) {
         const int d = l % D;
         KDT_LAUNCH assign_kernel<<<g, BT, 0, s>>>(lists[d], total, l, T, d_off, tree_of, d_points, D, side, nodes, ids);

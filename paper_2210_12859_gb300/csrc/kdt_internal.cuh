@@ -92,6 +92,15 @@ struct Topo {
         int64_t j = (P + 1) >> (tz + 1);
         return (((int64_t)1 << l) - 1) + j;
     }
+    // rightmost node of the subtree of t
+    __host__ __device__ __forceinline__ int64_t rightmost(int64_t t) const
+    {
+        int m = H - level(t);
+        int64_t u = ((t + 2) << m) - 2;
+        if (u >= n)
+            u = ((t + 2) << (m - 1)) - 2;
+        return u;
+    }
     // leftmost node of the subtree of t
     __host__ __device__ __forceinline__ int64_t leftmost(int64_t t) const
     {
@@ -127,6 +136,10 @@ __host__ __device__ __forceinline__ uint32_t float_key(float x)
 //   layout 0 (D <= 3): float4 {x, y, z, id bits} per node, unused coords = 0
 //   layout 1 (D == 4): float4 {c0..c3} per node + int32 ids[N]
 //   layout 2 (D 5..8): 2 x float4 {c0..c7} per node + int32 ids[N], unused = 0
+//   layout 3 (D <= 3, split dimension stored per node): as layout 0 with the
+//            node's split dimension in the two high bits of the id word
+constexpr uint32_t NODE_ID_MASK = 0x3fffffffu;
+constexpr int NODE_DIM_SHIFT = 30;
 __host__ __device__ __forceinline__ int layout_of(int D) { return D <= 3 ? 0 : (D == 4 ? 1 : 2); }
 __host__ __device__ __forceinline__ int float4_per_node(int D) { return D <= 4 ? 1 : 2; }
 
@@ -167,7 +180,7 @@ struct ForestDesc {
 struct kdt_tree {
     int64_t N = 0;
     int D = 0;
-    int layout = 0;
+    int layout = 0;                // 3: split dimension stored per node (widest extent)
     int device = 0;
     float4 *nodes = nullptr;       // N * float4_per_node(D), node t at nodes[t * float4_per_node(D)]
     float4 *nodes_alloc = nullptr; // allocation; 16-byte nodes start one slot in, so that the siblings
@@ -205,6 +218,8 @@ namespace kdt {
 // own setting, else the tuned value for its shape, else the default
 int stage_levels_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
+// widest: split dimension per node = widest extent of its points (T == 1,
+// D <= 3), stored in the node (layout 3); else level mod D
 int build_forest(const float *d_points, const int64_t *h_offsets, int T, int D, float4 *nodes,
-                 int32_t *ids, float *bbox, int *err, cudaStream_t s);
+                 int32_t *ids, float *bbox, int *err, cudaStream_t s, bool widest = false);
 }  // namespace kdt

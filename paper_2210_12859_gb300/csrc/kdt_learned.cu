@@ -28,7 +28,7 @@
 namespace kdt {
 
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, void *scratch, uint32_t **perm_out, cudaStream_t s);
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s);
 size_t morton_scratch_bytes(int64_t Q);
 
 namespace {
@@ -69,7 +69,7 @@ struct Norm {
 
 __global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict__ nodes, int N, int D,
                                                        const float *__restrict__ qs, int64_t Q, int staged,
-                                                       float *__restrict__ feat)
+                                                       bool stored, float *__restrict__ feat)
 {
     extern __shared__ float4 s_nodes[];
     stage_nodes<0>(nodes, s_nodes, staged);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict_
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
         float q[3];
         load_query<0>(qs, i, D, q);
-        const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q);
+        const float d2 = descent_leaf_d2(nodes, s_nodes, staged, N, D, q, stored);
         float4 f = make_float4(q[0], q[1], q[2], leaf_feature(d2));
         reinterpret_cast<float4 *>(feat)[i] = f;
     }
@@ -402,7 +402,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     uint32_t *perm = nullptr;
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
-                             t->N, B + off_m, &perm, s));
+                             t->N, t->layout == 3, B + off_m, &perm, s));
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
     KDT_TRY(tc_radius(t, wts, d_q, Q, perm, r2, r2q, s));
     // stats slots: [0] fallback count, [1] ratio sum (double bits)
@@ -429,8 +429,8 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.fb_count = (unsigned long long *)t->stats;
     a.ratio_sum = (double *)(t->stats + 1);
     const bool ordered = !(flags & KDT_UNORDERED);
-    KDT_TRY(launch_query(0, a, ordered, MODE_BOUNDED, false, s));
-    KDT_TRY(launch_query(0, a, ordered, MODE_FALLBACK, false, s));
+    KDT_TRY(launch_query(t->layout, a, ordered, MODE_BOUNDED, false, s));
+    KDT_TRY(launch_query(t->layout, a, ordered, MODE_FALLBACK, false, s));
     t->last_learned_q = Q;
     return KDT_OK;
 }
@@ -450,7 +450,8 @@ int kdt_descent_features(const kdt_tree *t, const float *d_q, int64_t Q, float *
         return KDT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int staged = staged_for_levels(t->N, stage_levels_for(t, 8));
-    KDT_LAUNCH features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged, d_feat);
+    KDT_LAUNCH features_kernel<<<grid_of(Q), 256, staged * 16, s>>>(t->nodes, (int)t->N, t->D, d_q, Q, staged,
+                                                                        t->layout == 3, d_feat);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }

@@ -105,6 +105,7 @@ struct TcArgs {
     // radius mode
     const float4 *nodes;
     int N, D;
+    bool stored;               // split dimension stored in the nodes
     const float *queries;
     const uint32_t *perm;
     float mu[4], sd[4];
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(TILE_M) mlp_tc_kernel(const TcArgs a)
                 qi = a.perm ? (int64_t)a.perm[i] : i;
                 float q[3];
                 load_query<0>(a.queries, qi, a.D, q);
-                const float d2 = descent_leaf_d2(a.nodes, nullptr, 0, a.N, a.D, q);
+                const float d2 = descent_leaf_d2(a.nodes, nullptr, 0, a.N, a.D, q, a.stored);
                 const float f[4] = {q[0], q[1], q[2], logf(fmaxf(d2, 1e-30f))};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
@@ -294,6 +295,7 @@ int tc_radius(const kdt_tree *t, const float *wts, const float *d_q, int64_t Q, 
     a.nodes = t->nodes;
     a.N = (int)t->N;
     a.D = t->D;
+    a.stored = t->layout == 3;
     a.queries = d_q;
     a.perm = perm;
     for (int j = 0; j < 4; ++j) {

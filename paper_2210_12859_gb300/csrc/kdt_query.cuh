@@ -45,12 +45,14 @@ enum : int { MODE_RESULTS = 0, MODE_VISITS = 1, MODE_BOUNDED = 2, MODE_FALLBACK 
 int launch_query_layout0(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
 int launch_query_layout1(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
 int launch_query_layout2(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
+int launch_query_layout3(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);
 
 inline int launch_query(int layout, const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s)
 {
     switch (layout) {
     case 0: return launch_query_layout0(a, ordered, mode, batched, s);
     case 1: return launch_query_layout1(a, ordered, mode, batched, s);
+    case 3: return launch_query_layout3(a, ordered, mode, batched, s);
     default: return launch_query_layout2(a, ordered, mode, batched, s);
     }
 }

@@ -208,7 +208,7 @@ inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, 
         return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE>, threads, smem, a, s);
     case MODE_BOUNDED:
     case MODE_FALLBACK:
-        if constexpr (LAYOUT == 0) {
+        if constexpr (LAYOUT == 0 || LAYOUT == 3) {
             if (mode == MODE_BOUNDED) {
                 if (ordered)
                     return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE>, threads, smem, a, s);
@@ -234,6 +234,8 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
     const int threads = K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS;
     size_t list_bytes = K <= MAX_REG_K ? 0 : (size_t)a.k * threads * 8;
     if (batched) {
+        if constexpr (LAYOUT == 3)
+            return set_error(KDT_EINVAL, "forests store no per-node split dimensions");
         if (ordered)
             return launch_kernel(knn_forest_kernel<LAYOUT, K, true>, threads, list_bytes, a, s);
         return launch_kernel(knn_forest_kernel<LAYOUT, K, false>, threads, list_bytes, a, s);

@@ -21,7 +21,7 @@
 namespace kdt {
 
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, void *scratch, uint32_t **perm_out, cudaStream_t s);
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s);
 size_t morton_scratch_bytes(int64_t Q);
 
 namespace {
@@ -98,7 +98,7 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     a.counter = (unsigned long long *)base;  // zeroed by the launch
     if (flags & KDT_MORTON)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr, t->N,
-                             (char *)base + STATIC_COUNTER_BYTES,
+                             t->layout == 3, (char *)base + STATIC_COUNTER_BYTES,
                              const_cast<uint32_t **>(&a.perm), s));
     a.nodes = t->nodes;
     a.ids = t->ids;

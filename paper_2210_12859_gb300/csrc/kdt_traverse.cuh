@@ -13,12 +13,24 @@ template <int LAYOUT> struct LayoutTraits;
 template <> struct LayoutTraits<0> { static constexpr int NC = 3; static constexpr int NF = 1; };
 template <> struct LayoutTraits<1> { static constexpr int NC = 4; static constexpr int NF = 1; };
 template <> struct LayoutTraits<2> { static constexpr int NC = 8; static constexpr int NF = 2; };
+template <> struct LayoutTraits<3> { static constexpr int NC = 3; static constexpr int NF = 1; };
 
 template <int LAYOUT>
 struct NodeVal {
     float c[LayoutTraits<LAYOUT>::NC];
-    uint32_t id;  // layout 0 only
+    uint32_t id;  // layouts 0 and 3 (the node's id word)
 };
+
+// split dimension of a node: stored in the id word (layout 3), else the
+// dimension the walker tracks (level mod D)
+template <int LAYOUT>
+__device__ __forceinline__ int split_dim_of(const NodeVal<LAYOUT> &nd, int tracked)
+{
+    if constexpr (LAYOUT == 3)
+        return (int)(nd.id >> NODE_DIM_SHIFT);
+    else
+        return tracked;
+}
 
 __device__ __forceinline__ float4 ldg_f4(const float4 *p) { return __ldg(p); }
 
@@ -211,7 +223,7 @@ __device__ __forceinline__ void process(const NodeVal<LAYOUT> &nd, int n, const 
 {
     const float d2 = dist2<LayoutTraits<LAYOUT>::NC>(nd.c, q);
     if (d2 <= key_d2(list.worst())) {
-        const uint32_t id = LAYOUT == 0 ? nd.id : (uint32_t)__ldg(ids + n);
+        const uint32_t id = LAYOUT == 0 ? nd.id : (LAYOUT == 3 ? (nd.id & NODE_ID_MASK) : (uint32_t)__ldg(ids + n));
         const unsigned long long key = pack_key(d2, id);
         if (key < list.worst())
             list.insert(key);
@@ -306,7 +318,8 @@ struct Walker {
         process<LAYOUT>(nc, c, ids, q, list);
         const int lcc = 2 * c + 1;
         if (lcc < N) {
-            const float sdc = __fsub_rn(select_dim<NC>(q, dimc), select_dim<NC>(nc.c, dimc));
+            const int dc = split_dim_of<LAYOUT>(nc, dimc);
+            const float sdc = __fsub_rn(select_dim<NC>(q, dc), select_dim<NC>(nc.c, dc));
             leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ga, gb, ids, N, q, list, visits);
         }
     }
@@ -329,7 +342,8 @@ struct Walker {
             ++visits;
             process<LAYOUT>(nd, curr, ids, q, list);
         }
-        const float sd = __fsub_rn(select_dim<NC>(q, dim), select_dim<NC>(nd.c, dim));
+        const int sdim = split_dim_of<LAYOUT>(nd, dim);
+        const float sd = __fsub_rn(select_dim<NC>(q, sdim), select_dim<NC>(nd.c, sdim));
         const float sd2 = __fmul_rn(sd, sd);
         const int lc = 2 * curr + 1;
         const int parent = (curr - 1) >> 1;  // -1 for the root
@@ -447,14 +461,16 @@ __device__ __forceinline__ void stage_nodes(const float4 *__restrict__ nodes, fl
 
 // Greedy close-child descent from the root (Sec. 3.2's closeSide rule at every
 // node) until that child does not exist; returns the FP32 squared distance to
-// the last node reached (layout 0 trees, D <= 3).
+// the last node reached (layout 0 / 3 trees, D <= 3; stored: split dimension
+// stored in the node).
 __device__ __forceinline__ float descent_leaf_d2(const float4 *__restrict__ nodes, const float4 *s_nodes, int staged,
-                                                 int N, int D, const float (&q)[3])
+                                                 int N, int D, const float (&q)[3], bool stored = false)
 {
     int node = 0, dim = 0;
     NodeVal<0> nd = fetch<0>(nodes, s_nodes, staged, 0);
     for (;;) {
-        const float sd = __fsub_rn(select_dim<3>(q, dim), select_dim<3>(nd.c, dim));
+        const int sdim = stored ? (int)(nd.id >> NODE_DIM_SHIFT) : dim;
+        const float sd = __fsub_rn(select_dim<3>(q, sdim), select_dim<3>(nd.c, sdim));
         const int child = 2 * node + 1 + (sd > 0.f);
         if (child >= N)
             break;

@@ -40,6 +40,7 @@ KDT_NO_STAGE = 0x8
 KDT_PER_TREE = 0x10
 KDT_COST_ORDER = 0x20
 KDT_BUILD_ASYNC = 0x1
+KDT_BUILD_WIDEST = 0x2
 
 MLP_HIDDEN = 64
 MLP_PARAMS = 64 * 4 + 64 + 64 * 64 + 64 + 64 + 1
@@ -78,6 +79,7 @@ _sig("kdt_rebuild", [_P, _P, _I, _P])
 _sig("kdt_tree_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I)])
 _sig("kdt_tree_export", [_P, _P, _P, _P])
 _sig("kdt_tree_save", [_P, ctypes.c_char_p])
+_sig("kdt_tree_split_dims", [_P, _P, _P])
 _sig("kdt_tree_load", [ctypes.c_char_p, _P, ctypes.POINTER(_P)])
 _sig("kdt_fcp", [_P, _P, _I64, _F, _I, _P, _P, _P])
 _sig("kdt_knn", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
@@ -242,6 +244,12 @@ def kdt_tree_export(tree: Tree, stream=None):
     _check(_lib.kdt_tree_export(tree.handle, ctypes.c_void_p(coords.data_ptr()), ctypes.c_void_p(ids.data_ptr()),
                                 _stream(stream)))
     return coords, ids
+
+
+def kdt_tree_split_dims(tree: Tree, stream=None) -> torch.Tensor:
+    dims = torch.empty(tree.N, dtype=torch.uint8, device="cuda")
+    _check(_lib.kdt_tree_split_dims(tree.handle, ctypes.c_void_p(dims.data_ptr()), _stream(stream)))
+    return dims
 
 
 def kdt_tree_save(tree: Tree, path: str) -> None:
