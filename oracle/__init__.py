@@ -52,6 +52,10 @@ def _load():
         lib.orc_left_size.restype = i64
         lib.orc_build.argtypes = [P, i64, i32, P]
         lib.orc_build.restype = i32
+        lib.orc_radius_brute.argtypes = [P, i64, i32, P, i64, f32, P, P, P, P]
+        lib.orc_radius_brute.restype = None
+        lib.orc_box_brute.argtypes = [P, i64, i32, P, P, i64, P, P, P]
+        lib.orc_box_brute.restype = None
         lib.orc_build_widest.argtypes = [P, i64, i32, P, P]
         lib.orc_build_widest.restype = i32
         lib.orc_knn_stackfree_batch_dims.argtypes = [P, P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
@@ -132,6 +136,39 @@ def knn_tree_dims(points, node_pid, node_dim, queries, k, max_radius=float("inf"
     if rc != 0:
         raise RuntimeError("oracle traversal exceeded its step cap")
     return ids, d2, nv
+
+
+def radius_brute(points, queries, radius: float):
+    """Every point with d2 <= fl(r*r): (counts int32[Q], offsets int64[Q+1],
+    ids int32[total], d2 float32[total]), ids of a query in index order."""
+    pts, qs = _f32(points), _f32(queries)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    counts = np.empty(Q, dtype=np.int32)
+    lib = _load()
+    lib.orc_radius_brute(_ptr(pts), N, D, _ptr(qs), Q, float(radius), _ptr(counts), None, None, None)
+    offsets = np.zeros(Q + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    d2 = np.empty(max(int(offsets[-1]), 1), dtype=np.float32)
+    lib.orc_radius_brute(_ptr(pts), N, D, _ptr(qs), Q, float(radius), _ptr(counts), _ptr(offsets), _ptr(ids),
+                         _ptr(d2))
+    return counts, offsets, ids[: offsets[-1]], d2[: offsets[-1]]
+
+
+def box_brute(points, lo, hi):
+    """Every point inside [lo, hi] (inclusive): (counts, offsets, ids)."""
+    pts, lo, hi = _f32(points), _f32(lo), _f32(hi)
+    N, D = pts.shape
+    Q = lo.shape[0]
+    counts = np.empty(Q, dtype=np.int32)
+    lib = _load()
+    lib.orc_box_brute(_ptr(pts), N, D, _ptr(lo), _ptr(hi), Q, _ptr(counts), None, None)
+    offsets = np.zeros(Q + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    lib.orc_box_brute(_ptr(pts), N, D, _ptr(lo), _ptr(hi), Q, _ptr(counts), _ptr(offsets), _ptr(ids))
+    return counts, offsets, ids[: offsets[-1]]
 
 
 def knn_brute(points, queries, k: int, max_radius: float = float("inf")):

@@ -24,6 +24,8 @@
  *   orc_knn_brute_f64   the same selection with distances in FP64
  *   orc_knn_recursive   the recursive ordered / unordered traversal (Sec. 3.1)
  *   orc_knn_stackfree   the (curr, prev) state machine (Sec. 3.2)
+ *   orc_radius_brute    every point within a radius / inside a box (the plain
+ *   orc_box_brute       definition of the range queries Sec. 3 mentions)
  *   orc_descent_leaf    greedy close-child descent (feature of the learned
  *                       radius proposal; not in the paper)
  *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
@@ -697,4 +699,58 @@ void orc_mlp_forward_bf16act(const float *params, int H, const float *x, int64_t
         y[s] = o;
     }
     free(h1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Range queries (Sec. 3: a point / sphere or a box as query primitive).     */
+/* ------------------------------------------------------------------------ */
+
+/* Every point with d2 <= fl(r * r) (FP32 distance as orc_d2), per query in
+ * input-index order.  counts[q] receives the number; when ids is not NULL,
+ * query q's ids (and d2 when not NULL) are written at offsets[q]. */
+void orc_radius_brute(const float *pts, int64_t N, int D, const float *qs, int64_t Q, float radius,
+                      int32_t *counts, const int64_t *offsets, int32_t *ids, float *d2)
+{
+    float r2 = radius * radius;
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t c = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            float v = orc_d2(pts + i * D, qs + q * D, D);
+            if (v <= r2) {
+                if (ids) {
+                    ids[offsets[q] + c] = (int32_t)i;
+                    if (d2)
+                        d2[offsets[q] + c] = v;
+                }
+                ++c;
+            }
+        }
+        counts[q] = (int32_t)c;
+    }
+}
+
+/* Every point p with lo_j <= p_j <= hi_j for all j, per query in input-index
+ * order (counts / offsets / ids as orc_radius_brute). */
+void orc_box_brute(const float *pts, int64_t N, int D, const float *lo, const float *hi, int64_t Q,
+                   int32_t *counts, const int64_t *offsets, int32_t *ids)
+{
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t c = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            int in = 1;
+            for (int j = 0; j < D; ++j) {
+                float v = pts[i * D + j];
+                if (!(lo[q * D + j] <= v && v <= hi[q * D + j])) {
+                    in = 0;
+                    break;
+                }
+            }
+            if (in) {
+                if (ids)
+                    ids[offsets[q] + c] = (int32_t)i;
+                ++c;
+            }
+        }
+        counts[q] = (int32_t)c;
+    }
 }

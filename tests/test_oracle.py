@@ -466,3 +466,37 @@ def test_widest_traversal_matches_brute(seed):
         for ordered in (True, False):
             got = oracle.knn_tree_dims(pts, node_pid, node_dim, qs, k, r, ordered)
             assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+# ---------------------------------------------------------------- range queries
+
+@pytest.mark.parametrize("seed", range(3))
+def test_radius_brute_equals_unbounded_knn_within_radius(seed):
+    """The ball query is the kNN definition with k >= N and the same radius."""
+    g = np.random.default_rng(400 + seed)
+    N, D = 150, int(g.integers(1, 4))
+    pts = g.integers(0, 5, size=(N, D)).astype(np.float32) * np.float32(0.25) if seed % 2 else \
+        g.random((N, D)).astype(np.float32)
+    qs = g.random((30, D)).astype(np.float32)
+    r = 0.4
+    counts, offsets, ids, d2 = oracle.radius_brute(pts, qs, r)
+    ki, kd = oracle.knn_brute(pts, qs, N, r)
+    for q in range(len(qs)):
+        got = ids[offsets[q]:offsets[q + 1]]
+        want = ki[q][ki[q] >= 0]
+        assert counts[q] == len(want)
+        assert sorted(got.tolist()) == sorted(want.tolist())
+        order = np.argsort(got)
+        assert np.array_equal(d2[offsets[q]:offsets[q + 1]][order].view(np.uint32),
+                              kd[q][: len(want)][np.argsort(want)].view(np.uint32))
+
+
+def test_box_brute_equals_mask():
+    g = np.random.default_rng(7)
+    pts = g.integers(0, 6, size=(300, 3)).astype(np.float32)
+    lo = g.integers(0, 4, size=(40, 3)).astype(np.float32)
+    hi = lo + g.integers(0, 3, size=(40, 3)).astype(np.float32)
+    counts, offsets, ids = oracle.box_brute(pts, lo, hi)
+    for q in range(40):
+        want = np.nonzero(((pts >= lo[q]) & (pts <= hi[q])).all(axis=1))[0]
+        assert ids[offsets[q]:offsets[q + 1]].tolist() == want.tolist()
