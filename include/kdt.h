@@ -143,9 +143,31 @@ int kdt_knn(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, floa
 int kdt_knn_visits(const kdt_tree *tree, const float *d_queries, int64_t Q, int k,
                    float max_radius, int flags, int32_t *d_visits, void *stream);
 
+/* ---- range queries ---------------------------------------------------------
+ * Every point within a radius of a query point (ball, inclusive, the same FP32
+ * squared distance as kdt_knn) or inside an axis-aligned box (inclusive
+ * bounds), found with the unordered stack-free traversal and a fixed range
+ * (Sec. 3: other query primitives change only the range test and processNode).
+ * Two passes: *_count writes d_counts int32 [Q]; kdt_offsets turns counts into
+ * d_offsets int64 [Q+1] (exclusive prefix sums, offsets[Q] = total); *_fill
+ * writes query q's point ids (and, for balls, squared distances if d_d2 is not
+ * NULL) to [offsets[q], offsets[q+1]) in traversal order (deterministic). */
+int kdt_radius_count(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int32_t *d_counts,
+                     void *stream);
+int kdt_radius_fill(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius,
+                    const int64_t *d_offsets, int32_t *d_ids, float *d_d2, void *stream);
+int kdt_box_count(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q, int32_t *d_counts,
+                  void *stream);
+int kdt_box_fill(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q,
+                 const int64_t *d_offsets, int32_t *d_ids, void *stream);
+/* Exclusive prefix sum of counts into d_offsets int64 [Q+1]; if h_total is not
+ * NULL the stream is synchronised and *h_total receives offsets[Q]. */
+int kdt_offsets(const int32_t *d_counts, int64_t Q, int64_t *d_offsets, int64_t *h_total, void *stream);
+
 /* Synchronise `stream` and report device-side failures recorded on the tree
- * since the last call: KDT_ENONFINITE (asynchronous build) or KDT_ETRAVERSAL.
- * Clears the recorded state. */
+ * since the last call: KDT_ENONFINITE (asynchronous build), KDT_ETRAVERSAL, or
+ * KDT_EINVAL (a range fill whose offsets did not match its hits).  Clears the
+ * recorded state. */
 int kdt_status(kdt_tree *tree, void *stream);
 
 /* Release a tree and its device memory (synchronises the device first). */

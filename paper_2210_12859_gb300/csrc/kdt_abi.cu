@@ -293,8 +293,9 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     return KDT_OK;
 }
 
+// o2 may be NULL when the call has a single output
 static int check_query_args(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, const void *o1,
-                            const void *o2)
+                            const void *o2, bool one_output = false)
 {
     if (!t)
         return set_error(KDT_EINVAL, "tree is NULL");
@@ -304,7 +305,7 @@ static int check_query_args(const kdt_tree *t, const float *d_q, int64_t Q, int 
         return set_error(KDT_EINVAL, "k must be in [1, 64] (got %d)", k);
     if (bad_radius(max_radius))
         return set_error(KDT_EINVAL, "max_radius must be >= 0 (got %g)", (double)max_radius);
-    if (Q > 0 && (!d_q || !o1 || (o2 == (const void *)1 ? false : !o2)))
+    if (Q > 0 && (!d_q || !o1 || (!one_output && !o2)))
         return set_error(KDT_EINVAL, "NULL query or output pointer");
     if (Q >= ((int64_t)1 << 32))
         return set_error(KDT_EINVAL, "Q must be < 2^32");
@@ -501,7 +502,7 @@ int kdt_fcp(const kdt_tree *t, const float *d_q, int64_t Q, float max_radius, in
 int kdt_knn_visits(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, int flags,
                    int32_t *d_visits, void *stream)
 {
-    KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_visits, (const void *)1));
+    KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_visits, nullptr, true));
     if (Q == 0)
         return KDT_OK;
     if (flags & KDT_LEARNED)
@@ -524,6 +525,8 @@ int kdt_status(kdt_tree *t, void *stream)
         return set_error(KDT_ENONFINITE, "a point coordinate is NaN or infinite");
     if (h & ERR_TRAVERSAL)
         return set_error(KDT_ETRAVERSAL, "a traversal exceeded its step bound");
+    if (h & ERR_RANGE)
+        return set_error(KDT_EINVAL, "a range fill found a different number of points than its offsets allow");
     return KDT_OK;
 }
 

@@ -32,7 +32,7 @@ void note_launch();
 #define KDT_LAUNCH ::kdt::note_launch(),
 
 // device error word bits
-enum : int { ERR_NONFINITE = 1, ERR_TRAVERSAL = 2 };
+enum : int { ERR_NONFINITE = 1, ERR_TRAVERSAL = 2, ERR_RANGE = 4 };
 
 // ---------------------------------------------------------------- topology
 // A complete, left-balanced tree of n nodes in level order (root 0, children
@@ -155,6 +155,7 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *
 // scan_scratch_elems(n) elements
 size_t scan_scratch_elems(int64_t n);
 int exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *scratch, cudaStream_t s);
+int exclusive_scan_u64(unsigned long long *data, int64_t n, unsigned long long *scratch, cudaStream_t s);
 
 int num_sms();
 

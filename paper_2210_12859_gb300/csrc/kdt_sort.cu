@@ -21,12 +21,13 @@ constexpr int RADIX_ITEMS = 8;
 constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;
 constexpr int RADIX_WARPS = RADIX_THREADS / 32;
 
-__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v)
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T v)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        T u = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o)
             v += u;
     }
@@ -35,79 +36,83 @@ __device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v)
 
 // exclusive block scan of one value per thread; returns the exclusive prefix
 // and writes the block total to *total (all threads)
-__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t *s_warp, uint32_t *total)
+template <typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T *s_warp, T *total)
 {
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    uint32_t inc = warp_inclusive_sum(v);
+    T inc = warp_inclusive_sum(v);
     if (lane == 31)
         s_warp[w] = inc;
     __syncthreads();
     if (w == 0) {
-        uint32_t x = lane < nw ? s_warp[lane] : 0;
-        uint32_t xi = warp_inclusive_sum(x);
+        T x = lane < nw ? s_warp[lane] : T(0);
+        T xi = warp_inclusive_sum(x);
         if (lane < nw)
             s_warp[lane] = xi - x;
         if (lane == nw - 1)
             s_warp[32] = xi;
     }
     __syncthreads();
-    uint32_t r = s_warp[w] + inc - v;
+    T r = s_warp[w] + inc - v;
     *total = s_warp[32];
     __syncthreads();
     return r;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const uint32_t *__restrict__ data, int64_t n,
-                                                                     uint32_t *__restrict__ partials)
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const T *__restrict__ data, int64_t n,
+                                                                     T *__restrict__ partials)
 {
-    __shared__ uint32_t s_warp[33];
+    __shared__ T s_warp[33];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    uint32_t sum = 0;
+    T sum = 0;
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         int64_t i = base + (int64_t)j * SCAN_THREADS + threadIdx.x;
         if (i < n)
             sum += data[i];
     }
-    uint32_t total;
+    T total;
     block_exclusive_sum(sum, s_warp, &total);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = total;
 }
 
 // single block: exclusive scan of the tile totals, in chunks
-__global__ void __launch_bounds__(1024) scan_partials_kernel(uint32_t *__restrict__ partials, int64_t np)
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_partials_kernel(T *__restrict__ partials, int64_t np)
 {
-    __shared__ uint32_t s_warp[33];
-    uint32_t carry = 0;
+    __shared__ T s_warp[33];
+    T carry = 0;
     for (int64_t base = 0; base < np; base += 1024) {
         int64_t i = base + threadIdx.x;
-        uint32_t v = i < np ? partials[i] : 0;
-        uint32_t total;
-        uint32_t ex = block_exclusive_sum(v, s_warp, &total);
+        T v = i < np ? partials[i] : T(0);
+        T total;
+        T ex = block_exclusive_sum(v, s_warp, &total);
         if (i < np)
             partials[i] = carry + ex;
         carry += total;
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep_kernel(uint32_t *__restrict__ data, int64_t n,
-                                                                        const uint32_t *__restrict__ partials)
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep_kernel(T *__restrict__ data, int64_t n,
+                                                                        const T *__restrict__ partials)
 {
-    __shared__ uint32_t s_warp[33];
+    __shared__ T s_warp[33];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS];
-    uint32_t sum = 0;
+    T v[SCAN_ITEMS];
+    T sum = 0;
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         int64_t i = base + j;
-        v[j] = i < n ? data[i] : 0;
+        v[j] = i < n ? data[i] : T(0);
         sum += v[j];
     }
-    uint32_t total;
-    uint32_t run = block_exclusive_sum(sum, s_warp, &total) + partials[blockIdx.x];
+    T total;
+    T run = block_exclusive_sum(sum, s_warp, &total) + partials[blockIdx.x];
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         int64_t i = base + j;
@@ -115,6 +120,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_downsweep_kernel(uint32_t *
             data[i] = run;
         run += v[j];
     }
+}
+
+template <typename T>
+int exclusive_scan_t(T *data, int64_t n, T *scratch, cudaStream_t s)
+{
+    if (n <= 0)
+        return KDT_OK;
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    KDT_LAUNCH scan_reduce_kernel<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
+    KDT_LAUNCH scan_partials_kernel<T><<<1, 1024, 0, s>>>(scratch, tiles);
+    KDT_LAUNCH scan_downsweep_kernel<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
+    KDT_CUDA(cudaGetLastError());
+    return KDT_OK;
 }
 
 // ---- radix sort
@@ -208,14 +226,12 @@ size_t scan_scratch_elems(int64_t n)
 
 int exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *scratch, cudaStream_t s)
 {
-    if (n <= 0)
-        return KDT_OK;
-    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    KDT_LAUNCH scan_reduce_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
-    KDT_LAUNCH scan_partials_kernel<<<1, 1024, 0, s>>>(scratch, tiles);
-    KDT_LAUNCH scan_downsweep_kernel<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(data, n, scratch);
-    KDT_CUDA(cudaGetLastError());
-    return KDT_OK;
+    return exclusive_scan_t<uint32_t>(data, n, scratch, s);
+}
+
+int exclusive_scan_u64(unsigned long long *data, int64_t n, unsigned long long *scratch, cudaStream_t s)
+{
+    return exclusive_scan_t<unsigned long long>(data, n, scratch, s);
 }
 
 size_t radix_scratch_elems(int64_t n)

@@ -85,6 +85,11 @@ _sig("kdt_fcp", [_P, _P, _I64, _F, _I, _P, _P, _P])
 _sig("kdt_knn", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
 _sig("kdt_knn_visits", [_P, _P, _I64, _I, _F, _I, _P, _P])
 _sig("kdt_knn_static", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
+_sig("kdt_radius_count", [_P, _P, _I64, _F, _P, _P])
+_sig("kdt_radius_fill", [_P, _P, _I64, _F, _P, _P, _P, _P])
+_sig("kdt_box_count", [_P, _P, _P, _I64, _P, _P])
+_sig("kdt_box_fill", [_P, _P, _P, _I64, _P, _P, _P])
+_sig("kdt_offsets", [_P, _I64, _P, ctypes.POINTER(_I64), _P])
 _sig("kdt_status", [_P, _P])
 _sig("kdt_free", [_P], None)
 _sig("kdt_knn_host", [_P, _I64, _I, _P, _I64, _I, _F, _I, _P, _P])
@@ -315,6 +320,69 @@ def kdt_knn_visits(tree: Tree, queries: torch.Tensor, k: int, max_radius: float 
     _check(_lib.kdt_knn_visits(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, k,
                                float(max_radius), flags, ctypes.c_void_p(v.data_ptr()), _stream(stream)))
     return v
+
+
+def kdt_radius_count(tree: Tree, queries: torch.Tensor, radius: float, stream=None) -> torch.Tensor:
+    Q = queries.shape[0]
+    counts = torch.empty(Q, dtype=torch.int32, device=queries.device)
+    _check(_lib.kdt_radius_count(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, float(radius),
+                                 ctypes.c_void_p(counts.data_ptr()), _stream(stream)))
+    return counts
+
+
+def kdt_offsets(counts: torch.Tensor, stream=None):
+    """Exclusive prefix offsets [Q+1] (int64) of the counts and their total."""
+    Q = counts.shape[0]
+    off = torch.empty(Q + 1, dtype=torch.int64, device=counts.device)
+    total = _I64()
+    _check(_lib.kdt_offsets(_dev(counts, torch.int32, "counts"), Q, ctypes.c_void_p(off.data_ptr()),
+                            ctypes.byref(total), _stream(stream)))
+    return off, total.value
+
+
+def kdt_radius_fill(tree: Tree, queries: torch.Tensor, radius: float, offsets: torch.Tensor, total: int,
+                    with_d2: bool = True, stream=None):
+    Q = queries.shape[0]
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device=queries.device)
+    d2 = torch.empty(max(total, 1), dtype=torch.float32, device=queries.device) if with_d2 else None
+    _check(_lib.kdt_radius_fill(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, float(radius),
+                                _dev(offsets, torch.int64, "offsets", (Q + 1,)), ctypes.c_void_p(ids.data_ptr()),
+                                ctypes.c_void_p(d2.data_ptr()) if with_d2 else None, _stream(stream)))
+    return ids[:total], (d2[:total] if with_d2 else None)
+
+
+def kdt_radius_search(tree: Tree, queries: torch.Tensor, radius: float, stream=None):
+    """All points within `radius` of each query: (offsets [Q+1], ids, d2)."""
+    counts = kdt_radius_count(tree, queries, radius, stream)
+    off, total = kdt_offsets(counts, stream)
+    ids, d2 = kdt_radius_fill(tree, queries, radius, off, total, True, stream)
+    return off, ids, d2
+
+
+def kdt_box_count(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, stream=None) -> torch.Tensor:
+    Q = lo.shape[0]
+    counts = torch.empty(Q, dtype=torch.int32, device=lo.device)
+    _check(_lib.kdt_box_count(tree.handle, _dev(lo, torch.float32, "lo", (Q, tree.D)),
+                              _dev(hi, torch.float32, "hi", (Q, tree.D)), Q, ctypes.c_void_p(counts.data_ptr()),
+                              _stream(stream)))
+    return counts
+
+
+def kdt_box_fill(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, offsets: torch.Tensor, total: int, stream=None):
+    Q = lo.shape[0]
+    ids = torch.empty(max(total, 1), dtype=torch.int32, device=lo.device)
+    _check(_lib.kdt_box_fill(tree.handle, _dev(lo, torch.float32, "lo", (Q, tree.D)),
+                             _dev(hi, torch.float32, "hi", (Q, tree.D)), Q,
+                             _dev(offsets, torch.int64, "offsets", (Q + 1,)), ctypes.c_void_p(ids.data_ptr()),
+                             _stream(stream)))
+    return ids[:total]
+
+
+def kdt_box_search(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, stream=None):
+    """All points inside each box [lo, hi]: (offsets [Q+1], ids)."""
+    counts = kdt_box_count(tree, lo, hi, stream)
+    off, total = kdt_offsets(counts, stream)
+    return off, kdt_box_fill(tree, lo, hi, off, total, stream)
 
 
 def kdt_status(tree: Tree, stream=None) -> None:
