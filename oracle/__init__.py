@@ -56,6 +56,12 @@ def _load():
         lib.orc_radius_brute.restype = None
         lib.orc_box_brute.argtypes = [P, i64, i32, P, P, i64, P, P, P]
         lib.orc_box_brute.restype = None
+        lib.orc_range_stackfree.argtypes = [P, P, P, i64, i32, i32, P, P, i64, f32, P, P, P, P]
+        lib.orc_range_stackfree.restype = i32
+        lib.orc_range_reduce.argtypes = [P, P, P, i64, i32, P, i64, f32, P, i32, i32, P, P]
+        lib.orc_range_reduce.restype = i32
+        lib.orc_knn_reduce.argtypes = [P, P, i64, i32, P, i32, i32, P]
+        lib.orc_knn_reduce.restype = None
         lib.orc_build_widest.argtypes = [P, i64, i32, P, P]
         lib.orc_build_widest.restype = i32
         lib.orc_knn_stackfree_batch_dims.argtypes = [P, P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
@@ -169,6 +175,60 @@ def box_brute(points, lo, hi):
     ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
     lib.orc_box_brute(_ptr(pts), N, D, _ptr(lo), _ptr(hi), Q, _ptr(counts), _ptr(offsets), _ptr(ids))
     return counts, offsets, ids[: offsets[-1]]
+
+
+def range_tree(points, node_pid, qa, qb=None, radius: float = 0.0, node_dim=None):
+    """Ball (qb None, radius) or box ([qa, qb]) queries through the unordered
+    stack-free machine: (counts, offsets, ids, d2 or None), hits in traversal order."""
+    pts, qa = _f32(points), _f32(qa)
+    N, D = pts.shape
+    Q = qa.shape[0]
+    kind = 0 if qb is None else 1
+    qb = None if qb is None else _f32(qb)
+    pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    nd = None if node_dim is None else np.ascontiguousarray(node_dim, dtype=np.uint8)
+    lib = _load()
+    counts = np.empty(Q, dtype=np.int32)
+    args = (_ptr(pts), _ptr(pid), None if nd is None else _ptr(nd), N, D, kind, _ptr(qa),
+            None if qb is None else _ptr(qb), Q, float(radius))
+    assert lib.orc_range_stackfree(*args, _ptr(counts), None, None, None) == 0
+    offsets = np.zeros(Q + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    d2 = np.empty(max(int(offsets[-1]), 1), dtype=np.float32) if kind == 0 else None
+    assert lib.orc_range_stackfree(*args, _ptr(counts), _ptr(offsets), _ptr(ids),
+                                   None if d2 is None else _ptr(d2)) == 0
+    return counts, offsets, ids[: offsets[-1]], (None if d2 is None else d2[: offsets[-1]])
+
+
+REDUCE_SUM, REDUCE_MEAN, REDUCE_DENSITY = 0, 1, 2
+
+
+def range_reduce(points, node_pid, queries, radius: float, payload, mode: int, node_dim=None):
+    """Payload reductions over ball hits in traversal order: (out [Q][C], counts)."""
+    pts, qs = _f32(points), _f32(queries)
+    pl = _f32(payload)
+    N, D = pts.shape
+    Q, C = qs.shape[0], pl.shape[1]
+    pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    nd = None if node_dim is None else np.ascontiguousarray(node_dim, dtype=np.uint8)
+    out = np.empty((Q, C), dtype=np.float32)
+    counts = np.empty(Q, dtype=np.int32)
+    assert _load().orc_range_reduce(_ptr(pts), _ptr(pid), None if nd is None else _ptr(nd), N, D, _ptr(qs), Q,
+                                    float(radius), _ptr(pl), C, int(mode), _ptr(out), _ptr(counts)) == 0
+    return out, counts
+
+
+def knn_reduce(ids, d2, payload, mode: int):
+    """Payload reductions over kNN lists (ascending, -1 empty), in list order: out [Q][C]."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    d2 = _f32(d2)
+    pl = _f32(payload)
+    Q, k = ids.shape
+    C = pl.shape[1]
+    out = np.empty((Q, C), dtype=np.float32)
+    _load().orc_knn_reduce(_ptr(ids), _ptr(d2), Q, k, _ptr(pl), C, int(mode), _ptr(out))
+    return out
 
 
 def knn_brute(points, queries, k: int, max_radius: float = float("inf")):

@@ -26,6 +26,14 @@
  *   orc_knn_stackfree   the (curr, prev) state machine (Sec. 3.2)
  *   orc_radius_brute    every point within a radius / inside a box (the plain
  *   orc_box_brute       definition of the range queries Sec. 3 mentions)
+ *   orc_range_stackfree the same queries through the unordered stack-free
+ *                       machine with a fixed range (Sec. 3: other primitives
+ *                       change only the range test and processNode), hits in
+ *                       traversal order
+ *   orc_range_reduce    per-query reductions of a per-point payload over those
+ *   orc_knn_reduce      hits / over a kNN result (Sec. 3: point types with
+ *                       payload such as photon power; the photon-map density
+ *                       estimate of the photon-mapping application it cites)
  *   orc_descent_leaf    greedy close-child descent (feature of the learned
  *                       radius proposal; not in the paper)
  *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
@@ -752,5 +760,161 @@ void orc_box_brute(const float *pts, int64_t N, int D, const float *lo, const fl
             }
         }
         counts[q] = (int32_t)c;
+    }
+}
+
+/* Range queries over a built tree through the (curr, prev) machine of
+ * Sec. 3.2, unordered (left child first), with a fixed range instead of a
+ * shrinking one.  kind 0: the ball d2 <= r2 around a; kind 1: the box
+ * [a, b].  Children are entered as in the unordered kNN traversal: a child
+ * whose side holds the query, or whose plane is within range.  Missing
+ * children are stepped into and left, as in orc_stackfree.  Writes the hits'
+ * input indices (and d2 for balls) in traversal order, up to cap of them, and
+ * returns their number (or -1 if the step bound was exceeded). */
+static int64_t orc_range_one(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
+                             int kind, const float *a, const float *b, float r2, int32_t *ids, float *d2, int64_t cap)
+{
+    int64_t curr = 0, prev = -1, count = 0;
+    int64_t bound = 3 * (2 * N + 1) + 8;
+    for (int64_t step = 0; step < bound; ++step) {
+        int64_t parent = (curr + 1) / 2 - 1;
+        if (curr >= N) {
+            prev = curr;
+            curr = parent;
+            continue;
+        }
+        const float *p = pts + (int64_t)node_pid[curr] * D;
+        int from_parent = prev < curr;
+        if (from_parent) {
+            int hit;
+            float v = 0.0f;
+            if (kind == 0) {
+                v = orc_d2(p, a, D);
+                hit = v <= r2;
+            } else {
+                hit = 1;
+                for (int j = 0; j < D; ++j)
+                    if (!(a[j] <= p[j] && p[j] <= b[j]))
+                        hit = 0;
+            }
+            if (hit) {
+                if (count < cap) {
+                    ids[count] = node_pid[curr];
+                    if (d2)
+                        d2[count] = v;
+                }
+                ++count;
+            }
+        }
+        int dim = node_dim ? node_dim[curr] : orc_level(curr) % D;
+        float split = p[dim];
+        int left_in, right_in;
+        if (kind == 0) {
+            float sd = a[dim] - split;
+            left_in = sd <= 0.0f || sd * sd <= r2;
+            right_in = sd > 0.0f || sd * sd <= r2;
+        } else {
+            left_in = a[dim] <= split;   /* left subtree: coordinates <= split */
+            right_in = b[dim] >= split;  /* right subtree: coordinates >= split */
+        }
+        int64_t lc = 2 * curr + 1, rc = 2 * curr + 2, next;
+        if (from_parent)
+            next = left_in ? lc : (right_in ? rc : parent);
+        else if (prev == lc)
+            next = right_in ? rc : parent;
+        else
+            next = parent;
+        if (next == -1)
+            return count;
+        prev = curr;
+        curr = next;
+    }
+    return -1;
+}
+
+/* Many range queries; counts[q] = hits of query q; when ids is not NULL,
+ * query q's hits go to ids[offsets[q] ...] (and d2 for balls) in traversal
+ * order.  qb: upper corners (boxes) or NULL (balls).  Returns -1 if any
+ * traversal exceeded its step bound. */
+int orc_range_stackfree(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
+                        int kind, const float *qa, const float *qb, int64_t Q, float radius, int32_t *counts,
+                        const int64_t *offsets, int32_t *ids, float *d2)
+{
+    float r2 = radius * radius;
+    int rc = 0;
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t c;
+        if (ids)
+            c = orc_range_one(pts, node_pid, node_dim, N, D, kind, qa + q * D, kind ? qb + q * D : NULL, r2,
+                              ids + offsets[q], d2 ? d2 + offsets[q] : NULL, offsets[q + 1] - offsets[q]);
+        else
+            c = orc_range_one(pts, node_pid, node_dim, N, D, kind, qa + q * D, kind ? qb + q * D : NULL, r2,
+                              NULL, NULL, 0);
+        if (c < 0)
+            rc = -1;
+        counts[q] = (int32_t)c;
+    }
+    return rc;
+}
+
+/* Reductions of a payload (C floats per input point, input order).  The sum
+ * runs in FP32 over the hits in the order given, one addition at a time.
+ * mode 0: the sum; 1: the sum / count; 2: density, the sum / fl(pi_f * R2)
+ * with R2 the squared radius of the disc the hits were gathered from.  No
+ * hit: 0 in every mode. */
+#define ORC_PI_F 3.14159265358979323846f
+
+static void orc_reduce_one(const float *payload, int C, const int32_t *hits, int64_t n, int mode, float R2,
+                           float *out)
+{
+    for (int c = 0; c < C; ++c) {
+        float s = 0.0f;
+        for (int64_t i = 0; i < n; ++i)
+            s = s + payload[(int64_t)hits[i] * C + c];
+        if (n == 0)
+            s = 0.0f;
+        else if (mode == 1)
+            s = s / (float)n;
+        else if (mode == 2)
+            s = s / (ORC_PI_F * R2);
+        out[c] = s;
+    }
+}
+
+/* Ball queries (radius r, R2 = fl(r * r)) through orc_range_one, reduced in
+ * traversal order: out [Q][C]; counts [Q] may be NULL. */
+int orc_range_reduce(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
+                     const float *qs, int64_t Q, float radius, const float *payload, int C, int mode, float *out,
+                     int32_t *counts)
+{
+    float r2 = radius * radius;
+    int32_t *hits = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
+    int rc = 0;
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t n = orc_range_one(pts, node_pid, node_dim, N, D, 0, qs + q * D, NULL, r2, hits, NULL, N);
+        if (n < 0) {
+            rc = -1;
+            n = 0;
+        }
+        orc_reduce_one(payload, C, hits, n, mode, r2, out + q * C);
+        if (counts)
+            counts[q] = (int32_t)n;
+    }
+    free(hits);
+    return rc;
+}
+
+/* Reductions over kNN results (ids / d2 [Q][k], ascending, -1 = empty), in
+ * list order; R2 = the largest d2 found (the disc through the farthest
+ * neighbour, as in the photon-map radiance estimate). */
+void orc_knn_reduce(const int32_t *ids, const float *d2, int64_t Q, int k, const float *payload, int C, int mode,
+                    float *out)
+{
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t n = 0;
+        while (n < k && ids[q * k + n] >= 0)
+            ++n;
+        float R2 = n ? d2[q * k + n - 1] : 0.0f;
+        orc_reduce_one(payload, C, ids + q * k, n, mode, R2, out + q * C);
     }
 }

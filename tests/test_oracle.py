@@ -500,3 +500,132 @@ def test_box_brute_equals_mask():
     for q in range(40):
         want = np.nonzero(((pts >= lo[q]) & (pts <= hi[q])).all(axis=1))[0]
         assert ids[offsets[q]:offsets[q + 1]].tolist() == want.tolist()
+
+
+# ------------------------------------------------- range queries on the tree
+
+def _preorder_rank(N):
+    """Preorder position of every node of a level-order complete tree (explicit stack)."""
+    rank = np.empty(N, dtype=np.int64)
+    stack, r = [0], 0
+    while stack:
+        n = stack.pop()
+        if n >= N:
+            continue
+        rank[n] = r
+        r += 1
+        stack.append(2 * n + 2)
+        stack.append(2 * n + 1)
+    return rank
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_range_traversal_hits_equal_brute_in_preorder(seed):
+    """The stack-free range traversal finds exactly the brute-force hit set, and
+    (left child first, node before its subtrees) lists them in preorder."""
+    g = np.random.default_rng(500 + seed)
+    N, D = int(g.integers(1, 400)), int(g.integers(1, 5))
+    pts = g.random((N, D)).astype(np.float32)
+    if seed % 2:
+        pts = g.integers(0, 5, size=(N, D)).astype(np.float32) * np.float32(0.25)
+    widest = seed % 3 == 2 and D <= 3
+    if widest:
+        pid, dims = oracle.build_widest(pts)
+    else:
+        pid, dims = oracle.build(pts), None
+    node_of = np.empty(N, dtype=np.int64)
+    node_of[pid] = np.arange(N)
+    rank = _preorder_rank(N)
+    qs = (g.random((40, D)) * 1.2 - 0.1).astype(np.float32)
+    qs[:10] = pts[g.integers(0, N, 10)]
+    for r in (0.0, 0.1, 0.35, np.inf):
+        c, off, ids, d2 = oracle.range_tree(pts, pid, qs, radius=r, node_dim=dims)
+        wc, woff, wids, wd2 = oracle.radius_brute(pts, qs, r)
+        assert np.array_equal(c, wc)
+        for q in range(len(qs)):
+            got, gd = ids[off[q]:off[q + 1]], d2[off[q]:off[q + 1]]
+            o = np.argsort(got)
+            assert np.array_equal(got[o], wids[woff[q]:woff[q + 1]])
+            assert np.array_equal(gd[o].view(np.uint32), wd2[woff[q]:woff[q + 1]].view(np.uint32))
+            assert np.all(np.diff(rank[node_of[got]]) > 0)
+    lo = (g.random((40, D)) * 0.8).astype(np.float32)
+    hi = lo + (g.random((40, D)) * 0.5).astype(np.float32)
+    lo[:5], hi[:5] = pts[:5], pts[:5]
+    c, off, ids, _ = oracle.range_tree(pts, pid, lo, hi, node_dim=dims)
+    wc, woff, wids = oracle.box_brute(pts, lo, hi)
+    assert np.array_equal(c, wc)
+    for q in range(len(lo)):
+        got = ids[off[q]:off[q + 1]]
+        assert np.array_equal(np.sort(got), wids[woff[q]:woff[q + 1]])
+        assert np.all(np.diff(rank[node_of[got]]) > 0)
+
+
+def test_range_traversal_six_point_example():
+    """Figure 1's six points: a ball of radius 3 around (7,2) holds (7,2) (d2 0),
+    (5,4) (d2 8) and (8,1) (d2 2), not (9,6) (d2 20); the traversal meets them as
+    the root, then in the left subtree, then in the right subtree."""
+    gd = json.load(open(GOLDEN))
+    pts = np.array(gd["points"], dtype=np.float32)
+    pid = oracle.build(pts)
+    q = np.array([[7.0, 2.0]], dtype=np.float32)
+    c, off, ids, d2 = oracle.range_tree(pts, pid, q, radius=3.0)
+    names = [tuple(pts[i].tolist()) for i in ids]
+    assert names == [(7.0, 2.0), (5.0, 4.0), (8.0, 1.0)]
+    assert d2.tolist() == [0.0, 8.0, 2.0]
+
+
+def test_payload_reductions_integer_payload_exact():
+    """Small-integer payloads sum exactly in FP32: the reductions equal integer
+    sums over the brute-force hit sets; the density times pi R^2 gives the sum back."""
+    g = np.random.default_rng(9)
+    N, D, C = 3000, 3, 4
+    pts = g.random((N, D)).astype(np.float32)
+    pay = g.integers(-50, 50, size=(N, C)).astype(np.float32)
+    pid = oracle.build(pts)
+    qs = g.random((60, D)).astype(np.float32)
+    r = 0.12
+    _, woff, wids, _ = oracle.radius_brute(pts, qs, r)
+    s, cnt = oracle.range_reduce(pts, pid, qs, r, pay, oracle.REDUCE_SUM)
+    m, _ = oracle.range_reduce(pts, pid, qs, r, pay, oracle.REDUCE_MEAN)
+    dn, _ = oracle.range_reduce(pts, pid, qs, r, pay, oracle.REDUCE_DENSITY)
+    r2 = float(np.float32(r) * np.float32(r))
+    for q in range(len(qs)):
+        hit = wids[woff[q]:woff[q + 1]]
+        want = pay[hit].astype(np.int64).sum(0)
+        assert cnt[q] == len(hit)
+        assert np.array_equal(s[q], want.astype(np.float32))
+        if len(hit):
+            assert np.allclose(m[q], want / len(hit), rtol=1e-6, atol=0)
+            assert np.allclose(dn[q] * np.pi * r2, want, rtol=1e-5, atol=1e-5)
+        else:
+            assert not m[q].any() and not dn[q].any()
+    # kNN: over the k best, R^2 = the farthest found neighbour's d2
+    k = 10
+    ki, kd = oracle.knn_brute(pts, qs, k, 0.05)
+    ks = oracle.knn_reduce(ki, kd, pay, oracle.REDUCE_SUM)
+    kdn = oracle.knn_reduce(ki, kd, pay, oracle.REDUCE_DENSITY)
+    for q in range(len(qs)):
+        v = ki[q][ki[q] >= 0]
+        want = pay[v].astype(np.int64).sum(0)
+        assert np.array_equal(ks[q], want.astype(np.float32))
+        if len(v):
+            R2 = float(kd[q][len(v) - 1])
+            assert R2 == float(kd[q][ki[q] >= 0].max())
+            assert np.allclose(kdn[q] * np.pi * R2, want, rtol=1e-5, atol=1e-5)
+
+
+def test_payload_sum_float_within_rounding_bound():
+    """Float payloads: the sequential FP32 sum is within n * eps * sum|x| of the FP64 sum."""
+    g = np.random.default_rng(10)
+    N, D, C = 2000, 2, 3
+    pts = g.random((N, D)).astype(np.float32)
+    pay = g.standard_normal((N, C)).astype(np.float32)
+    pid = oracle.build(pts)
+    qs = g.random((50, D)).astype(np.float32)
+    s, cnt = oracle.range_reduce(pts, pid, qs, 0.1, pay, oracle.REDUCE_SUM)
+    _, woff, wids, _ = oracle.radius_brute(pts, qs, 0.1)
+    eps = np.finfo(np.float32).eps
+    for q in range(len(qs)):
+        x = pay[wids[woff[q]:woff[q + 1]]].astype(np.float64)
+        bound = len(x) * eps * np.abs(x).sum(0) + 1e-30
+        assert np.all(np.abs(s[q] - x.sum(0)) <= bound)
