@@ -145,24 +145,58 @@ int kdt_knn_visits(const kdt_tree *tree, const float *d_queries, int64_t Q, int 
 
 /* ---- range queries ---------------------------------------------------------
  * Every point within a radius of a query point (ball, inclusive, the same FP32
- * squared distance as kdt_knn) or inside an axis-aligned box (inclusive
- * bounds), found with the unordered stack-free traversal and a fixed range
- * (Sec. 3: other query primitives change only the range test and processNode).
+ * squared distance as kdt_knn: d2 <= fl(radius * radius)) or inside an
+ * axis-aligned box (inclusive bounds; lo > hi in any dimension gives none),
+ * found with the unordered stack-free traversal and a fixed range (Sec. 3:
+ * other query primitives change only the range test and processNode).
+ * Queries float [Q][D] (ball centres, box lower / upper corners), device.
  * Two passes: *_count writes d_counts int32 [Q]; kdt_offsets turns counts into
  * d_offsets int64 [Q+1] (exclusive prefix sums, offsets[Q] = total); *_fill
  * writes query q's point ids (and, for balls, squared distances if d_d2 is not
- * NULL) to [offsets[q], offsets[q+1]) in traversal order (deterministic). */
-int kdt_radius_count(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int32_t *d_counts,
-                     void *stream);
-int kdt_radius_fill(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius,
+ * NULL) to [offsets[q], offsets[q+1]) in traversal order, the same on every
+ * call.  flags: 0 or KDT_MORTON (queries run in Morton order; results are the
+ * same); any other bit is KDT_EINVAL.  A fill whose hits do not match its
+ * offsets writes nothing outside the query's slice and is reported by
+ * kdt_status.  Buffers are the caller's; nothing is kept after the call. */
+int kdt_radius_count(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int flags,
+                     int32_t *d_counts, void *stream);
+int kdt_radius_fill(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int flags,
                     const int64_t *d_offsets, int32_t *d_ids, float *d_d2, void *stream);
-int kdt_box_count(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q, int32_t *d_counts,
-                  void *stream);
-int kdt_box_fill(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q,
+int kdt_box_count(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q, int flags,
+                  int32_t *d_counts, void *stream);
+int kdt_box_fill(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q, int flags,
                  const int64_t *d_offsets, int32_t *d_ids, void *stream);
 /* Exclusive prefix sum of counts into d_offsets int64 [Q+1]; if h_total is not
  * NULL the stream is synchronised and *h_total receives offsets[Q]. */
 int kdt_offsets(const int32_t *d_counts, int64_t Q, int64_t *d_offsets, int64_t *h_total, void *stream);
+
+/* ---- payloads and reductions ------------------------------------------------
+ * Sec. 3: the point type may carry payload data (its example: surface normal
+ * and photon power for photon mapping, the application Sec. 1 cites).  A
+ * payload is C floats per point (1 <= C <= KDT_PAYLOAD_MAX_C), given in input
+ * order float [N][C]; the tree keeps its own copy in node order (N*C*4 + N*4
+ * bytes, freed with the tree, dropped by kdt_rebuild).  Synchronises `stream`.
+ * Reductions sum a payload over each query's hits, in FP32, one addition at a
+ * time, in a fixed order, and write d_out float [Q][C]:
+ *   KDT_REDUCE_SUM      the sum;
+ *   KDT_REDUCE_MEAN     the sum / the number of hits;
+ *   KDT_REDUCE_DENSITY  the sum / fl(pi * R2), the photon-map density estimate
+ *                       (R2: kdt_radius_reduce fl(radius^2), the gather disc;
+ *                       kdt_knn_reduce the largest d2 found, the disc through
+ *                       the farthest neighbour);
+ * a query with no hit gets 0 in every mode.  kdt_radius_reduce sums over the
+ * ball's hits in traversal order (d_counts int32 [Q] may be NULL; flags as for
+ * the range queries); kdt_knn_reduce over the kNN result in ascending (d2, id)
+ * order (k, max_radius and flags as kdt_knn). */
+#define KDT_PAYLOAD_MAX_C 8
+#define KDT_REDUCE_SUM 0
+#define KDT_REDUCE_MEAN 1
+#define KDT_REDUCE_DENSITY 2
+int kdt_tree_set_payload(kdt_tree *tree, const float *d_payload, int C, void *stream);
+int kdt_radius_reduce(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int flags, int mode,
+                      float *d_out, int32_t *d_counts, void *stream);
+int kdt_knn_reduce(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, float max_radius, int flags,
+                   int mode, float *d_out, void *stream);
 
 /* Synchronise `stream` and report device-side failures recorded on the tree
  * since the last call: KDT_ENONFINITE (asynchronous build), KDT_ETRAVERSAL, or

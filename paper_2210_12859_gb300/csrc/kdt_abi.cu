@@ -58,59 +58,6 @@ int grid_for_kernel(const void *fn, int threads, size_t smem)
     return g;
 }
 
-static void pool_setup_once()
-{
-    static bool done[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || done[dev])
-        return;
-    done[dev] = true;
-    // keep freed scratch in the stream-ordered pool of this process instead of
-    // returning it to the driver after every call
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-}
-
-// stream-ordered scratch released at scope exit
-struct Scratch {
-    void *p = nullptr;
-    cudaStream_t s = nullptr;
-    explicit Scratch(cudaStream_t s_) : s(s_) {}
-    int alloc(size_t bytes)
-    {
-        KDT_CUDA(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s));
-        return KDT_OK;
-    }
-    ~Scratch()
-    {
-        if (p)
-            cudaFreeAsync(p, s);
-    }
-};
-
-struct Carve {
-    char *base;
-    size_t off = 0;
-    template <class T> T *take(size_t n)
-    {
-        T *r = (T *)(base + off);
-        off += (n * sizeof(T) + 255) & ~(size_t)255;
-        return r;
-    }
-};
-
-static size_t carve_size(std::initializer_list<size_t> bytes)
-{
-    size_t s = 0;
-    for (size_t b : bytes)
-        s += (b + 255) & ~(size_t)255;
-    return s;
-}
-
 static bool bad_radius(float r) { return !(r >= 0.f); }
 
 // ---------------------------------------------------------------- Morton order
@@ -444,6 +391,15 @@ int kdt_rebuild(kdt_tree *t, const float *d_points, int opts, void *stream)
         return set_error(KDT_EINVAL, "tree is NULL");
     KDT_TRY(check_build_args(d_points, t->N, t->D));
     cudaStream_t s = (cudaStream_t)stream;
+    if (t->payload_c) {
+        // the payload follows the old node order: drop it
+        KDT_CUDA(cudaStreamSynchronize(s));
+        cudaFree(t->payload);
+        cudaFree(t->node_of);
+        t->payload = nullptr;
+        t->node_of = nullptr;
+        t->payload_c = 0;
+    }
     int64_t off[2] = {0, t->N};
     KDT_TRY(build_forest(d_points, off, 1, t->D, t->nodes, t->ids, t->bbox, t->err, s, t->layout == 3));
     return finish_build(t, opts, s);
@@ -539,6 +495,8 @@ void kdt_free(kdt_tree *t)
     cudaFree(t->ids);
     cudaFree(t->bbox);
     cudaFree(t->err);
+    cudaFree(t->payload);
+    cudaFree(t->node_of);
     free_model(t);
     if (t->prof) {
         Prof *p = (Prof *)t->prof;

@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA translation units of the library.
 #pragma once
 
+#include <initializer_list>
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -159,6 +161,67 @@ int exclusive_scan_u64(unsigned long long *data, int64_t n, unsigned long long *
 
 int num_sms();
 
+// permutation of queries along the Morton curve (traversal order -> query index)
+int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s);
+size_t morton_scratch_bytes(int64_t Q);
+
+// ---------------------------------------------------------------- scratch
+
+inline void pool_setup_once()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev])
+        return;
+    done[dev] = true;
+    // keep freed scratch in the stream-ordered pool of this process instead of
+    // returning it to the driver after every call
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+}
+
+// stream-ordered scratch released at scope exit
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    explicit Scratch(cudaStream_t s_) : s(s_) {}
+    int alloc(size_t bytes)
+    {
+        KDT_CUDA(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s));
+        return KDT_OK;
+    }
+    ~Scratch()
+    {
+        if (p)
+            cudaFreeAsync(p, s);
+    }
+};
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    template <class T> T *take(size_t n)
+    {
+        T *r = (T *)(base + off);
+        off += (n * sizeof(T) + 255) & ~(size_t)255;
+        return r;
+    }
+};
+
+inline size_t carve_size(std::initializer_list<size_t> bytes)
+{
+    size_t s = 0;
+    for (size_t b : bytes)
+        s += (b + 255) & ~(size_t)255;
+    return s;
+}
+
+
 // ---------------------------------------------------------------- objects
 
 struct Model {
@@ -196,6 +259,11 @@ struct kdt_tree {
     // top tree levels staged in shared memory by the traversal kernels
     // (-1: the tuned or default depth for this tree's shape)
     int stage_levels = -1;
+    // per-point payload in node order [N][payload_c] and node_of[input index]
+    // (kdt_tree_set_payload; dropped by a rebuild)
+    float *payload = nullptr;
+    int32_t *node_of = nullptr;
+    int payload_c = 0;
     // profiling
     bool profiling = false;
     void *prof = nullptr;

@@ -1,16 +1,23 @@
-// Range queries: every point within a fixed radius of a query point (ball), or
+// Range queries and payload reductions.
+//
+// Ball: every point within a fixed radius of a query point; box: every point
 // inside an axis-aligned box.  Sec. 3 notes that other query primitives only
 // change the in-range test and what processNode does, and that a non-ordered
 // traversal is a simplification of the ordered one; both queries use the
 // unordered stack-free machine (left child first, a child is entered iff it
 // can hold a point in range) with a fixed range instead of a shrinking one.
-//
-// Output protocol: a count pass writes each query's number of hits; the
-// caller (or kdt_offsets) turns the counts into exclusive prefix offsets; a
-// fill pass writes query q's hits to [offsets[q], offsets[q+1]) in traversal
-// order.  A fill whose hits disagree with its offsets writes nothing beyond
-// its slice and records the mismatch for kdt_status.
-#include <algorithm>
+// The kernel is templated over the processNode action:
+//   ACT_COUNT   count the hits;
+//   ACT_FILL    write the hits to the query's slice [offsets[q], offsets[q+1])
+//               in traversal order (count and fill walk the same nodes in the
+//               same order, so no atomics are needed);
+//   ACT_REDUCE  sum a per-point payload over the hits in traversal order (the
+//               point types with payload, e.g. photon power, that Sec. 3 names;
+//               the fixed-radius photon-map density estimate on top).
+// A payload is attached to the tree in node order, so that its loads follow
+// the node loads of the traversal; kNN reductions gather it through the
+// inverse permutation after an ordinary kNN query.
+#include <string.h>
 
 #include "kdt_learned.cuh"
 #include "kdt_query.cuh"
@@ -19,6 +26,9 @@ namespace kdt {
 namespace {
 
 constexpr int RANGE_THREADS = 128;
+enum : int { ACT_COUNT = 0, ACT_FILL = 1, ACT_REDUCE = 2 };
+// binary32 rounding of pi
+constexpr float PI_F = 3.14159265358979323846f;
 
 struct RangeArgs {
     const float4 *nodes;
@@ -27,11 +37,16 @@ struct RangeArgs {
     const float *a;  // ball: centres; box: lower corners   [Q][D]
     const float *b;  // box: upper corners                  [Q][D]
     int64_t Q;
+    const uint32_t *perm;  // traversal order -> query index, or NULL
     float r2;
     int32_t *counts;
     const int64_t *offsets;
     int32_t *out_ids;
     float *out_d2;
+    const float *payload;  // [N][C] in node order (ACT_REDUCE)
+    int C;
+    int mode;              // KDT_REDUCE_*
+    float *out;            // [Q][C] (ACT_REDUCE)
     int *err;
     unsigned long long *counter;
 };
@@ -64,14 +79,29 @@ __device__ __forceinline__ int64_t claim(bool need, unsigned long long *counter)
     return slot;
 }
 
+// Final value of a reduction: no hit -> 0; mean: / count; density: / fl(pi * R2).
+__device__ __forceinline__ float finish_reduce(float s, int64_t n, int mode, float R2)
+{
+    if (n == 0)
+        return 0.f;
+    if (mode == KDT_REDUCE_MEAN)
+        return __fdiv_rn(s, (float)n);
+    if (mode == KDT_REDUCE_DENSITY)
+        return __fdiv_rn(s, __fmul_rn(PI_F, R2));
+    return s;
+}
+
 // KIND 0: ball of squared radius r2 around a[q]; KIND 1: box [a[q], b[q]].
-template <int LAYOUT, int KIND, bool FILL>
+// Persistent blocks; every lane claims its next query when its current one
+// ends (checked every STEPS_PER_CLAIM steps), as in the kNN kernel.
+template <int LAYOUT, int KIND, int ACT>
 __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
     int64_t qi = -1;
     bool exhausted = false;
     float lo[NC], hi[NC];
+    float acc[KDT_PAYLOAD_MAX_C];
     int curr = 0, prev = -1, dim = 0;
     uint32_t steps = 0;
     int64_t count = 0, base = 0, limit = 0;
@@ -81,7 +111,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
         const int64_t slot = claim(need, a.counter);
         if (need) {
             if (slot < a.Q) {
-                qi = slot;
+                qi = a.perm ? (int64_t)a.perm[slot] : slot;
                 load_query<LAYOUT>(a.a, qi, a.D, lo);
                 if (KIND == 1)
                     load_query<LAYOUT>(a.b, qi, a.D, hi);
@@ -90,9 +120,14 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                 dim = 0;
                 steps = 0;
                 count = 0;
-                if (FILL) {
+                if (ACT == ACT_FILL) {
                     base = a.offsets[qi];
                     limit = a.offsets[qi + 1] - base;
+                }
+                if (ACT == ACT_REDUCE) {
+#pragma unroll
+                    for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                        acc[c] = 0.f;
                 }
             } else {
                 exhausted = true;
@@ -124,10 +159,17 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                         hit = hit && lo[j] <= nd.c[j] && nd.c[j] <= hi[j];
                 }
                 if (hit) {
-                    if (FILL && count < limit) {
+                    if (ACT == ACT_FILL && count < limit) {
                         a.out_ids[base + count] = (int32_t)node_id<LAYOUT>(nd, a.ids, curr);
                         if (KIND == 0 && a.out_d2)
                             a.out_d2[base + count] = d2;
+                    }
+                    if (ACT == ACT_REDUCE) {
+                        const float *p = a.payload + (int64_t)curr * a.C;
+#pragma unroll
+                        for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                            if (c < a.C)
+                                acc[c] = __fadd_rn(acc[c], __ldg(p + c));
                     }
                     ++count;
                 }
@@ -169,53 +211,71 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
         }
         if (!done)
             continue;
-        if (FILL) {
+        if (ACT == ACT_FILL) {
             if (count != limit)
                 atomicOr(a.err, ERR_RANGE);
         } else {
-            a.counts[qi] = (int32_t)count;
+            if (a.counts)
+                a.counts[qi] = (int32_t)count;
+            if (ACT == ACT_REDUCE) {
+#pragma unroll
+                for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                    if (c < a.C)
+                        a.out[qi * a.C + c] = finish_reduce(acc[c], count, a.mode, a.r2);
+            }
         }
         qi = -1;
     }
 }
 
-template <int LAYOUT>
-int launch_range_layout(int kind, bool fill, const RangeArgs &a, cudaStream_t s)
+template <int LAYOUT, int KIND, int ACT>
+int launch_one(const RangeArgs &a, cudaStream_t s)
 {
-    const void *fn;
-    if (kind == 0)
-        fn = fill ? (const void *)range_kernel<LAYOUT, 0, true> : (const void *)range_kernel<LAYOUT, 0, false>;
-    else
-        fn = fill ? (const void *)range_kernel<LAYOUT, 1, true> : (const void *)range_kernel<LAYOUT, 1, false>;
-    const int grid = grid_for_kernel(fn, RANGE_THREADS, 0);
-    KDT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
-    if (kind == 0 && fill)
-        KDT_LAUNCH range_kernel<LAYOUT, 0, true><<<grid, RANGE_THREADS, 0, s>>>(a);
-    else if (kind == 0)
-        KDT_LAUNCH range_kernel<LAYOUT, 0, false><<<grid, RANGE_THREADS, 0, s>>>(a);
-    else if (fill)
-        KDT_LAUNCH range_kernel<LAYOUT, 1, true><<<grid, RANGE_THREADS, 0, s>>>(a);
-    else
-        KDT_LAUNCH range_kernel<LAYOUT, 1, false><<<grid, RANGE_THREADS, 0, s>>>(a);
+    const int grid = grid_for_kernel((const void *)range_kernel<LAYOUT, KIND, ACT>, RANGE_THREADS, 0);
+    KDT_LAUNCH range_kernel<LAYOUT, KIND, ACT><<<grid, RANGE_THREADS, 0, s>>>(a);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
 
-int run_range(const kdt_tree *t, int kind, bool fill, const float *qa, const float *qb, int64_t Q, float r2,
-              int32_t *counts, const int64_t *offsets, int32_t *out_ids, float *out_d2, cudaStream_t s)
+template <int LAYOUT>
+int launch_range_layout(int kind, int act, const RangeArgs &a, cudaStream_t s)
 {
-    unsigned long long *counter = nullptr;
-    KDT_CUDA(cudaMallocAsync(&counter, 256, s));
-    RangeArgs a{t->nodes, t->ids, (int)t->N, t->D, qa, qb, Q, r2, counts, offsets, out_ids, out_d2, t->err, counter};
-    int rc;
-    switch (t->layout) {
-    case 0: rc = launch_range_layout<0>(kind, fill, a, s); break;
-    case 1: rc = launch_range_layout<1>(kind, fill, a, s); break;
-    case 3: rc = launch_range_layout<3>(kind, fill, a, s); break;
-    default: rc = launch_range_layout<2>(kind, fill, a, s); break;
+    if (kind == 0) {
+        if (act == ACT_COUNT)
+            return launch_one<LAYOUT, 0, ACT_COUNT>(a, s);
+        if (act == ACT_FILL)
+            return launch_one<LAYOUT, 0, ACT_FILL>(a, s);
+        return launch_one<LAYOUT, 0, ACT_REDUCE>(a, s);
     }
-    cudaFreeAsync(counter, s);
-    return rc;
+    if (act == ACT_COUNT)
+        return launch_one<LAYOUT, 1, ACT_COUNT>(a, s);
+    return launch_one<LAYOUT, 1, ACT_FILL>(a, s);
+}
+
+int run_range(const kdt_tree *t, int kind, int act, int flags, RangeArgs a, cudaStream_t s)
+{
+    pool_setup_once();
+    const bool morton = flags & KDT_MORTON;
+    Scratch sc(s);
+    KDT_TRY(sc.alloc(carve_size({64}) + (morton ? morton_scratch_bytes(a.Q) : 0)));
+    Carve c{(char *)sc.p};
+    a.counter = c.take<unsigned long long>(8);
+    a.nodes = t->nodes;
+    a.ids = t->ids;
+    a.N = (int)t->N;
+    a.D = t->D;
+    a.err = t->err;
+    a.perm = nullptr;
+    if (morton)
+        KDT_TRY(morton_order(a.a, a.Q, t->D, t->bbox, 1, nullptr, 0, nullptr, t->N, t->layout == 3, c.base + c.off,
+                             const_cast<uint32_t **>(&a.perm), s));
+    KDT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
+    switch (t->layout) {
+    case 0: return launch_range_layout<0>(kind, act, a, s);
+    case 1: return launch_range_layout<1>(kind, act, a, s);
+    case 3: return launch_range_layout<3>(kind, act, a, s);
+    default: return launch_range_layout<2>(kind, act, a, s);
+    }
 }
 
 __global__ void counts_to_u64_kernel(const int32_t *__restrict__ counts, int64_t Q, unsigned long long *__restrict__ out)
@@ -224,7 +284,57 @@ __global__ void counts_to_u64_kernel(const int32_t *__restrict__ counts, int64_t
         out[i] = i < Q ? (unsigned long long)(counts[i] > 0 ? counts[i] : 0) : 0ull;
 }
 
-int check_range(const kdt_tree *t, int64_t Q, const void *a, const void *b, bool need_b)
+// payload[id][C] (input order) -> node order; node_of[id] = node
+template <int LAYOUT>
+__global__ void payload_permute_kernel(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids, int64_t N,
+                                       const float *__restrict__ in, int C, float *__restrict__ out,
+                                       int32_t *__restrict__ node_of)
+{
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const NodeVal<LAYOUT> nd = fetch<LAYOUT, false>(nodes, nullptr, 0, (int)n);
+        const int64_t id = node_id<LAYOUT>(nd, ids, (int)n);
+        for (int c = 0; c < C; ++c)
+            out[n * C + c] = in[id * C + c];
+        node_of[id] = (int32_t)n;
+    }
+}
+
+// Sum of the payload over each query's kNN list in list order (ascending
+// (d2, id)); density radius R2 = the farthest found neighbour's d2.
+__global__ void knn_reduce_kernel(const int32_t *__restrict__ ids, const float *__restrict__ d2, int64_t Q, int k,
+                                  const int32_t *__restrict__ node_of, const float *__restrict__ payload, int C,
+                                  int mode, float *__restrict__ out)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *row = ids + q * k;
+        int n = 0;
+        while (n < k && row[n] >= 0)
+            ++n;
+        const float R2 = n ? d2[q * k + n - 1] : 0.f;
+        float acc[KDT_PAYLOAD_MAX_C];
+#pragma unroll
+        for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+            acc[c] = 0.f;
+        for (int i = 0; i < n; ++i) {
+            const float *p = payload + (int64_t)node_of[row[i]] * C;
+#pragma unroll
+            for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                if (c < C)
+                    acc[c] = __fadd_rn(acc[c], __ldg(p + c));
+        }
+#pragma unroll
+        for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+            if (c < C)
+                out[q * C + c] = finish_reduce(acc[c], n, mode, R2);
+    }
+}
+
+unsigned grid_for(int64_t n)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
+}
+
+int check_range(const kdt_tree *t, int64_t Q, const void *a, const void *b, bool need_b, int flags)
 {
     if (!t)
         return set_error(KDT_EINVAL, "tree is NULL");
@@ -232,7 +342,23 @@ int check_range(const kdt_tree *t, int64_t Q, const void *a, const void *b, bool
         return set_error(KDT_EINVAL, "Q must be in [0, 2^32)");
     if (Q > 0 && (!a || (need_b && !b)))
         return set_error(KDT_EINVAL, "NULL query pointer");
+    if (flags & ~KDT_MORTON)
+        return set_error(KDT_EINVAL, "range queries take no flag but KDT_MORTON (got %#x)", flags);
     return KDT_OK;
+}
+
+int check_radius(float radius)
+{
+    if (!(radius >= 0.f))
+        return set_error(KDT_EINVAL, "radius must be >= 0 (got %g)", (double)radius);
+    return KDT_OK;
+}
+
+RangeArgs blank_args()
+{
+    RangeArgs a;
+    memset(&a, 0, sizeof(a));
+    return a;
 }
 
 }  // namespace
@@ -242,49 +368,73 @@ using namespace kdt;
 
 extern "C" {
 
-int kdt_radius_count(const kdt_tree *t, const float *d_q, int64_t Q, float radius, int32_t *d_counts, void *stream)
+int kdt_radius_count(const kdt_tree *t, const float *d_q, int64_t Q, float radius, int flags, int32_t *d_counts,
+                     void *stream)
 {
-    KDT_TRY(check_range(t, Q, d_q, nullptr, false));
-    if (!(radius >= 0.f) || (Q > 0 && !d_counts))
-        return set_error(KDT_EINVAL, "bad radius or NULL counts");
-    if (Q == 0)
-        return KDT_OK;
-    return run_range(t, 0, false, d_q, nullptr, Q, radius * radius, d_counts, nullptr, nullptr, nullptr,
-                     (cudaStream_t)stream);
-}
-
-int kdt_radius_fill(const kdt_tree *t, const float *d_q, int64_t Q, float radius, const int64_t *d_offsets,
-                    int32_t *d_ids, float *d_d2, void *stream)
-{
-    KDT_TRY(check_range(t, Q, d_q, nullptr, false));
-    if (!(radius >= 0.f) || (Q > 0 && (!d_offsets || !d_ids)))
-        return set_error(KDT_EINVAL, "bad radius or NULL offsets / ids");
-    if (Q == 0)
-        return KDT_OK;
-    return run_range(t, 0, true, d_q, nullptr, Q, radius * radius, nullptr, d_offsets, d_ids, d_d2,
-                     (cudaStream_t)stream);
-}
-
-int kdt_box_count(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_t Q, int32_t *d_counts,
-                  void *stream)
-{
-    KDT_TRY(check_range(t, Q, d_lo, d_hi, true));
+    KDT_TRY(check_range(t, Q, d_q, nullptr, false, flags));
+    KDT_TRY(check_radius(radius));
     if (Q > 0 && !d_counts)
         return set_error(KDT_EINVAL, "NULL counts");
     if (Q == 0)
         return KDT_OK;
-    return run_range(t, 1, false, d_lo, d_hi, Q, 0.f, d_counts, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+    RangeArgs a = blank_args();
+    a.a = d_q;
+    a.Q = Q;
+    a.r2 = radius * radius;
+    a.counts = d_counts;
+    return run_range(t, 0, ACT_COUNT, flags, a, (cudaStream_t)stream);
 }
 
-int kdt_box_fill(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_t Q, const int64_t *d_offsets,
-                 int32_t *d_ids, void *stream)
+int kdt_radius_fill(const kdt_tree *t, const float *d_q, int64_t Q, float radius, int flags, const int64_t *d_offsets,
+                    int32_t *d_ids, float *d_d2, void *stream)
 {
-    KDT_TRY(check_range(t, Q, d_lo, d_hi, true));
+    KDT_TRY(check_range(t, Q, d_q, nullptr, false, flags));
+    KDT_TRY(check_radius(radius));
     if (Q > 0 && (!d_offsets || !d_ids))
         return set_error(KDT_EINVAL, "NULL offsets / ids");
     if (Q == 0)
         return KDT_OK;
-    return run_range(t, 1, true, d_lo, d_hi, Q, 0.f, nullptr, d_offsets, d_ids, nullptr, (cudaStream_t)stream);
+    RangeArgs a = blank_args();
+    a.a = d_q;
+    a.Q = Q;
+    a.r2 = radius * radius;
+    a.offsets = d_offsets;
+    a.out_ids = d_ids;
+    a.out_d2 = d_d2;
+    return run_range(t, 0, ACT_FILL, flags, a, (cudaStream_t)stream);
+}
+
+int kdt_box_count(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_t Q, int flags, int32_t *d_counts,
+                  void *stream)
+{
+    KDT_TRY(check_range(t, Q, d_lo, d_hi, true, flags));
+    if (Q > 0 && !d_counts)
+        return set_error(KDT_EINVAL, "NULL counts");
+    if (Q == 0)
+        return KDT_OK;
+    RangeArgs a = blank_args();
+    a.a = d_lo;
+    a.b = d_hi;
+    a.Q = Q;
+    a.counts = d_counts;
+    return run_range(t, 1, ACT_COUNT, flags, a, (cudaStream_t)stream);
+}
+
+int kdt_box_fill(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_t Q, int flags,
+                 const int64_t *d_offsets, int32_t *d_ids, void *stream)
+{
+    KDT_TRY(check_range(t, Q, d_lo, d_hi, true, flags));
+    if (Q > 0 && (!d_offsets || !d_ids))
+        return set_error(KDT_EINVAL, "NULL offsets / ids");
+    if (Q == 0)
+        return KDT_OK;
+    RangeArgs a = blank_args();
+    a.a = d_lo;
+    a.b = d_hi;
+    a.Q = Q;
+    a.offsets = d_offsets;
+    a.out_ids = d_ids;
+    return run_range(t, 1, ACT_FILL, flags, a, (cudaStream_t)stream);
 }
 
 int kdt_offsets(const int32_t *d_counts, int64_t Q, int64_t *d_offsets, int64_t *h_total, void *stream)
@@ -292,20 +442,105 @@ int kdt_offsets(const int32_t *d_counts, int64_t Q, int64_t *d_offsets, int64_t 
     if (Q < 0 || !d_offsets || (Q > 0 && !d_counts))
         return set_error(KDT_EINVAL, "bad offsets arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    pool_setup_once();
     unsigned long long *out = (unsigned long long *)d_offsets;
     const int64_t n = Q + 1;
-    unsigned long long *scratch = nullptr;
-    KDT_CUDA(cudaMallocAsync(&scratch, (scan_scratch_elems(n) + 1) * sizeof(unsigned long long), s));
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
-    KDT_LAUNCH counts_to_u64_kernel<<<g, 256, 0, s>>>(d_counts, Q, out);
-    int rc = exclusive_scan_u64(out, n, scratch, s);
-    cudaFreeAsync(scratch, s);
-    if (rc != KDT_OK)
-        return rc;
+    Scratch sc(s);
+    KDT_TRY(sc.alloc((scan_scratch_elems(n) + 1) * sizeof(unsigned long long)));
+    KDT_LAUNCH counts_to_u64_kernel<<<grid_for(n), 256, 0, s>>>(d_counts, Q, out);
+    KDT_TRY(exclusive_scan_u64(out, n, (unsigned long long *)sc.p, s));
     if (h_total) {
         KDT_CUDA(cudaMemcpyAsync(h_total, d_offsets + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         KDT_CUDA(cudaStreamSynchronize(s));
     }
+    return KDT_OK;
+}
+
+int kdt_tree_set_payload(kdt_tree *t, const float *d_payload, int C, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (C < 1 || C > KDT_PAYLOAD_MAX_C || (t->N > 0 && !d_payload))
+        return set_error(KDT_EINVAL, "payload: C must be in [1, %d] and the pointer non-NULL", KDT_PAYLOAD_MAX_C);
+    cudaStream_t s = (cudaStream_t)stream;
+    KDT_CUDA(cudaStreamSynchronize(s));
+    cudaFree(t->payload);
+    cudaFree(t->node_of);
+    t->payload = nullptr;
+    t->node_of = nullptr;
+    t->payload_c = 0;
+    const int64_t N = std::max<int64_t>(t->N, 1);
+    KDT_CUDA(cudaMalloc(&t->payload, (size_t)N * C * sizeof(float)));
+    KDT_CUDA(cudaMalloc(&t->node_of, (size_t)N * sizeof(int32_t)));
+    if (t->N > 0) {
+        const unsigned g = grid_for(t->N);
+        switch (t->layout) {
+        case 0: KDT_LAUNCH payload_permute_kernel<0><<<g, 256, 0, s>>>(t->nodes, t->ids, t->N, d_payload, C,
+                                                                     t->payload, t->node_of); break;
+        case 1: KDT_LAUNCH payload_permute_kernel<1><<<g, 256, 0, s>>>(t->nodes, t->ids, t->N, d_payload, C,
+                                                                     t->payload, t->node_of); break;
+        case 3: KDT_LAUNCH payload_permute_kernel<3><<<g, 256, 0, s>>>(t->nodes, t->ids, t->N, d_payload, C,
+                                                                     t->payload, t->node_of); break;
+        default: KDT_LAUNCH payload_permute_kernel<2><<<g, 256, 0, s>>>(t->nodes, t->ids, t->N, d_payload, C,
+                                                                      t->payload, t->node_of); break;
+        }
+        KDT_CUDA(cudaGetLastError());
+    }
+    t->payload_c = C;
+    return KDT_OK;
+}
+
+int kdt_radius_reduce(const kdt_tree *t, const float *d_q, int64_t Q, float radius, int flags, int mode, float *d_out,
+                      int32_t *d_counts, void *stream)
+{
+    KDT_TRY(check_range(t, Q, d_q, nullptr, false, flags));
+    KDT_TRY(check_radius(radius));
+    if (mode < KDT_REDUCE_SUM || mode > KDT_REDUCE_DENSITY)
+        return set_error(KDT_EINVAL, "unknown reduction mode %d", mode);
+    if (t->payload_c == 0)
+        return set_error(KDT_EINVAL, "the tree has no payload (kdt_tree_set_payload)");
+    if (Q > 0 && !d_out)
+        return set_error(KDT_EINVAL, "NULL output");
+    if (Q == 0)
+        return KDT_OK;
+    RangeArgs a = blank_args();
+    a.a = d_q;
+    a.Q = Q;
+    a.r2 = radius * radius;
+    a.counts = d_counts;
+    a.payload = t->payload;
+    a.C = t->payload_c;
+    a.mode = mode;
+    a.out = d_out;
+    return run_range(t, 0, ACT_REDUCE, flags, a, (cudaStream_t)stream);
+}
+
+int kdt_knn_reduce(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_radius, int flags, int mode,
+                   float *d_out, void *stream)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (mode < KDT_REDUCE_SUM || mode > KDT_REDUCE_DENSITY)
+        return set_error(KDT_EINVAL, "unknown reduction mode %d", mode);
+    if (t->payload_c == 0)
+        return set_error(KDT_EINVAL, "the tree has no payload (kdt_tree_set_payload)");
+    if (k < 1 || k > 64)
+        return set_error(KDT_EINVAL, "k must be in [1, 64] (got %d)", k);
+    if (Q < 0 || (Q > 0 && (!d_q || !d_out)))
+        return set_error(KDT_EINVAL, "bad query count or NULL pointer");
+    if (Q == 0)
+        return KDT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    pool_setup_once();
+    Scratch sc(s);
+    KDT_TRY(sc.alloc(carve_size({(size_t)Q * k * 4, (size_t)Q * k * 4})));
+    Carve c{(char *)sc.p};
+    int32_t *ids = c.take<int32_t>((size_t)Q * k);
+    float *d2 = c.take<float>((size_t)Q * k);
+    KDT_TRY(kdt_knn(t, d_q, Q, k, max_radius, flags, ids, d2, stream));
+    KDT_LAUNCH knn_reduce_kernel<<<grid_for(Q), 256, 0, s>>>(ids, d2, Q, k, t->node_of, t->payload, t->payload_c, mode,
+                                                             d_out);
+    KDT_CUDA(cudaGetLastError());
     return KDT_OK;
 }
 

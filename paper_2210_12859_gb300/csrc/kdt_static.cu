@@ -20,9 +20,6 @@
 
 namespace kdt {
 
-int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s);
-size_t morton_scratch_bytes(int64_t Q);
 
 namespace {
 

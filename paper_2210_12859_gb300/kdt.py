@@ -40,6 +40,8 @@ KDT_NO_STAGE = 0x8
 KDT_PER_TREE = 0x10
 KDT_COST_ORDER = 0x20
 KDT_BUILD_ASYNC = 0x1
+KDT_REDUCE_SUM, KDT_REDUCE_MEAN, KDT_REDUCE_DENSITY = 0, 1, 2
+KDT_PAYLOAD_MAX_C = 8
 KDT_BUILD_WIDEST = 0x2
 
 MLP_HIDDEN = 64
@@ -85,11 +87,14 @@ _sig("kdt_fcp", [_P, _P, _I64, _F, _I, _P, _P, _P])
 _sig("kdt_knn", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
 _sig("kdt_knn_visits", [_P, _P, _I64, _I, _F, _I, _P, _P])
 _sig("kdt_knn_static", [_P, _P, _I64, _I, _F, _I, _P, _P, _P])
-_sig("kdt_radius_count", [_P, _P, _I64, _F, _P, _P])
-_sig("kdt_radius_fill", [_P, _P, _I64, _F, _P, _P, _P, _P])
-_sig("kdt_box_count", [_P, _P, _P, _I64, _P, _P])
-_sig("kdt_box_fill", [_P, _P, _P, _I64, _P, _P, _P])
+_sig("kdt_radius_count", [_P, _P, _I64, _F, _I, _P, _P])
+_sig("kdt_radius_fill", [_P, _P, _I64, _F, _I, _P, _P, _P, _P])
+_sig("kdt_box_count", [_P, _P, _P, _I64, _I, _P, _P])
+_sig("kdt_box_fill", [_P, _P, _P, _I64, _I, _P, _P, _P])
 _sig("kdt_offsets", [_P, _I64, _P, ctypes.POINTER(_I64), _P])
+_sig("kdt_tree_set_payload", [_P, _P, _I, _P])
+_sig("kdt_radius_reduce", [_P, _P, _I64, _F, _I, _I, _P, _P, _P])
+_sig("kdt_knn_reduce", [_P, _P, _I64, _I, _F, _I, _I, _P, _P])
 _sig("kdt_status", [_P, _P])
 _sig("kdt_free", [_P], None)
 _sig("kdt_knn_host", [_P, _I64, _I, _P, _I64, _I, _F, _I, _P, _P])
@@ -241,6 +246,7 @@ def kdt_launch_count() -> int:
 def kdt_rebuild(tree: Tree, points: torch.Tensor, opts: int = 0, stream=None) -> None:
     _dev(points, torch.float32, "points", (tree.N, tree.D))
     _check(_lib.kdt_rebuild(tree.handle, ctypes.c_void_p(points.data_ptr()), opts, _stream(stream)))
+    tree.payload_c = 0  # the library drops a payload on rebuild
 
 
 def kdt_tree_export(tree: Tree, stream=None):
@@ -322,11 +328,12 @@ def kdt_knn_visits(tree: Tree, queries: torch.Tensor, k: int, max_radius: float 
     return v
 
 
-def kdt_radius_count(tree: Tree, queries: torch.Tensor, radius: float, stream=None) -> torch.Tensor:
+def kdt_radius_count(tree: Tree, queries: torch.Tensor, radius: float, flags: int = 0,
+                     stream=None) -> torch.Tensor:
     Q = queries.shape[0]
     counts = torch.empty(Q, dtype=torch.int32, device=queries.device)
     _check(_lib.kdt_radius_count(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, float(radius),
-                                 ctypes.c_void_p(counts.data_ptr()), _stream(stream)))
+                                 flags, ctypes.c_void_p(counts.data_ptr()), _stream(stream)))
     return counts
 
 
@@ -341,48 +348,84 @@ def kdt_offsets(counts: torch.Tensor, stream=None):
 
 
 def kdt_radius_fill(tree: Tree, queries: torch.Tensor, radius: float, offsets: torch.Tensor, total: int,
-                    with_d2: bool = True, stream=None):
+                    with_d2: bool = True, flags: int = 0, stream=None):
     Q = queries.shape[0]
     ids = torch.empty(max(total, 1), dtype=torch.int32, device=queries.device)
     d2 = torch.empty(max(total, 1), dtype=torch.float32, device=queries.device) if with_d2 else None
     _check(_lib.kdt_radius_fill(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, float(radius),
-                                _dev(offsets, torch.int64, "offsets", (Q + 1,)), ctypes.c_void_p(ids.data_ptr()),
+                                flags, _dev(offsets, torch.int64, "offsets", (Q + 1,)),
+                                ctypes.c_void_p(ids.data_ptr()),
                                 ctypes.c_void_p(d2.data_ptr()) if with_d2 else None, _stream(stream)))
     return ids[:total], (d2[:total] if with_d2 else None)
 
 
-def kdt_radius_search(tree: Tree, queries: torch.Tensor, radius: float, stream=None):
+def kdt_radius_search(tree: Tree, queries: torch.Tensor, radius: float, flags: int = 0, stream=None):
     """All points within `radius` of each query: (offsets [Q+1], ids, d2)."""
-    counts = kdt_radius_count(tree, queries, radius, stream)
+    counts = kdt_radius_count(tree, queries, radius, flags, stream)
     off, total = kdt_offsets(counts, stream)
-    ids, d2 = kdt_radius_fill(tree, queries, radius, off, total, True, stream)
+    ids, d2 = kdt_radius_fill(tree, queries, radius, off, total, True, flags, stream)
     return off, ids, d2
 
 
-def kdt_box_count(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, stream=None) -> torch.Tensor:
+def kdt_box_count(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, flags: int = 0, stream=None) -> torch.Tensor:
     Q = lo.shape[0]
     counts = torch.empty(Q, dtype=torch.int32, device=lo.device)
     _check(_lib.kdt_box_count(tree.handle, _dev(lo, torch.float32, "lo", (Q, tree.D)),
-                              _dev(hi, torch.float32, "hi", (Q, tree.D)), Q, ctypes.c_void_p(counts.data_ptr()),
-                              _stream(stream)))
+                              _dev(hi, torch.float32, "hi", (Q, tree.D)), Q, flags,
+                              ctypes.c_void_p(counts.data_ptr()), _stream(stream)))
     return counts
 
 
-def kdt_box_fill(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, offsets: torch.Tensor, total: int, stream=None):
+def kdt_box_fill(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, offsets: torch.Tensor, total: int, flags: int = 0,
+                 stream=None):
     Q = lo.shape[0]
     ids = torch.empty(max(total, 1), dtype=torch.int32, device=lo.device)
     _check(_lib.kdt_box_fill(tree.handle, _dev(lo, torch.float32, "lo", (Q, tree.D)),
-                             _dev(hi, torch.float32, "hi", (Q, tree.D)), Q,
+                             _dev(hi, torch.float32, "hi", (Q, tree.D)), Q, flags,
                              _dev(offsets, torch.int64, "offsets", (Q + 1,)), ctypes.c_void_p(ids.data_ptr()),
                              _stream(stream)))
     return ids[:total]
 
 
-def kdt_box_search(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, stream=None):
+def kdt_box_search(tree: Tree, lo: torch.Tensor, hi: torch.Tensor, flags: int = 0, stream=None):
     """All points inside each box [lo, hi]: (offsets [Q+1], ids)."""
-    counts = kdt_box_count(tree, lo, hi, stream)
+    counts = kdt_box_count(tree, lo, hi, flags, stream)
     off, total = kdt_offsets(counts, stream)
-    return off, kdt_box_fill(tree, lo, hi, off, total, stream)
+    return off, kdt_box_fill(tree, lo, hi, off, total, flags, stream)
+
+
+def kdt_tree_set_payload(tree: Tree, payload: torch.Tensor, stream=None) -> None:
+    """Attach a per-point payload float32 [N, C] (input order, 1 <= C <= 8)."""
+    if payload.dim() != 2:
+        raise ValueError("payload must be [N, C]")
+    C = payload.shape[1]
+    _check(_lib.kdt_tree_set_payload(tree.handle, _dev(payload, torch.float32, "payload", (tree.N, C)), C,
+                                     _stream(stream)))
+    tree.payload_c = C
+
+
+def kdt_radius_reduce(tree: Tree, queries: torch.Tensor, radius: float, mode: int = 0, flags: int = 0,
+                      with_counts: bool = False, stream=None):
+    """Payload reduction over each ball's hits: out [Q, C] (and counts [Q])."""
+    Q = queries.shape[0]
+    C = getattr(tree, "payload_c", 0) or 1
+    out = torch.empty((Q, C), dtype=torch.float32, device=queries.device)
+    counts = torch.empty(Q, dtype=torch.int32, device=queries.device) if with_counts else None
+    _check(_lib.kdt_radius_reduce(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q,
+                                  float(radius), flags, mode, ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(counts.data_ptr()) if with_counts else None, _stream(stream)))
+    return (out, counts) if with_counts else out
+
+
+def kdt_knn_reduce(tree: Tree, queries: torch.Tensor, k: int, max_radius: float = math.inf, mode: int = 0,
+                   flags: int = 0, stream=None) -> torch.Tensor:
+    """Payload reduction over each query's k nearest neighbours: out [Q, C]."""
+    Q = queries.shape[0]
+    C = getattr(tree, "payload_c", 0) or 1
+    out = torch.empty((Q, C), dtype=torch.float32, device=queries.device)
+    _check(_lib.kdt_knn_reduce(tree.handle, _dev(queries, torch.float32, "queries", (Q, tree.D)), Q, k,
+                               float(max_radius), flags, mode, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 def kdt_status(tree: Tree, stream=None) -> None:

@@ -1,7 +1,8 @@
 """GPU parity of the range queries (ball: every point within a radius; box:
-every point inside [lo, hi]) against the oracle's brute force: counts and
-offsets exact, each query's hits equal as a set, squared distances bit-exact,
-on every node layout (D = 1..8, stored split dimensions)."""
+every point inside [lo, hi]) against the oracle: counts and offsets exact,
+hits equal to the brute-force sets and, in order, to the oracle's stack-free
+range traversal; squared distances bit-exact; every node layout (D = 1..8,
+stored split dimensions), with and without Morton order."""
 import numpy as np
 import pytest
 
@@ -59,6 +60,12 @@ def build(kdt, pts, widest):
     return kdt.kdt_build(cu(pts), opts=kdt.KDT_BUILD_WIDEST if widest else 0)
 
 
+def oracle_tree(pts, widest):
+    if widest:
+        return oracle.build_widest(pts)
+    return oracle.build(pts), None
+
+
 @pytest.mark.parametrize("D,N,widest", CASES)
 def test_radius_equals_brute(kdt, D, N, widest):
     g = np.random.default_rng(10 * D + N + widest)
@@ -66,12 +73,18 @@ def test_radius_equals_brute(kdt, D, N, widest):
     qs = np.concatenate([pts[g.integers(0, N, 100)], g.random((157, D)).astype(np.float32)])
     r = radius_for(pts, 20)
     tree = build(kdt, pts, widest)
-    off, ids, d2 = kdt.kdt_radius_search(tree, cu(qs), r)
-    kdt.kdt_status(tree)
     counts, want_off, want_ids, want_d2 = oracle.radius_brute(pts, qs, r)
     assert want_off[-1] > 5 * len(qs)
-    same_sets(off.cpu().numpy(), ids.cpu().numpy(), want_off, want_ids, d2.cpu().numpy(), want_d2)
-    assert np.array_equal(kdt.kdt_radius_count(tree, cu(qs), r).cpu().numpy(), counts)
+    pid, dims = oracle_tree(pts, widest)
+    _, t_off, t_ids, t_d2 = oracle.range_tree(pts, pid, qs, radius=r, node_dim=dims)
+    for flags in (0, kdt.KDT_MORTON):
+        off, ids, d2 = kdt.kdt_radius_search(tree, cu(qs), r, flags=flags)
+        kdt.kdt_status(tree)
+        off, ids, d2 = off.cpu().numpy(), ids.cpu().numpy(), d2.cpu().numpy()
+        same_sets(off, ids, want_off, want_ids, d2, want_d2)
+        # the same hits in the same order as the oracle's stack-free range traversal
+        assert np.array_equal(ids, t_ids) and np.array_equal(bits(d2), bits(t_d2))
+        assert np.array_equal(kdt.kdt_radius_count(tree, cu(qs), r, flags).cpu().numpy(), counts)
 
 
 @pytest.mark.parametrize("D,N,widest", CASES)
@@ -86,11 +99,16 @@ def test_box_equals_brute(kdt, D, N, widest):
     hi[:5] = pts[:5]
     lo[5] = hi[5] + 0.1  # an empty box
     tree = build(kdt, pts, widest)
-    off, ids = kdt.kdt_box_search(tree, cu(lo), cu(hi))
-    kdt.kdt_status(tree)
     _, want_off, want_ids = oracle.box_brute(pts, lo, hi)
     assert want_off[-1] > 3 * Q
-    same_sets(off.cpu().numpy(), ids.cpu().numpy(), want_off, want_ids)
+    pid, dims = oracle_tree(pts, widest)
+    _, _, t_ids, _ = oracle.range_tree(pts, pid, lo, hi, node_dim=dims)
+    for flags in (0, kdt.KDT_MORTON):
+        off, ids = kdt.kdt_box_search(tree, cu(lo), cu(hi), flags=flags)
+        kdt.kdt_status(tree)
+        off, ids = off.cpu().numpy(), ids.cpu().numpy()
+        same_sets(off, ids, want_off, want_ids)
+        assert np.array_equal(ids, t_ids)
 
 
 def test_duplicates_and_zero_radius(kdt):
@@ -134,6 +152,8 @@ def test_empty_queries_and_bad_arguments(kdt):
         kdt.kdt_radius_count(tree, cu(pts[:4]), -1.0)
     with pytest.raises(kdt.KdtError):
         kdt.kdt_radius_count(tree, cu(pts[:4]), float("nan"))
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_radius_count(tree, cu(pts[:4]), 0.1, flags=kdt.KDT_UNORDERED)
 
 
 def test_fill_with_mismatched_offsets_is_reported(kdt):
@@ -181,7 +201,7 @@ def test_full_size_sampled(kdt):
     tree = kdt.kdt_build(cu(pts))
     r = 0.002
     dq = cu(qs)
-    off, ids, d2 = kdt.kdt_radius_search(tree, dq, r)
+    off, ids, d2 = kdt.kdt_radius_search(tree, dq, r, flags=kdt.KDT_MORTON)
     kdt.kdt_status(tree)
     off, ids, d2 = off.cpu().numpy(), ids.cpu().numpy(), d2.cpu().numpy()
     sample = np.random.default_rng(0).choice(len(qs), 96, replace=False)
