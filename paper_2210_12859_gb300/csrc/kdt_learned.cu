@@ -386,8 +386,8 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
         return set_error(KDT_ENOMODEL, "the tree has no trained radius model");
     KDT_TRY(ensure_stats(t));
     const bool morton = flags & KDT_MORTON;
-    size_t off_w = 0, off_r2 = 1 << 15, off_fb = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
-    size_t off_m = off_fb + (((size_t)Q * 4 + 255) & ~(size_t)255);
+    size_t off_w = 0, off_r2 = 1 << 15;
+    size_t off_m = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
     size_t bytes = off_m + (morton ? morton_scratch_bytes(Q) : 0);
     Dev sc(s);
     KDT_CUDA(cudaMallocAsync(&sc.p, bytes, s));
@@ -395,7 +395,6 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     float *wts = (float *)(B + off_w);                                  // P floats
     unsigned long long *counter = (unsigned long long *)(B + 20480);    // 3 x u64 after the weights
     float *r2q = (float *)(B + off_r2);
-    uint32_t *fb_list = (uint32_t *)(B + off_fb);
     uint32_t *perm = nullptr;
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
@@ -422,12 +421,10 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.counter = counter;
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.r2q = r2q;
-    a.fb_list = fb_list;
     a.fb_count = (unsigned long long *)t->stats;
     a.ratio_sum = (double *)(t->stats + 1);
     const bool ordered = !(flags & KDT_UNORDERED);
     KDT_TRY(launch_query(t->layout, a, ordered, MODE_BOUNDED, false, s));
-    KDT_TRY(launch_query(t->layout, a, ordered, MODE_FALLBACK, false, s));
     t->last_learned_q = Q;
     return KDT_OK;
 }

@@ -33,13 +33,14 @@ struct QueryArgs {
     const int64_t *q_off = nullptr;    // [T+1]
     // learned radius proposal
     const float *r2q = nullptr;        // per-query cull radius of the bounded pass (mode 2)
-    uint32_t *fb_list = nullptr;       // queries to re-run (appended by mode 2, read by mode 3)
     unsigned long long *fb_count = nullptr;
     double *ratio_sum = nullptr;       // sum of proposed / true k-th radius (mode 2, exact queries)
 };
 
 // kernel modes: results, visit counts, learned bounded pass, fallback pass
-enum : int { MODE_RESULTS = 0, MODE_VISITS = 1, MODE_BOUNDED = 2, MODE_FALLBACK = 3 };
+// (MODE_BOUNDED: per-query cull radius r2q; a query whose list is not full
+// restarts in the same lane with the caller's radius)
+enum : int { MODE_RESULTS = 0, MODE_VISITS = 1, MODE_BOUNDED = 2 };
 
 // Launch a traversal for one layout (mode: MODE_*).
 int launch_query_layout0(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);

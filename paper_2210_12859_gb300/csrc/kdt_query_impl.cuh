@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         stage_nodes<LAYOUT>(a.nodes, s_nodes, a.staged);
         __syncthreads();
     }
-    const int64_t Qn = MODE == MODE_FALLBACK ? (int64_t)*a.fb_count : a.Q;
+    const int64_t Qn = a.Q;
     double ratio = 0.0;
     int64_t qi = -1;
     bool exhausted = false;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         const int64_t slot = claim_slot(need, a.counter);
         if (need) {
             if (slot < Qn) {
-                qi = MODE == MODE_FALLBACK ? (int64_t)a.fb_list[slot] : (a.perm ? (int64_t)a.perm[slot] : slot);
+                qi = a.perm ? (int64_t)a.perm[slot] : slot;
                 r2 = MODE == MODE_BOUNDED ? a.r2q[qi] : a.r2;
                 load_query<LAYOUT>(a.queries, qi, a.D, q);
                 list.init(a.k, r2);
@@ -89,22 +89,23 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         const bool full = list.full(a.k);
         // a bounded query is exact when its list is full (every point outside
         // the proposed radius is farther than all k held) or when the proposal
-        // did not shrink the caller's radius; the others are re-run
+        // did not shrink the caller's radius; the others restart at once in the
+        // same lane with the caller's radius (the plain traversal): no second
+        // launch, and the re-run stays next to its Morton neighbours
         const bool fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
-        if (MODE != MODE_VISITS && !fallback && a.out_ids)
+        if (fallback) {
+            atomicAdd(a.fb_count, 1ull);
+            r2 = a.r2;
+            list.init(a.k, r2);
+            w.start();
+            continue;
+        }
+        if (MODE != MODE_VISITS && a.out_ids)
             list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
         if (MODE == MODE_VISITS || (MODE == MODE_BOUNDED && a.visits))
             a.visits[qi] = overflow ? -1 : visits;
-        if (MODE == MODE_FALLBACK && a.visits)
-            a.visits[qi] += visits;
-        if (MODE == MODE_BOUNDED) {
-            if (fallback) {
-                const unsigned long long at = atomicAdd(a.fb_count, 1ull);
-                a.fb_list[at] = (uint32_t)qi;
-            } else if (full && list.cull() > 0.f && r2 < __int_as_float(0x7f800000)) {
-                ratio += sqrt((double)r2 / (double)list.cull());
-            }
-        }
+        if (MODE == MODE_BOUNDED && full && list.cull() > 0.f && r2 < __int_as_float(0x7f800000))
+            ratio += sqrt((double)r2 / (double)list.cull());
         qi = -1;
     }
     if (MODE == MODE_BOUNDED) {
@@ -207,16 +208,10 @@ inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, 
             return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS, STAGE>, threads, smem, a, s);
         return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE>, threads, smem, a, s);
     case MODE_BOUNDED:
-    case MODE_FALLBACK:
         if constexpr (LAYOUT == 0 || LAYOUT == 3) {
-            if (mode == MODE_BOUNDED) {
-                if (ordered)
-                    return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE>, threads, smem, a, s);
-                return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE>, threads, smem, a, s);
-            }
             if (ordered)
-                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_FALLBACK, STAGE>, threads, smem, a, s);
-            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_FALLBACK, STAGE>, threads, smem, a, s);
+                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE>, threads, smem, a, s);
         } else {
             return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
         }
