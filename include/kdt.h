@@ -242,6 +242,11 @@ typedef struct kdt_train_opts {
                              calibrated after training so that a fraction fallback_target of
                              the training queries would fall back */
     float fallback_target;/* see margin (default 0.02 if <= 0) */
+    int uniform_weights;  /* 0 (default): weight each training query by the work the plain
+                             traversal spends on it (processed nodes plus a floor of a tenth of
+                             the mean), by resampling the training set with those
+                             probabilities; the margin's fallback target is then a share of
+                             that work.  1: every query weighs the same */
 } kdt_train_opts;
 
 /* Width of the two hidden layers of the radius model. */
@@ -255,7 +260,9 @@ typedef struct kdt_train_opts {
  * (the leaf is where repeated close-child steps from the root end), normalised
  * by their training mean and standard deviation; the MLP 4 -> 64 -> 64 -> 1
  * (ReLU) runs with BF16-rounded weights and FP32 accumulation and is fitted by
- * Adam on the mean squared error, entirely by the library's kernels.
+ * Adam (step size decaying along a half cosine) on the mean squared error over
+ * the (by default cost-weighted) training sample, entirely by the library's
+ * kernels.
  * Synchronous.  *final_loss (may be NULL) receives the last epoch's mean loss. */
 int kdt_radius_model_train(kdt_tree *tree, const float *d_train_queries, int64_t Qt, int k,
                            const kdt_train_opts *opts, float *final_loss, void *stream);

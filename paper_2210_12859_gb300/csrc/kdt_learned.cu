@@ -299,6 +299,62 @@ __global__ void normalize_kernel(float *__restrict__ feat, int64_t n, Norm nm)
             feat[i * 4 + j] = __fdiv_rn(__fsub_rn(feat[i * 4 + j], nm.mu[j]), nm.sd[j]);
 }
 
+// ---- cost-weighted resampling of the training set
+// The proposal exists to save traversal work, so each training query is
+// weighted by the work the plain method spends on it: its processed nodes
+// plus a floor (a tenth of the mean), which keeps cheap queries represented.
+// Systematic resampling draws Qt samples with those probabilities (sample j
+// takes the query whose cumulative-weight interval holds (j + u) / Qt of the
+// total); a sort by hashed keys then shuffles them so that minibatches mix.
+
+__global__ void visits_to_u64_kernel(const int32_t *__restrict__ v, int64_t n, unsigned long long *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = i < n ? (unsigned long long)(v[i] > 0 ? v[i] : 0) : 0ull;
+}
+
+__device__ __forceinline__ uint32_t hash32(uint64_t x)
+{
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return (uint32_t)x;
+}
+
+// cdf: exclusive prefix sums of the visits [n+1]; weight of query i =
+// visits_i + floor, so its interval is [cdf[i] + floor*i, cdf[i+1] + floor*(i+1))
+__global__ void resample_kernel(const unsigned long long *__restrict__ cdf, int64_t n, double floor_w, double u,
+                                uint64_t seed, uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    const double total = (double)cdf[n] + floor_w * (double)n;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double target = ((double)j + u) * total / (double)n;
+        int64_t lo = 0, hi = n - 1;  // largest i with start(i) <= target
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if ((double)cdf[mid] + floor_w * (double)mid <= target)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        idx[j] = (uint32_t)lo;
+        keys[j] = hash32(seed * 0x9e3779b97f4a7c15ull + (uint64_t)j);
+    }
+}
+
+__global__ void gather_samples_kernel(const uint32_t *__restrict__ idx, int64_t n, const float4 *__restrict__ feat,
+                                      const float *__restrict__ lab, float4 *__restrict__ feat_out,
+                                      float *__restrict__ lab_out)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = idx[j];
+        feat_out[j] = feat[i];
+        lab_out[j] = lab[i];
+    }
+}
+
 __global__ void fill_inf_kernel(float *p, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -519,7 +575,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     if (Qt > ((int64_t)1 << 26))
         return set_error(KDT_EINVAL, "at most 2^26 training queries");
     cudaStream_t s = (cudaStream_t)stream;
-    kdt_train_opts o{6, 1024, 2e-3f, 1, 0.f, 0.02f};
+    kdt_train_opts o{6, 1024, 2e-3f, 1, 0.f, 0.02f, 0};
     if (opts) {
         if (opts->epochs > 0)
             o.epochs = opts->epochs;
@@ -532,6 +588,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
             o.margin = opts->margin;
         if (opts->fallback_target > 0)
             o.fallback_target = std::min(opts->fallback_target, 0.5f);
+        o.uniform_weights = opts->uniform_weights;
     }
     o.batch = std::max(TS, (o.batch / TS) * TS);
     KDT_TRY(ensure_params(t));
@@ -543,7 +600,14 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     size_t o_lab = o_feat + al((size_t)Qt * 16), o_w = o_lab + al((size_t)Qt * 4), o_m = o_w + al(P * 4);
     size_t o_v = o_m + al(P * 4), o_g = o_v + al(P * 4), o_part = o_g + al((P + 1) * 4);
     size_t o_stat = o_part + al((size_t)nbmax * (P + 1) * 4), o_loss = o_stat + al(STAT_BLOCKS * 10 * 8);
-    size_t bytes = o_loss + 256;
+    // resampling: visits, cdf + scan scratch, keys / idx / sort temporaries, resampled features and labels
+    const bool weighted = !o.uniform_weights;
+    size_t o_vis = o_loss + 256, o_cdf = o_vis + al((size_t)Qt * 4);
+    size_t o_scan = o_cdf + al(((size_t)Qt + 1) * 8), o_keys = o_scan + al((scan_scratch_elems(Qt + 1) + 1) * 8);
+    size_t o_idx = o_keys + al((size_t)Qt * 4), o_tk = o_idx + al((size_t)Qt * 4), o_tv = o_tk + al((size_t)Qt * 4);
+    size_t o_rs = o_tv + al((size_t)Qt * 4), o_f2 = o_rs + al((radix_scratch_elems(Qt) + 1) * 4);
+    size_t o_l2 = o_f2 + al((size_t)Qt * 16);
+    size_t bytes = weighted ? o_l2 + al((size_t)Qt * 4) : o_loss + 256;
     Dev buf(s);
     KDT_CUDA(cudaMallocAsync(&buf.p, bytes, s));
     char *B = (char *)buf.p;
@@ -563,6 +627,28 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     KDT_TRY(run_query(t, d_q, Qt, k, INFINITY, KDT_MORTON, MODE_RESULTS, ids, d2, nullptr, s));
     KDT_LAUNCH label_kernel<<<grid_of(Qt), 256, 0, s>>>(d2, Qt, k, lab);
     KDT_TRY(kdt_descent_features(t, d_q, Qt, feat, s));
+    if (weighted) {
+        int32_t *vis = (int32_t *)(B + o_vis);
+        unsigned long long *cdf = (unsigned long long *)(B + o_cdf);
+        uint32_t *keys = (uint32_t *)(B + o_keys), *idx = (uint32_t *)(B + o_idx);
+        KDT_TRY(run_query(t, d_q, Qt, k, INFINITY, KDT_MORTON, MODE_VISITS, nullptr, nullptr, vis, s));
+        KDT_LAUNCH visits_to_u64_kernel<<<grid_of(Qt + 1), 256, 0, s>>>(vis, Qt, cdf);
+        KDT_TRY(exclusive_scan_u64(cdf, Qt + 1, (unsigned long long *)(B + o_scan), s));
+        unsigned long long total = 0;
+        KDT_CUDA(cudaMemcpyAsync(&total, cdf + Qt, 8, cudaMemcpyDeviceToHost, s));
+        KDT_CUDA(cudaStreamSynchronize(s));
+        const double floor_w = std::max(1.0, 0.1 * (double)total / (double)Qt);
+        uint64_t su = o.seed * 0xD1B54A32D192ED03ull + 99;
+        const double u = (double)(splitmix(su) >> 11) * (1.0 / 9007199254740992.0);
+        KDT_LAUNCH resample_kernel<<<grid_of(Qt), 256, 0, s>>>(cdf, Qt, floor_w, u, o.seed, keys, idx);
+        KDT_TRY(radix_sort_pairs(keys, idx, (uint32_t *)(B + o_tk), (uint32_t *)(B + o_tv), Qt, 32,
+                                 (uint32_t *)(B + o_rs), s));
+        float *feat2 = (float *)(B + o_f2), *lab2 = (float *)(B + o_l2);
+        KDT_LAUNCH gather_samples_kernel<<<grid_of(Qt), 256, 0, s>>>(idx, Qt, (const float4 *)feat, lab,
+                                                                     (float4 *)feat2, lab2);
+        feat = feat2;
+        lab = lab2;
+    }
     KDT_LAUNCH stats_kernel<<<STAT_BLOCKS, 256, 0, s>>>(feat, lab, Qt, stat);
     std::vector<double> hs(STAT_BLOCKS * 10);
     KDT_CUDA(cudaMemcpyAsync(hs.data(), stat, hs.size() * 8, cudaMemcpyDeviceToHost, s));
@@ -599,6 +685,9 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
 
     double b1t = 1.0, b2t = 1.0;
     float last = 0.f;
+    // step size decays along a half cosine from lr to 0 over the run
+    const int64_t steps_total = (int64_t)o.epochs * ((Qt + o.batch - 1) / o.batch);
+    int64_t step = 0;
     for (int ep = 0; ep < o.epochs; ++ep) {
         KDT_CUDA(cudaMemsetAsync(loss_acc, 0, 8, s));
         for (int64_t b0 = 0; b0 < Qt; b0 += o.batch) {
@@ -606,7 +695,9 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
             KDT_TRY(loss_grad_dev(w, feat, lab, b0, cnt, part, grad, s));
             b1t *= 0.9;
             b2t *= 0.999;
-            KDT_LAUNCH adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, m, v, grad, o.lr, (float)(1.0 - b1t),
+            const float lr = (float)(0.5 * o.lr * (1.0 + cos(M_PI * (double)step / (double)steps_total)));
+            ++step;
+            KDT_LAUNCH adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, m, v, grad, lr, (float)(1.0 - b1t),
                                                        (float)(1.0 - b2t), w, loss_acc);
         }
         KDT_CUDA(cudaGetLastError());
@@ -619,7 +710,8 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     if (!(margin > 0.f)) {
         // calibrate: the proposal falls short for a query iff its residual
         // label - prediction exceeds log(margin); take the (1 - target)
-        // quantile of the training residuals
+        // quantile of the training residuals (of the cost-weighted sample:
+        // re-runs then cost about a fraction `target` of the plain work)
         float *pred = d2;  // reuse: Qt floats
         KDT_TRY(tc_forward(w, feat, Qt, pred, t->err, s));
         std::vector<float> hp(Qt), hl(Qt);

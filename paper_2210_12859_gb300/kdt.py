@@ -63,7 +63,8 @@ _D = ctypes.c_double
 
 class TrainOpts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("margin", ctypes.c_float), ("fallback_target", ctypes.c_float)]
+                ("seed", ctypes.c_uint64), ("margin", ctypes.c_float), ("fallback_target", ctypes.c_float),
+                ("uniform_weights", ctypes.c_int)]
 
 
 def _sig(name, args, res=_I):
@@ -532,8 +533,8 @@ def _need(name):
 
 def kdt_radius_model_train(tree: Tree, train_queries: torch.Tensor, k: int, epochs: int = 0, batch: int = 0,
                            lr: float = 0.0, seed: int = 0, margin: float = 0.0, fallback_target: float = 0.0,
-                           stream=None) -> float:
-    opts = TrainOpts(epochs, batch, lr, seed, margin, fallback_target)
+                           uniform_weights: bool = False, stream=None) -> float:
+    opts = TrainOpts(epochs, batch, lr, seed, margin, fallback_target, int(uniform_weights))
     loss = _F()
     Qt = train_queries.shape[0]
     _check(_need("kdt_radius_model_train")(tree.handle, _dev(train_queries, torch.float32, "train_queries",
