@@ -345,7 +345,7 @@ def main():
         mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
         train_q = torch.from_numpy(synth.gmm_queries(mix, 1 << 20, 0.1, synth.BASE_SEED + 77)).to(dev)
         t0 = time.perf_counter()
-        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=6, seed=1)
+        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=20, seed=1)
         train_s = time.perf_counter() - t0
         li = torch.empty_like(out_i)
         ld = torch.empty_like(out_d)
@@ -358,7 +358,8 @@ def main():
                    "plain_query_qps": n / (query_ms / 1000.0), "speedup_vs_plain": query_ms / learned_ms,
                    "fallback_rate": fb / n, "radius_ratio": ratio, "identical_to_plain": same,
                    "visits_per_query": float(lv.double().mean().item()), "train_s": train_s,
-                   "train_loss": loss, "train_queries": 1 << 20}
+                   "train_loss": loss, "train_queries": 1 << 20, "train_epochs": 20,
+                   "train_weighting": "plain-traversal work (resampled)"}
 
     # ---- the same queries on a tree with a stored per-node split dimension
     # (widest extent; the paper's other splitDimOf variant), same results

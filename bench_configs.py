@@ -96,7 +96,7 @@ def run_config(args):
         tree = kdt.kdt_build(dp)
         for k in (8, 32):
             t0 = time.perf_counter()
-            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=6, seed=1)
+            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1)
             train_s = time.perf_counter() - t0
             out_i = torch.empty((n, k), dtype=torch.int32, device="cuda")
             out_d = torch.empty((n, k), dtype=torch.float32, device="cuda")
