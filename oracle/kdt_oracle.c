@@ -327,7 +327,8 @@ typedef struct {
     int64_t N;
     int D;
     const float *q;
-    int ordered;
+    int ordered;       /* 0 unordered, 1 ordered (node before its close child),
+                          2 ordered with the node after its close subtree */
     orc_list *L;
     int32_t *visits;   /* first visits (processNode calls), may be NULL */
     int64_t nvisits;
@@ -361,13 +362,17 @@ static void orc_process(orc_trav *T, int64_t node)
 /* Sec. 3.1, second formulation: empty subtree -> return; process; close child;
  * far child if it still overlaps the (possibly shrunk) query range.  The
  * unordered variant always takes the left child first and enters a child iff
- * the query lies on its side or the plane is within the cull radius. */
+ * the query lies on its side or the plane is within the cull radius.  With
+ * ordered == 2 the node is processed after its close subtree instead of
+ * before it (the swap of root and close subtree that the footnote of Sec. 3.1
+ * allows). */
 static void orc_rec(orc_trav *T, int64_t node)
 {
     orc_log(T->steps, &T->nsteps, T->scap, node);
     if (node >= T->N)
         return;
-    orc_process(T, node);
+    if (T->ordered != 2)
+        orc_process(T, node);
     int dim = orc_split_dim(T, node);
     float split = T->pts[(int64_t)T->node_pid[node] * T->D + dim];
     float sd = T->q[dim] - split;
@@ -377,6 +382,8 @@ static void orc_rec(orc_trav *T, int64_t node)
         int64_t far_child = 2 * node + 2 - close_side;
         orc_rec(T, close_child);
         orc_log(T->steps, &T->nsteps, T->scap, node);
+        if (T->ordered == 2)
+            orc_process(T, node);
         if (sd * sd <= orc_list_cull(T->L)) {
             orc_rec(T, far_child);
             orc_log(T->steps, &T->nsteps, T->scap, node);
@@ -395,7 +402,9 @@ static void orc_rec(orc_trav *T, int64_t node)
 
 /* Sec. 3.2: only the current and the previous node are kept.  The ordered
  * branch follows the published step logic; the unordered branch is the same
- * machine with the child order fixed to (left, right). */
+ * machine with the child order fixed to (left, right).  With ordered == 2 a
+ * node is processed when the machine comes back from its close child, and
+ * the far child is then judged against the radius that processing left. */
 static int orc_stackfree(orc_trav *T)
 {
     int64_t curr = 0;
@@ -410,7 +419,7 @@ static int orc_stackfree(orc_trav *T)
             continue;
         }
         int from_parent = prev < curr;
-        if (from_parent)
+        if (from_parent && T->ordered != 2)
             orc_process(T, curr);
         float cull = orc_list_cull(T->L);
         int dim = orc_split_dim(T, curr);
@@ -421,13 +430,17 @@ static int orc_stackfree(orc_trav *T)
             int close_side = sd > 0.0f;
             int64_t close_child = 2 * curr + 1 + close_side;
             int64_t far_child = 2 * curr + 2 - close_side;
-            int far_in_range = sd * sd <= cull;
-            if (from_parent)
+            if (from_parent) {
                 next = close_child;
-            else if (prev == close_child)
-                next = far_in_range ? far_child : parent;
-            else
+            } else if (prev == close_child) {
+                if (T->ordered == 2) {
+                    orc_process(T, curr);
+                    cull = orc_list_cull(T->L);
+                }
+                next = sd * sd <= cull ? far_child : parent;
+            } else {
                 next = parent;
+            }
         } else {
             int64_t lc = 2 * curr + 1;
             int64_t rc = 2 * curr + 2;

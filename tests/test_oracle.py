@@ -629,3 +629,76 @@ def test_payload_sum_float_within_rounding_bound():
         x = pay[wids[woff[q]:woff[q + 1]]].astype(np.float64)
         bound = len(x) * eps * np.abs(x).sum(0) + 1e-30
         assert np.all(np.abs(s[q] - x.sum(0)) <= bound)
+
+
+# ------------------------------------- swapped order (node after close subtree)
+
+CLOSE_FIRST = 2
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_close_first_equals_brute_and_recursion(seed):
+    """The footnote of Sec. 3.1 allows processing a node after its close
+    subtree: the same exact results, and the stack-free machine walks the
+    same steps as the recursion in that order."""
+    g = np.random.default_rng(700 + seed)
+    N, D = int(g.integers(1, 260)), int(g.integers(1, 5))
+    pts = g.random((N, D)).astype(np.float32)
+    if seed % 2:
+        pts = g.integers(0, 4, size=(N, D)).astype(np.float32)
+    pid = oracle.build(pts)
+    qs = (g.random((12, D)) * 1.2 - 0.1).astype(np.float32)
+    for k, r in ((1, math.inf), (4, math.inf), (8, 0.3), (N + 2, math.inf)):
+        want_i, want_d = oracle.knn_brute(pts, qs, k, r)
+        for i in range(len(qs)):
+            a = oracle.knn_recursive(pts, pid, qs[i], k, r, ordered=CLOSE_FIRST)
+            b = oracle.knn_stackfree(pts, pid, qs[i], k, r, ordered=CLOSE_FIRST)
+            assert np.array_equal(a[0], want_i[i]) and np.array_equal(a[1].view(np.uint32), want_d[i].view(np.uint32))
+            assert np.array_equal(b[0], a[0]) and np.array_equal(b[1], a[1])
+            assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+        got = oracle.knn_tree(pts, pid, qs, k, r, ordered=CLOSE_FIRST)
+        assert np.array_equal(got[0], want_i) and np.array_equal(got[1], want_d)
+
+
+def test_close_first_unbounded_is_inorder_by_close_side():
+    """With k >= N and r = inf nothing is culled: every node is processed once,
+    after all nodes of its close subtree and before all nodes of its far one."""
+    g = np.random.default_rng(5)
+    N, D = 200, 3
+    pts = g.random((N, D)).astype(np.float32)
+    pid = oracle.build(pts)
+    q = g.random(D).astype(np.float32)
+
+    def subtree(n):
+        out, stack = [], [n]
+        while stack:
+            m = stack.pop()
+            if m < N:
+                out.append(m)
+                stack += [2 * m + 1, 2 * m + 2]
+        return out
+
+    _, _, visits, _ = oracle.knn_stackfree(pts, pid, q, N, math.inf, ordered=CLOSE_FIRST)
+    assert sorted(visits.tolist()) == list(range(N))
+    pos = np.empty(N, dtype=np.int64)
+    pos[visits] = np.arange(N)
+    for n in range(N):
+        d = int(np.floor(np.log2(n + 1))) % D
+        sd = np.float32(q[d]) - pts[pid[n], d]
+        close, far = (2 * n + 2, 2 * n + 1) if sd > 0 else (2 * n + 1, 2 * n + 2)
+        assert all(pos[m] < pos[n] for m in subtree(close))
+        assert all(pos[m] > pos[n] for m in subtree(far))
+
+
+def test_close_first_six_point_trace():
+    """Figure 1's points, query (8,1.5), k = 1: the root-first order processes
+    (7,2) first; close-first descends to (8,1) before processing anything."""
+    gd = json.load(open(GOLDEN))
+    pts = np.array(gd["points"], dtype=np.float32)
+    pid = oracle.build(pts)
+    q = np.array([8.0, 1.5], dtype=np.float32)
+    _, _, v_root, _ = oracle.knn_stackfree(pts, pid, q, 1)
+    ids, _, v_close, _ = oracle.knn_stackfree(pts, pid, q, 1, ordered=CLOSE_FIRST)
+    assert tuple(pts[pid[v_root[0]]].tolist()) == (7.0, 2.0)
+    assert tuple(pts[pid[v_close[0]]].tolist()) == (8.0, 1.0)
+    assert tuple(pts[ids[0]].tolist()) == (8.0, 1.0)
