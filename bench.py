@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--config", default="gmm_large",
-                    choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched"],
+                    choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched", "ablation"],
                     help="gmm_large: the contract line; the others print one JSON line per measured form")
     return ap.parse_args()
 

@@ -115,6 +115,37 @@ def run_config(args):
                   bit_exact_sample=_exact(oracle, pts, qs, out_i.cpu().numpy(), out_d.cpu().numpy(), k))
         return
 
+    if args.config == "ablation":
+        # the traversal choices around the stack-free machine, same results:
+        # production kernel (inlined bottom subtrees, lane refill), the machine
+        # as stated (one node per step), node after close subtree, stack-based
+        forms = (("production", 0), ("stack-free, one node per step", kdt.KDT_PLAIN_STEP),
+                 ("stack-free, node after close subtree", kdt.KDT_CLOSE_FIRST),
+                 ("stack-based (explicit per-thread stack)", kdt.KDT_STACK))
+        n = 1 << 24
+        mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
+        pts = synth.gmm_sample(mix, n, synth.BASE_SEED + 2)
+        qs = synth.gmm_queries(mix, n, 0.1, synth.BASE_SEED + 3)
+        rig_q = 10_000_000
+        rig_pts = synth.uniform(1 << 22, 4, seed=synth.BASE_SEED + 6)
+        rig_qs = synth.uniform(rig_q, 4, seed=synth.BASE_SEED + 7)
+        cases = (("gmm_large N=Q=2^24 kNN k=8", pts, qs, 8, kdt.KDT_MORTON | kdt.KDT_COST_ORDER),
+                 ("paper rig: uniform float4, N=2^22, Q=10^7, fcp", rig_pts, rig_qs, 1, kdt.KDT_MORTON),
+                 ("paper rig: uniform float4, N=2^22, Q=10^7, kNN k=8", rig_pts, rig_qs, 8, kdt.KDT_MORTON))
+        for cname, p_, q_, k, base in cases:
+            dp, dq = cu(p_), cu(q_)
+            tree = kdt.kdt_build(dp)
+            ref_i, ref_d = kdt.kdt_knn(tree, dq, k, math.inf, base)
+            out_i, out_d = torch.empty_like(ref_i), torch.empty_like(ref_d)
+            for name, fl in forms:
+                ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, base | fl, out_i, out_d), 2)
+                same = bool(torch.equal(out_i, ref_i) and torch.equal(out_d.view(torch.int32), ref_d.view(torch.int32)))
+                v = kdt.kdt_knn_visits(tree, dq, k, math.inf, base | fl).double().mean().item()
+                _emit(config=cname, form=name, query_qps=len(q_) / (ms / 1e3), query_ms=ms, visits_per_query=v,
+                      identical_to_production=same)
+            del tree, dp, dq, ref_i, ref_d, out_i, out_d
+        return
+
     if args.config == "batched":
         c = synth.clouds(4096, seed=synth.BASE_SEED + 5)
         dp, dq = cu(c.points), cu(c.queries)

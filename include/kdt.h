@@ -64,6 +64,17 @@ extern "C" {
                               spacing), Morton order within a class.  Pays when a few queries
                               cost far more than the rest (queries outside the data); costs one
                               descent per query */
+/* Traversal ablations (ordered kNN / fcp, k <= 16, D <= 4; at most one; not
+ * with KDT_UNORDERED or KDT_LEARNED).  Same results as without them; they
+ * measure the choices around Sec. 3's stack-free traversal, for which the
+ * paper makes no speed claim against a stack-based one: */
+#define KDT_PLAIN_STEP  0x40  /* the stack-free machine as stated: one node per step, no
+                                 inlined bottom subtrees */
+#define KDT_CLOSE_FIRST 0x80  /* process a node after its close subtree instead of before
+                                 it (the order swap the footnote of Sec. 3.1 allows) */
+#define KDT_STACK       0x100 /* a stack-based traversal (far child pushed with its plane
+                                 distance, culled when popped): the recursion of Sec. 3.1
+                                 with an explicit per-thread stack */
 
 /* ---- build options ----------------------------------------------------- */
 #define KDT_BUILD_ASYNC 0x1 /* kdt_build_ex: do not synchronise to check the points for

@@ -234,9 +234,25 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     cudaEvent_t stop;
     KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
-    KDT_TRY(launch_query(t->layout, a, !(flags & KDT_UNORDERED), mode, false, s));
+    if (flags & (KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
+        KDT_TRY(launch_ablation(t->layout, a, flags, mode, s));
+    else
+        KDT_TRY(launch_query(t->layout, a, !(flags & KDT_UNORDERED), mode, false, s));
     if (stop)
         KDT_CUDA(cudaEventRecord(stop, s));
+    return KDT_OK;
+}
+
+// the traversal ablations are ordered plain-radius variants of kdt_knn
+static int check_ablation_flags(int flags)
+{
+    const int abl = flags & (KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK);
+    if (!abl)
+        return KDT_OK;
+    if (abl & (abl - 1))
+        return set_error(KDT_EINVAL, "at most one of KDT_PLAIN_STEP, KDT_CLOSE_FIRST, KDT_STACK");
+    if (flags & (KDT_UNORDERED | KDT_LEARNED))
+        return set_error(KDT_EINVAL, "the traversal ablations are ordered and take no learned radius");
     return KDT_OK;
 }
 
@@ -443,6 +459,7 @@ int kdt_knn(const kdt_tree *t, const float *d_q, int64_t Q, int k, float max_rad
     if (Q == 0)
         return KDT_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    KDT_TRY(check_ablation_flags(flags));
     float r2 = max_radius * max_radius;
     if (flags & KDT_LEARNED)
         return run_learned_query(const_cast<kdt_tree *>(t), d_q, Q, k, r2, flags, d_ids, d_d2, nullptr, s);
@@ -459,6 +476,7 @@ int kdt_knn_visits(const kdt_tree *t, const float *d_q, int64_t Q, int k, float 
                    int32_t *d_visits, void *stream)
 {
     KDT_TRY(check_query_args(t, d_q, Q, k, max_radius, d_visits, nullptr, true));
+    KDT_TRY(check_ablation_flags(flags));
     if (Q == 0)
         return KDT_OK;
     if (flags & KDT_LEARNED)
@@ -704,6 +722,8 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
         return set_error(KDT_EINVAL, "bad k or max_radius");
     if (flags & KDT_LEARNED)
         return set_error(KDT_EINVAL, "KDT_LEARNED is not supported for forests");
+    if (flags & (KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
+        return set_error(KDT_EINVAL, "the traversal ablations are single-tree only");
     if (h_qoff[0] != 0)
         return set_error(KDT_EINVAL, "query offsets must start at 0");
     for (int i = 0; i < T; ++i)

@@ -37,10 +37,33 @@ struct QueryArgs {
     double *ratio_sum = nullptr;       // sum of proposed / true k-th radius (mode 2, exact queries)
 };
 
+// Claim the next queries for the lanes of the warp that need one: one atomic
+// per warp, consecutive slots in lane order.  Returns the slot of this lane
+// (or a value >= limit when the work is exhausted); all 32 lanes must call.
+__device__ __forceinline__ int64_t claim_slot(bool need, unsigned long long *counter)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    int64_t slot = INT64_MAX;
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader)
+            base = atomicAdd(counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need)
+            slot = (int64_t)(base + __popc(m & lane_mask_lt()));
+    }
+    return slot;
+}
+
 // kernel modes: results, visit counts, learned bounded pass, fallback pass
 // (MODE_BOUNDED: per-query cull radius r2q; a query whose list is not full
 // restarts in the same lane with the caller's radius)
 enum : int { MODE_RESULTS = 0, MODE_VISITS = 1, MODE_BOUNDED = 2 };
+
+// Ablation kernels (kdt_ablation.cu): flags select the variant
+int launch_ablation(int layout, const QueryArgs &a, int flags, int mode, cudaStream_t s);
 
 // Launch a traversal for one layout (mode: MODE_*).
 int launch_query_layout0(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s);

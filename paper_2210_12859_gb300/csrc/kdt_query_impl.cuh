@@ -7,26 +7,6 @@
 
 namespace kdt {
 
-// Claim the next queries for the lanes of the warp that need one: one atomic
-// per warp, consecutive slots in lane order.  Returns the slot of this lane
-// (or a value >= limit when the work is exhausted); all 32 lanes must call.
-__device__ __forceinline__ int64_t claim_slot(bool need, unsigned long long *counter)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    int64_t slot = INT64_MAX;
-    if (m) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader)
-            base = atomicAdd(counter, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (need)
-            slot = (int64_t)(base + __popc(m & lane_mask_lt()));
-    }
-    return slot;
-}
-
 // Single tree.  Persistent blocks stage the top levels once; every lane then
 // runs queries back to back: when its query ends it claims the next one
 // (persistent threads with replacement), so a lane never idles while a slow

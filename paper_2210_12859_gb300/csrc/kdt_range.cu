@@ -62,23 +62,6 @@ __device__ __forceinline__ uint32_t node_id(const NodeVal<LAYOUT> &nd, const int
         return (uint32_t)__ldg(ids + n);
 }
 
-__device__ __forceinline__ int64_t claim(bool need, unsigned long long *counter)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    int64_t slot = INT64_MAX;
-    if (m) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (lane == leader)
-            base = atomicAdd(counter, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (need)
-            slot = (int64_t)(base + __popc(m & lane_mask_lt()));
-    }
-    return slot;
-}
-
 // Final value of a reduction: no hit -> 0; mean: / count; density: / fl(pi * R2).
 __device__ __forceinline__ float finish_reduce(float s, int64_t n, int mode, float R2)
 {
@@ -108,7 +91,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
     const uint32_t cap = 3u * (uint32_t)a.N + 3u;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
-        const int64_t slot = claim(need, a.counter);
+        const int64_t slot = claim_slot(need, a.counter);
         if (need) {
             if (slot < a.Q) {
                 qi = a.perm ? (int64_t)a.perm[slot] : slot;

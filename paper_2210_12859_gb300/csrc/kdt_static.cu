@@ -79,8 +79,8 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
         return set_error(KDT_EINVAL, "k must be in [1, 64] (got %d)", k);
     if (!(max_radius >= 0.f))
         return set_error(KDT_EINVAL, "max_radius must be >= 0 (got %g)", (double)max_radius);
-    if (flags & KDT_LEARNED)
-        return set_error(KDT_EINVAL, "kdt_knn_static does not take KDT_LEARNED");
+    if (flags & (KDT_LEARNED | KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
+        return set_error(KDT_EINVAL, "kdt_knn_static takes neither KDT_LEARNED nor the traversal ablations");
     if (Q > 0 && (!d_q || !d_ids || !d_d2))
         return set_error(KDT_EINVAL, "NULL query or output pointer");
     if (Q == 0)
