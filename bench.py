@@ -256,6 +256,10 @@ def main():
     flags = kdt.KDT_MORTON | kdt.KDT_COST_ORDER
     tree = kdt.kdt_build(dp)
     stream = torch.cuda.current_stream()
+    # the library's launch tuner (inline depth, claim steps, staging depth),
+    # measured on 2^20 of the queries before anything is timed
+    kdt.kdt_autotune(tree, dq, K_NN, flags)
+    tuned = dict(zip(("stage_levels", "claim_steps", "inline_depth"), kdt.kdt_tuned_params(tree, K_NN)))
 
     def step():
         kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC)
@@ -401,7 +405,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.log2n),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args.log2n), launch_autotuned=tuned),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk.summary(), "bit_exact_sample": exact,
             "breakdown": {"build_ms": build_ms, "query_ms": query_ms, "query_qps": n / (query_ms / 1000.0)},

@@ -77,10 +77,15 @@ def run_config(args):
             dp, dq = cu(pts), cu(qs)
             tree = kdt.kdt_build(dp)
             build_ms = timeit(lambda: kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC), 3)
+            default_ms = timeit(lambda: kdt.kdt_knn(tree, dq, 16, flags=kdt.KDT_MORTON), 2)
+            kdt.kdt_autotune(tree, dq, 16, kdt.KDT_MORTON)
+            tuned = kdt.kdt_tuned_params(tree, 16)
             ms = timeit(lambda: kdt.kdt_knn(tree, dq, 16, flags=kdt.KDT_MORTON), 2)
             gi, gd = kdt.kdt_knn(tree, dq, 16, flags=kdt.KDT_MORTON)
             v = kdt.kdt_knn_visits(tree, dq, 16, flags=kdt.KDT_MORTON).double().mean().item()
             _emit(config="dims N=Q=2^22 kNN k=16 ordered", form=name, query_qps=n / (ms / 1e3), query_ms=ms,
+                  default_launch_query_ms=default_ms,
+                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth"), tuned)),
                   build_ms=build_ms, visits_per_query=v,
                   bit_exact_sample=_exact(oracle, pts, qs, gi.cpu().numpy(), gd.cpu().numpy(), 16))
             del tree
@@ -137,6 +142,17 @@ def run_config(args):
             tree = kdt.kdt_build(dp)
             ref_i, ref_d = kdt.kdt_knn(tree, dq, k, math.inf, base)
             out_i, out_d = torch.empty_like(ref_i), torch.empty_like(ref_d)
+            kdt.kdt_autotune(tree, dq, k, base)
+            tuned = kdt.kdt_tuned_params(tree, k)
+            ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, base, out_i, out_d), 2)
+            same = bool(torch.equal(out_i, ref_i) and torch.equal(out_d.view(torch.int32), ref_d.view(torch.int32)))
+            _emit(config=cname, form="production, autotuned launch", query_qps=len(q_) / (ms / 1e3), query_ms=ms,
+                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth"), tuned)),
+                  identical_to_production=same)
+            # the forms below run at the untuned defaults
+            kdt.kdt_set_stage_levels(tree, 0)
+            kdt.kdt_set_claim_steps(tree, 32 if k <= 1 else 64)
+            kdt.kdt_set_inline_depth(tree, 2)
             for name, fl in forms:
                 ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, base | fl, out_i, out_d), 2)
                 same = bool(torch.equal(out_i, ref_i) and torch.equal(out_d.view(torch.int32), ref_d.view(torch.int32)))

@@ -347,12 +347,35 @@ void kdt_forest_free(kdt_forest *forest);
  * one, else 0: no staging).  levels in [-1, 16]. */
 int kdt_set_stage_levels(kdt_tree *tree, int levels);
 
-/* Time the plain traversal of up to 2^20 of the given queries for each
- * staging depth in {0, 4, 6, 8, 10, 11, 12} (within 64 KB of shared memory)
- * and remember the fastest for this tree's shape (GPU name, D, k bucket,
- * floor(log2 N)); later queries on trees of that shape use it unless
- * kdt_set_stage_levels overrides.  Synchronous.  *best_levels and *best_ms
- * (may be NULL) receive the choice and its time per launch. */
+/* Traversal steps a lane takes between two claim rounds of its warp (a lane
+ * whose query ends waits for the round to take its next one): large values
+ * amortise the claim vote for long queries, small ones idle less behind short
+ * queries.  -1 restores the tuned or default value (32 for k = 1, 64
+ * otherwise).  Range 1..256. */
+int kdt_set_claim_steps(kdt_tree *tree, int steps);
+
+/* Depth of the bottom subtrees one traversal step processes whole, with all
+ * their loads issued at once: 2 (default) saves steps on long queries, 1
+ * avoids loads that short queries rarely use, 0 selects the simplest kernel
+ * (one node per step; ordered kNN with k <= 16 and D <= 4 without staging,
+ * else depth 1 is used); -1 restores the tuned or default value.  Results and
+ * processed nodes are the same for every depth. */
+int kdt_set_inline_depth(kdt_tree *tree, int depth);
+
+/* The launch parameters kdt_knn uses for this tree and k: set on the tree,
+ * else tuned for its shape (kdt_autotune / kdt_tuning_load), else defaults
+ * (no staging, 32 claim steps for k = 1 and 64 otherwise, inline depth 2). */
+int kdt_tuned_params(const kdt_tree *tree, int k, int *stage_levels, int *claim_steps, int *inline_depth);
+
+/* Time the plain traversal of up to 2^20 of the given queries and remember
+ * the fastest launch parameters for this tree's shape (GPU name, D, k bucket,
+ * floor(log2 N)): a coordinate search over the inline depth {2, 1, 0}, then
+ * the claim steps {16, 32, 64, 128}, then the staging depth {0, 4, 6, 8}, each
+ * candidate timed over two launches after a warm-up and taken only when it is
+ * faster than the best so far by 2 % (staging: 5 %).  Later queries on trees of that shape use the choice unless
+ * the kdt_set_* calls override.  Synchronous.  *best_levels and *best_ms (may
+ * be NULL) receive the staging depth and the best time per launch;
+ * kdt_tuned_params reports all three. */
 int kdt_autotune(kdt_tree *tree, const float *d_queries, int64_t Q, int k, int flags, int *best_levels,
                  float *best_ms, void *stream);
 

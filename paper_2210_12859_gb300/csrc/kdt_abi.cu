@@ -232,10 +232,19 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.err = t->err;
     a.counter = counter;
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
+    a.claim_steps = claim_steps_for(t, k);
+    a.inline_depth = inline_depth_for(t, k);
     cudaEvent_t stop;
     KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
+    // inline depth 0: the one-node-per-step kernel, where it applies
+    const bool simple = a.inline_depth == 0 && a.staged == 0 && !(flags & KDT_UNORDERED) && k <= 16 &&
+                        t->layout != 2 && (mode == MODE_RESULTS || mode == MODE_VISITS);
+    if (a.inline_depth == 0 && !simple)
+        a.inline_depth = 1;
     if (flags & (KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
         KDT_TRY(launch_ablation(t->layout, a, flags, mode, s));
+    else if (simple)
+        KDT_TRY(launch_ablation(t->layout, a, KDT_PLAIN_STEP, mode, s));
     else
         KDT_TRY(launch_query(t->layout, a, !(flags & KDT_UNORDERED), mode, false, s));
     if (stop)

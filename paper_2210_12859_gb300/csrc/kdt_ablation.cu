@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(ABL_THREADS) ablation_kernel(const QueryArgs a
         if (qi < 0)
             continue;
         bool done = false;
-        for (int s = 0; s < STEPS_PER_CLAIM && !done; ++s) {
+        for (int s = 0; s < a.claim_steps && !done; ++s) {
             if (++steps > cap) {
                 bad = true;
                 done = true;

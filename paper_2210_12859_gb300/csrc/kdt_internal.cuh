@@ -259,6 +259,12 @@ struct kdt_tree {
     // top tree levels staged in shared memory by the traversal kernels
     // (-1: the tuned or default depth for this tree's shape)
     int stage_levels = -1;
+    // traversal steps between two claim rounds of a warp (-1: the tuned or
+    // default value for this tree's shape)
+    int claim_steps = -1;
+    // depth of the bottom subtrees a traversal step processes whole (1 or 2;
+    // -1: tuned or default)
+    int inline_depth = -1;
     // per-point payload in node order [N][payload_c] and node_of[input index]
     // (kdt_tree_set_payload; dropped by a rebuild)
     float *payload = nullptr;
@@ -286,6 +292,8 @@ namespace kdt {
 // staging depth (levels) for a query on tree t with k neighbours: the tree's
 // own setting, else the tuned value for its shape, else the default
 int stage_levels_for(const kdt_tree *t, int k);
+int claim_steps_for(const kdt_tree *t, int k);
+int inline_depth_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,
 // D <= 3), stored in the node (layout 3); else level mod D

@@ -11,7 +11,7 @@ namespace kdt {
 // runs queries back to back: when its query ends it claims the next one
 // (persistent threads with replacement), so a lane never idles while a slow
 // neighbour in its warp is still traversing, until the work runs out.
-template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE>
+template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_kernel(const QueryArgs a)
 {
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
         list.stride = blockDim.x;
     }
-    Walker<LAYOUT, ORDERED> w;
+    Walker<LAYOUT, ORDERED, INLINE> w;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
         const int64_t slot = claim_slot(need, a.counter);
@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
             break;
         if (qi < 0)
             continue;
-        // up to STEPS_PER_CLAIM steps between claims: amortises the warp vote
+        // up to claim_steps steps between claims: amortises the warp vote
         bool overflow = false;
         bool fin = false;
-        for (int s = 0; s < STEPS_PER_CLAIM && !fin; ++s)
+        for (int s = 0; s < a.claim_steps && !fin; ++s)
             fin = w.template step<STAGE>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits, overflow);
         if (!fin)
             continue;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
             continue;
         bool overflow = false;
         bool fin = false;
-        for (int s = 0; s < STEPS_PER_CLAIM && !fin; ++s)
+        for (int s = 0; s < a.claim_steps && !fin; ++s)
             fin = w.template step<false>(nodes, ids, nullptr, 0, N, a.D, q, list, visits, overflow);
         if (!fin)
             continue;
@@ -179,26 +179,26 @@ inline int launch_kernel(Kern fn, int threads, size_t smem, const QueryArgs &a, 
     return KDT_OK;
 }
 
-template <int LAYOUT, int K, bool STAGE>
+template <int LAYOUT, int K, bool STAGE, int INLINE>
 inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, size_t smem, cudaStream_t s)
 {
     switch (mode) {
     case MODE_VISITS:
         if (ordered)
-            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS, STAGE>, threads, smem, a, s);
-        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS, STAGE, INLINE>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE, INLINE>, threads, smem, a, s);
     case MODE_BOUNDED:
         if constexpr (LAYOUT == 0 || LAYOUT == 3) {
             if (ordered)
-                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE>, threads, smem, a, s);
-            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE>, threads, smem, a, s);
+                return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE, INLINE>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE, INLINE>, threads, smem, a, s);
         } else {
             return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
         }
     default:
         if (ordered)
-            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, STAGE>, threads, smem, a, s);
-        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, STAGE>, threads, smem, a, s);
+            return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, STAGE, INLINE>, threads, smem, a, s);
+        return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, STAGE, INLINE>, threads, smem, a, s);
     }
 }
 
@@ -216,9 +216,12 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
         return launch_kernel(knn_forest_kernel<LAYOUT, K, false>, threads, list_bytes, a, s);
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
+    // staging is paired with depth-2 inlining only (both serve long queries)
     if (a.staged > 0)
-        return launch_mode<LAYOUT, K, true>(a, ordered, mode, threads, smem, s);
-    return launch_mode<LAYOUT, K, false>(a, ordered, mode, threads, smem, s);
+        return launch_mode<LAYOUT, K, true, 2>(a, ordered, mode, threads, smem, s);
+    if (a.inline_depth == 1)
+        return launch_mode<LAYOUT, K, false, 1>(a, ordered, mode, threads, smem, s);
+    return launch_mode<LAYOUT, K, false, 2>(a, ordered, mode, threads, smem, s);
 }
 
 template <int LAYOUT>

@@ -244,10 +244,13 @@ __device__ __forceinline__ void process(const NodeVal<LAYOUT> &nd, int n, const 
 //    if in range), and the step returns to the parent - the same processed
 //    nodes in the same order, without the steps into and out of them.
 // Depth of the bottom subtrees processed inside one step (1: a node whose
-// children are leaves; 2: also a node whose grandchildren are leaves).
+// children are leaves; 2: also a node whose grandchildren are leaves).  Depth
+// 2 pays when queries process many nodes; for short queries the four extra
+// up-front loads cost more than the steps they save, and depth 1 is faster
+// (the tuner measures which).
 constexpr int INLINE_DEPTH = 2;
 
-template <int LAYOUT, bool ORDERED>
+template <int LAYOUT, bool ORDERED, int INLINE = INLINE_DEPTH>
 struct Walker {
     static constexpr int NC = LayoutTraits<LAYOUT>::NC;
     int curr, prev, dim;
@@ -349,7 +352,7 @@ struct Walker {
         const int parent = (curr - 1) >> 1;  // -1 for the root
         int next;
         const int rc = lc + 1;
-        if (INLINE_DEPTH >= 2 && from_parent && lc < N && 2 * lc + 1 < N &&
+        if (INLINE >= 2 && from_parent && lc < N && 2 * lc + 1 < N &&
             2u * (2u * (uint32_t)lc + 1u) + 1u >= (uint32_t)N) {
             // the children have only leaves below them: the whole depth-2
             // subtree in the machine's order.  Its six node indices are known
@@ -380,7 +383,7 @@ struct Walker {
                     leaf_parent(rc, dim1, c1, g10, g11, ids, N, q, list, visits);
             }
             next = parent;
-        } else if (from_parent && lc < N && 2 * lc + 1 >= N) {
+        } else if (INLINE >= 1 && from_parent && lc < N && 2 * lc + 1 >= N) {
             // both children are leaves (the right one may be missing): both
             // loads first
             const NodeVal<LAYOUT> a = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);

@@ -1,9 +1,19 @@
-// Launch tuning: how many top tree levels the traversal kernels stage in
-// shared memory.  Staging saves the latency of the first loads of every query
-// but takes shared memory from the same on-chip array as the L1 cache, which
-// the deeper levels need; the best depth depends on the tree and the queries,
-// so it is measured (kdt_autotune) and remembered per shape
-// (GPU, D, k bucket, floor(log2 N)), in memory and optionally in a JSON file.
+// Launch tuning of the traversal kernels.  Three choices never change a result
+// (every combination processes the same nodes in the same order) but move its
+// speed, and the best values depend on how much work a query does:
+//   * stage_levels: top tree levels staged in shared memory (saves the latency
+//     of the first loads, but the shared memory comes out of the same on-chip
+//     array as the L1 cache that the deeper levels need);
+//   * claim_steps: traversal steps a lane takes between two claim rounds of its
+//     warp (long runs amortise the warp vote; a lane whose query has ended
+//     waits for the round);
+//   * inline_depth: depth of the bottom subtrees one step processes whole
+//     (2 saves steps on long queries; 1 avoids the extra up-front loads that
+//     short queries rarely use; 0 selects the simplest kernel, one node per
+//     step, where it applies: ordered, k <= 16, D <= 4, no staging).
+// kdt_autotune measures them on the caller's queries and remembers the best
+// per shape (GPU, D, k bucket, floor(log2 N)), in memory and optionally in a
+// JSON file; without a tuning the defaults below apply.
 #include <stdio.h>
 #include <string.h>
 
@@ -20,11 +30,21 @@ namespace kdt {
 namespace {
 
 constexpr int DEFAULT_STAGE_LEVELS = 0;
+constexpr int DEFAULT_INLINE_DEPTH = 2;
+// measured on GB300: 64 steps per claim round is best for k >= 2 on every
+// workload tried, 32 for fcp
+int default_claim_steps(int k) { return k <= 1 ? 32 : 64; }
+
+struct Tuned {
+    int stage_levels;
+    int claim_steps;
+    int inline_depth;
+};
 
 using ShapeKey = std::tuple<std::string, int, int, int>;  // gpu, D, k bucket, log2 N
 
 std::mutex g_mu;
-std::map<ShapeKey, int> g_tuned;
+std::map<ShapeKey, Tuned> g_tuned;
 
 int k_bucket(int k)
 {
@@ -60,19 +80,48 @@ ShapeKey shape_of(const kdt_tree *t, int k)
     return ShapeKey(gpu_name(), t->D, k_bucket(k), floor_log2((uint64_t)t->N));
 }
 
+bool tuned_for(const kdt_tree *t, int k, Tuned *out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_tuned.empty())
+        return false;
+    auto it = g_tuned.find(shape_of(t, k));
+    if (it == g_tuned.end())
+        return false;
+    *out = it->second;
+    return true;
+}
+
+bool stage_fits(const kdt_tree *t, int levels, int budget)
+{
+    const int per = t->layout == 2 ? 32 : 16;
+    return levels <= 0 || (((int64_t)1 << levels) - 1) * per <= budget;
+}
+
 }  // namespace
 
 int stage_levels_for(const kdt_tree *t, int k)
 {
     if (t->stage_levels >= 0)
         return t->stage_levels;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_tuned.empty()) {
-        auto it = g_tuned.find(shape_of(t, k));
-        if (it != g_tuned.end())
-            return it->second;
-    }
-    return DEFAULT_STAGE_LEVELS;
+    Tuned v;
+    return tuned_for(t, k, &v) ? v.stage_levels : DEFAULT_STAGE_LEVELS;
+}
+
+int claim_steps_for(const kdt_tree *t, int k)
+{
+    if (t->claim_steps > 0)
+        return t->claim_steps;
+    Tuned v;
+    return tuned_for(t, k, &v) ? v.claim_steps : default_claim_steps(k);
+}
+
+int inline_depth_for(const kdt_tree *t, int k)
+{
+    if (t->inline_depth >= 0)
+        return t->inline_depth;
+    Tuned v;
+    return tuned_for(t, k, &v) ? v.inline_depth : DEFAULT_INLINE_DEPTH;
 }
 
 }  // namespace kdt
@@ -87,20 +136,58 @@ int kdt_set_stage_levels(kdt_tree *t, int levels)
         return set_error(KDT_EINVAL, "tree is NULL");
     if (levels < -1 || levels > 16)
         return set_error(KDT_EINVAL, "levels must be in [-1, 16] (got %d)", levels);
-    const int per = t->layout == 2 ? 32 : 16;
-    if (levels > 0 && (((int64_t)1 << levels) - 1) * per > 160 * 1024)
+    if (!stage_fits(t, levels, 160 * 1024))
         return set_error(KDT_EINVAL, "%d staged levels exceed the shared-memory budget", levels);
     t->stage_levels = levels;
     return KDT_OK;
 }
 
+int kdt_set_claim_steps(kdt_tree *t, int steps)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (steps < -1 || steps == 0 || steps > 256)
+        return set_error(KDT_EINVAL, "steps must be -1 or in [1, 256] (got %d)", steps);
+    t->claim_steps = steps;
+    return KDT_OK;
+}
+
+int kdt_set_inline_depth(kdt_tree *t, int depth)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (depth < -1 || depth > 2)
+        return set_error(KDT_EINVAL, "depth must be -1, 0, 1 or 2 (got %d)", depth);
+    t->inline_depth = depth;
+    return KDT_OK;
+}
+
+int kdt_tuned_params(const kdt_tree *t, int k, int *stage_levels, int *claim_steps, int *inline_depth)
+{
+    if (!t || k < 1 || k > 64)
+        return set_error(KDT_EINVAL, "bad tree or k");
+    if (stage_levels)
+        *stage_levels = stage_levels_for(t, k);
+    if (claim_steps)
+        *claim_steps = claim_steps_for(t, k);
+    if (inline_depth)
+        *inline_depth = inline_depth_for(t, k);
+    return KDT_OK;
+}
+
+// Coordinate search: inline depth, then claim steps, then staging depth, each
+// over its candidates with the others at their best so far; every candidate is
+// timed over two launches on up to 2^20 of the queries after one warm-up, and
+// replaces the best so far only if it is faster by a margin (2 %; 5 % for
+// staging, whose cost in occupancy shows more on long runs than on a sample).
+// Staging is limited to 8 levels (4 KB), which leaves occupancy unchanged.
 int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int *best_levels, float *best_ms,
                  void *stream)
 {
     if (!t || !d_q || Q < 1 || k < 1 || k > 64)
         return set_error(KDT_EINVAL, "bad autotune arguments");
-    if (flags & KDT_LEARNED)
-        return set_error(KDT_EINVAL, "autotune the plain traversal (no KDT_LEARNED)");
+    if (flags & (KDT_LEARNED | KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
+        return set_error(KDT_EINVAL, "autotune the plain traversal (no KDT_LEARNED, no ablation)");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = Q < ((int64_t)1 << 20) ? Q : ((int64_t)1 << 20);
     int32_t *ids = nullptr;
@@ -110,36 +197,58 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     cudaEvent_t e0, e1;
     KDT_CUDA(cudaEventCreate(&e0));
     KDT_CUDA(cudaEventCreate(&e1));
-    const int saved = t->stage_levels;
-    const int per = t->layout == 2 ? 32 : 16;
-    const int cand[] = {0, 4, 6, 8, 10, 11, 12};
-    int best = DEFAULT_STAGE_LEVELS;
+    const int saved_stage = t->stage_levels, saved_claim = t->claim_steps, saved_inline = t->inline_depth;
+    Tuned best{DEFAULT_STAGE_LEVELS, default_claim_steps(k), DEFAULT_INLINE_DEPTH};
     float best_t = 3.4e38f;
     int rc = KDT_OK;
-    for (int c : cand) {
-        if (c > 0 && (((int64_t)1 << c) - 1) * per > 64 * 1024)
-            continue;
-        t->stage_levels = c;
-        float ms = 0.f;
+    auto measure = [&](const Tuned &c, float *out) {
+        t->stage_levels = c.stage_levels;
+        t->claim_steps = c.claim_steps;
+        t->inline_depth = c.inline_depth;
         for (int rep = 0; rep < 3 && rc == KDT_OK; ++rep) {
             rc = run_query(t, d_q, n, k, INFINITY, flags & ~KDT_NO_STAGE, MODE_RESULTS, ids, d2, nullptr, s);
             if (rc == KDT_OK && rep == 0)
                 rc = cudaEventRecord(e0, s) == cudaSuccess ? KDT_OK : set_error(KDT_ECUDA, "event record");
         }
-        if (rc != KDT_OK)
-            break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        float ms = 0.f;
+        if (rc == KDT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
             rc = set_error(KDT_ECUDA, "event timing failed");
-            break;
-        }
-        ms *= 0.5f;  // two timed launches
-        if (ms < best_t) {
+        *out = ms * 0.5f;  // two timed launches
+        return rc == KDT_OK;
+    };
+    auto consider = [&](Tuned c, float margin) {
+        float ms;
+        if (measure(c, &ms) && ms < best_t * (1.f - margin)) {
             best_t = ms;
             best = c;
         }
+    };
+    const bool simple_ok = !(flags & KDT_UNORDERED) && k <= 16 && t->layout != 2;
+    consider(best, 0.f);
+    for (int d : {1, 0}) {
+        Tuned c = best;
+        c.inline_depth = d;
+        if (rc == KDT_OK && (d > 0 || simple_ok))
+            consider(c, 0.02f);
     }
-    t->stage_levels = saved;
+    for (int cs : {16, 32, 64, 128}) {
+        Tuned c = best;
+        c.claim_steps = cs;
+        if (rc == KDT_OK && cs != best.claim_steps)
+            consider(c, 0.02f);
+    }
+    if (best.inline_depth > 0) {
+        for (int lv : {4, 6, 8}) {
+            Tuned c = best;
+            c.stage_levels = lv;
+            if (rc == KDT_OK && stage_fits(t, lv, 64 * 1024))
+                consider(c, 0.05f);
+        }
+    }
+    t->stage_levels = saved_stage;
+    t->claim_steps = saved_claim;
+    t->inline_depth = saved_inline;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(ids, s);
@@ -151,7 +260,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
         g_tuned[shape_of(t, k)] = best;
     }
     if (best_levels)
-        *best_levels = best;
+        *best_levels = best.stage_levels;
     if (best_ms)
         *best_ms = best_t;
     return KDT_OK;
@@ -161,7 +270,7 @@ int kdt_tuning_save(const char *path)
 {
     if (!path)
         return set_error(KDT_EINVAL, "path is NULL");
-    std::vector<std::pair<ShapeKey, int>> rows;
+    std::vector<std::pair<ShapeKey, Tuned>> rows;
     {
         std::lock_guard<std::mutex> lock(g_mu);
         rows.assign(g_tuned.begin(), g_tuned.end());
@@ -172,16 +281,20 @@ int kdt_tuning_save(const char *path)
     bool ok = fprintf(f, "[\n") > 0;
     for (size_t i = 0; i < rows.size() && ok; ++i) {
         const ShapeKey &key = rows[i].first;
-        ok = fprintf(f, "  {\"gpu\": \"%s\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d}%s\n",
-                     std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), rows[i].second,
-                     i + 1 < rows.size() ? "," : "") > 0;
+        const Tuned &v = rows[i].second;
+        ok = fprintf(f,
+                     "  {\"gpu\": \"%s\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d, "
+                     "\"claim_steps\": %d, \"inline_depth\": %d}%s\n",
+                     std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), v.stage_levels,
+                     v.claim_steps, v.inline_depth, i + 1 < rows.size() ? "," : "") > 0;
     }
     ok = ok && fprintf(f, "]\n") > 0;
     ok = (fclose(f) == 0) && ok;
     return ok ? KDT_OK : set_error(KDT_EIO, "write to %s failed", path);
 }
 
-// reads the format kdt_tuning_save writes (one object per line)
+// reads the format kdt_tuning_save writes (one object per line); rows without
+// claim_steps / inline_depth take the defaults
 int kdt_tuning_load(const char *path)
 {
     if (!path)
@@ -190,7 +303,7 @@ int kdt_tuning_load(const char *path)
     if (!f)
         return set_error(KDT_EIO, "cannot open %s", path);
     char line[512];
-    std::vector<std::pair<ShapeKey, int>> rows;
+    std::vector<std::pair<ShapeKey, Tuned>> rows;
     bool bad = false;
     while (fgets(line, sizeof line, f)) {
         const char *g = strstr(line, "\"gpu\": \"");
@@ -198,13 +311,22 @@ int kdt_tuning_load(const char *path)
             continue;
         g += 8;
         const char *ge = strchr(g, '"');
-        int D, kb, l2, lv;
+        int D, kb, l2, lv, cs = -1, inl = -1;
         if (!ge || sscanf(ge, "\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d", &D, &kb, &l2,
-                          &lv) != 4 || lv < 0 || lv > 16) {
+                          &lv) != 4 || lv < 0 || lv > 16 || kb < 0 || kb > 5) {
             bad = true;
             break;
         }
-        rows.emplace_back(ShapeKey(std::string(g, ge - g), D, kb, l2), lv);
+        const char *c = strstr(ge, "\"claim_steps\": ");
+        const char *d = strstr(ge, "\"inline_depth\": ");
+        if ((c && (sscanf(c + 15, "%d", &cs) != 1 || cs < 1 || cs > 256)) ||
+            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 2))) {
+            bad = true;
+            break;
+        }
+        const int k_rep = kb == 0 ? 1 : (1 << kb);
+        rows.emplace_back(ShapeKey(std::string(g, ge - g), D, kb, l2),
+                          Tuned{lv, c ? cs : default_claim_steps(k_rep), d ? inl : DEFAULT_INLINE_DEPTH});
     }
     fclose(f);
     if (bad)

@@ -108,6 +108,9 @@ _sig("kdt_forest_export", [_P, _P, _P, _P])
 _sig("kdt_forest_free", [_P], None)
 _sig("kdt_profile_enable", [_P, _I])
 _sig("kdt_set_stage_levels", [_P, _I])
+_sig("kdt_set_claim_steps", [_P, _I])
+_sig("kdt_set_inline_depth", [_P, _I])
+_sig("kdt_tuned_params", [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)])
 _sig("kdt_autotune", [_P, _P, _I64, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_tuning_save", [ctypes.c_char_p])
 _sig("kdt_tuning_load", [ctypes.c_char_p])
@@ -456,12 +459,28 @@ def kdt_knn_host(points, queries, k: int, max_radius: float = math.inf, flags: i
     return out_ids, out_d2
 
 
+def kdt_set_claim_steps(tree: Tree, steps: int) -> None:
+    _check(_lib.kdt_set_claim_steps(tree.handle, steps))
+
+
+def kdt_set_inline_depth(tree: Tree, depth: int) -> None:
+    _check(_lib.kdt_set_inline_depth(tree.handle, depth))
+
+
+def kdt_tuned_params(tree: Tree, k: int):
+    """(stage_levels, claim_steps, inline_depth) that kdt_knn uses for this tree and k."""
+    a, b, c = _I(), _I(), _I()
+    _check(_lib.kdt_tuned_params(tree.handle, k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def kdt_set_stage_levels(tree: Tree, levels: int) -> None:
     _check(_lib.kdt_set_stage_levels(tree.handle, int(levels)))
 
 
 def kdt_autotune(tree: Tree, queries: torch.Tensor, k: int, flags: int = 0, stream=None):
-    """Measure the staging depths on these queries; returns (levels, ms)."""
+    """Tune inline depth, claim steps and staging depth on these queries;
+    returns (staging levels, ms); kdt_tuned_params gives all three."""
     Q = queries.shape[0]
     lv = _I()
     ms = _F()

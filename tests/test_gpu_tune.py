@@ -1,6 +1,7 @@
-"""Launch tuning never changes a result: every staging depth gives the same
-bits; the autotuner picks one of its candidates and its choice survives a
-save / load round trip."""
+"""Launch tuning never changes a result: every staging depth, claim interval
+and inline depth gives the same bits and the same processed-node counts; the
+autotuner picks one of its candidates and its choice survives a save / load
+round trip."""
 import json
 import os
 
@@ -39,16 +40,46 @@ def test_staging_depths_identical(kdt):
         kdt.kdt_set_stage_levels(tree, 17)
 
 
+@pytest.mark.parametrize("k", [1, 8, 32])
+def test_claim_steps_and_inline_depth_identical(kdt, k):
+    mix = synth.gmm_mixture(16, 3, 0.02, 4)
+    pts = synth.gmm_sample(mix, 1 << 16, 5)
+    qs = synth.gmm_queries(mix, 20000, 0.1, 6)
+    tree = kdt.kdt_build(torch.from_numpy(pts).cuda())
+    dq = torch.from_numpy(qs).cuda()
+    ref = kdt.kdt_knn(tree, dq, k, flags=kdt.KDT_MORTON)
+    ref_v = kdt.kdt_knn_visits(tree, dq, k)
+    for depth in (0, 1, 2):
+        for cs in (1, 7, 16, 64, 256):
+            kdt.kdt_set_inline_depth(tree, depth)
+            kdt.kdt_set_claim_steps(tree, cs)
+            assert kdt.kdt_tuned_params(tree, k)[1:] == (cs, depth)
+            for flags in (kdt.KDT_MORTON, kdt.KDT_UNORDERED, 0):
+                r = kdt.kdt_knn(tree, dq, k, flags=flags)
+                assert torch.equal(r[0], ref[0]) and torch.equal(r[1], ref[1]), (depth, cs, flags)
+            assert torch.equal(kdt.kdt_knn_visits(tree, dq, k), ref_v)
+    for bad in ((kdt.kdt_set_inline_depth, 3), (kdt.kdt_set_claim_steps, 0), (kdt.kdt_set_claim_steps, 257)):
+        with pytest.raises(kdt.KdtError):
+            bad[0](tree, bad[1])
+    kdt.kdt_set_inline_depth(tree, -1)
+    kdt.kdt_set_claim_steps(tree, -1)
+    assert kdt.kdt_tuned_params(tree, 1) == (0, 32, 2)
+    assert kdt.kdt_tuned_params(tree, 8) == (0, 64, 2)
+
+
 def test_autotune_and_tuning_file(kdt, tmp_path):
     pts, qs = synth.gmm_large(1 << 18, 1 << 16)
     tree = kdt.kdt_build(torch.from_numpy(pts).cuda())
     dq = torch.from_numpy(qs).cuda()
     lv, ms = kdt.kdt_autotune(tree, dq, 8, kdt.KDT_MORTON)
-    assert lv in (0, 4, 6, 8, 10, 11, 12) and ms > 0
+    assert lv in (0, 4, 6, 8) and ms > 0
+    tlv, cs, depth = kdt.kdt_tuned_params(tree, 8)
+    assert tlv == lv and cs in (16, 32, 64, 128) and depth in (0, 1, 2)
     path = os.path.join(tmp_path, "tuning.json")
     kdt.kdt_tuning_save(path)
     rows = json.load(open(path))
-    assert any(r["D"] == 3 and r["log2n"] == 18 and r["stage_levels"] == lv for r in rows)
+    assert any(r["D"] == 3 and r["log2n"] == 18 and r["stage_levels"] == lv and r["claim_steps"] == cs and
+               r["inline_depth"] == depth for r in rows)
     kdt.kdt_tuning_load(path)
     a = kdt.kdt_knn(tree, dq, 8, flags=kdt.KDT_MORTON)
     kdt.kdt_set_stage_levels(tree, 0)
@@ -57,3 +88,10 @@ def test_autotune_and_tuning_file(kdt, tmp_path):
     open(path, "w").write('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, "stage_levels": 99}\n]\n')
     with pytest.raises(kdt.KdtError):
         kdt.kdt_tuning_load(path)
+    open(path, "w").write('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, "stage_levels": 0, '
+                          '"claim_steps": 64, "inline_depth": 5}\n]\n')
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_tuning_load(path)
+    # rows written before the claim / inline fields existed still load
+    open(path, "w").write('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, "stage_levels": 4}\n]\n')
+    kdt.kdt_tuning_load(path)
