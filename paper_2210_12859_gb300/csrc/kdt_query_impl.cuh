@@ -11,8 +11,15 @@ namespace kdt {
 // runs queries back to back: when its query ends it claims the next one
 // (persistent threads with replacement), so a lane never idles while a slow
 // neighbour in its warp is still traversing, until the work runs out.
+// Register-list kernels with k <= 8 are built for 6 resident blocks per SM
+// (at most 85 registers a thread): the depth-2 kernel otherwise takes 82
+// registers and only 5 blocks fit (measured: 5.4 % faster on the clustered
+// 2^24 workload, no spills; a bound of 8 blocks spills and is slower; k = 16
+// lists would spill under the bound of 6).  The learned radius's bounded
+// kernel runs best at 7 blocks (a small spill; measured 2.7 % faster than 6).
 template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE>
-__global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
+__global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
+                                  K <= 8 ? (MODE == MODE_BOUNDED ? 7 : 6) : 1)
     knn_kernel(const QueryArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
