@@ -162,6 +162,59 @@ def run_config(args):
             del tree, dp, dq, ref_i, ref_d, out_i, out_d
         return
 
+    if args.config == "range":
+        # range queries (count -> offsets -> fill) and payload reductions on
+        # the clustered distribution; hits compared with the oracle on samples
+        n, nq = 1 << 24, 1 << 22
+        mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
+        pts = synth.gmm_sample(mix, n, synth.BASE_SEED + 2)
+        qs = synth.gmm_queries(mix, nq, 0.1, synth.BASE_SEED + 8)
+        dp, dq = cu(pts), cu(qs)
+        tree = kdt.kdt_build(dp)
+        r = 0.001
+        F = kdt.KDT_MORTON
+        sample = np.sort(np.random.default_rng(1).choice(nq, 48, replace=False))
+        cnt_ms = timeit(lambda: kdt.kdt_radius_count(tree, dq, r, F), 3)
+        counts = kdt.kdt_radius_count(tree, dq, r, F)
+        off_ms = timeit(lambda: kdt.kdt_offsets(counts), 3)
+        off, total = kdt.kdt_offsets(counts)
+        fill_ms = timeit(lambda: kdt.kdt_radius_fill(tree, dq, r, off, total, True, F), 3)
+        ids, d2 = kdt.kdt_radius_fill(tree, dq, r, off, total, True, F)
+        kdt.kdt_status(tree)
+        offh, idsh = off.cpu().numpy(), ids.cpu().numpy()
+        _, woff, wids, _ = oracle.radius_brute(pts, qs[sample], r)
+        ok = all(np.array_equal(np.sort(idsh[offh[q]:offh[q + 1]]), wids[woff[j]:woff[j + 1]])
+                 for j, q in enumerate(sample))
+        _emit(config=f"range: gmm N=2^24, Q=2^22 (90% mixture, 10% uniform), ball r={r}", form="ball count / offsets / fill",
+              queries_per_s=nq / ((cnt_ms + off_ms + fill_ms) / 1e3), hits=int(total), hits_per_query=total / nq,
+              hits_per_s=total / ((cnt_ms + off_ms + fill_ms) / 1e3), count_ms=cnt_ms, offsets_ms=off_ms,
+              fill_ms=fill_ms, oracle_sample_sets_equal=ok)
+        lo, hi = (dq - r).contiguous(), (dq + r).contiguous()
+        bc_ms = timeit(lambda: kdt.kdt_box_count(tree, lo, hi, F), 3)
+        bcounts = kdt.kdt_box_count(tree, lo, hi, F)
+        boff, btotal = kdt.kdt_offsets(bcounts)
+        bf_ms = timeit(lambda: kdt.kdt_box_fill(tree, lo, hi, boff, btotal, F), 3)
+        bids = kdt.kdt_box_fill(tree, lo, hi, boff, btotal, F).cpu().numpy()
+        bo = boff.cpu().numpy()
+        _, wbo, wbi = oracle.box_brute(pts, qs[sample] - np.float32(r), qs[sample] + np.float32(r))
+        okb = all(np.array_equal(np.sort(bids[bo[q]:bo[q + 1]]), wbi[wbo[j]:wbo[j + 1]]) for j, q in enumerate(sample))
+        _emit(config=f"range: gmm N=2^24, Q=2^22, box half-width {r}", form="box count / offsets / fill",
+              queries_per_s=nq / ((bc_ms + bf_ms) / 1e3), hits=int(btotal), hits_per_query=btotal / nq,
+              count_ms=bc_ms, fill_ms=bf_ms, oracle_sample_sets_equal=okb)
+        power = np.random.default_rng(2).random((n, 3)).astype(np.float32)  # photon power (RGB)
+        kdt.kdt_tree_set_payload(tree, cu(power))
+        red_ms = timeit(lambda: kdt.kdt_radius_reduce(tree, dq, r, kdt.KDT_REDUCE_DENSITY, F), 3)
+        knn_ms = timeit(lambda: kdt.kdt_knn_reduce(tree, dq, 32, math.inf, kdt.KDT_REDUCE_DENSITY, F), 2)
+        ko, kd = kdt.kdt_knn(tree, dq[torch.from_numpy(sample).cuda()], 32)
+        want = oracle.knn_reduce(ko.cpu().numpy(), kd.cpu().numpy(), power, 2)
+        got = kdt.kdt_knn_reduce(tree, dq, 32, math.inf, kdt.KDT_REDUCE_DENSITY, F).cpu().numpy()[sample]
+        _emit(config="photon-map density (RGB power payload), gmm N=2^24, Q=2^22",
+              form="fixed-radius gather (kdt_radius_reduce) / k=32 nearest (kdt_knn_reduce)",
+              radius_reduce_qps=nq / (red_ms / 1e3), radius_reduce_ms=red_ms, knn_reduce_qps=nq / (knn_ms / 1e3),
+              knn_reduce_ms=knn_ms, knn_reduce_equals_oracle_on_sample=bool(np.array_equal(got.view(np.uint32),
+                                                                                            want.view(np.uint32))))
+        return
+
     if args.config == "batched":
         c = synth.clouds(4096, seed=synth.BASE_SEED + 5)
         dp, dq = cu(c.points), cu(c.queries)
