@@ -283,6 +283,8 @@ struct kdt_forest {
     int64_t *h_offsets = nullptr;  // host copy [T+1]
     int *err = nullptr;
     void *graph = nullptr;         // cached graph of the batched query
+    int threads = 0;               // block size of the batched kernel (0: default 128)
+    int claim_steps = 0;           // traversal steps between claim rounds (0: default for k)
 };
 
 // allocate an empty tree object with device arrays for N nodes of dimension D
@@ -293,6 +295,8 @@ namespace kdt {
 // own setting, else the tuned value for its shape, else the default
 int stage_levels_for(const kdt_tree *t, int k);
 int claim_steps_for(const kdt_tree *t, int k);
+// default claim steps for k neighbours (no tuning)
+int default_claim_steps_k(int k);
 int inline_depth_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,

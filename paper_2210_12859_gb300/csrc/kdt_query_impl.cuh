@@ -213,7 +213,7 @@ template <int LAYOUT, int K>
 inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cudaStream_t s)
 {
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
-    const int threads = K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS;
+    const int threads = batched && a.threads > 0 ? a.threads : (K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS);
     size_t list_bytes = K <= MAX_REG_K ? 0 : (size_t)a.k * threads * 8;
     if (batched) {
         if constexpr (LAYOUT == 3)

@@ -100,6 +100,8 @@ bool stage_fits(const kdt_tree *t, int levels, int budget)
 
 }  // namespace
 
+int default_claim_steps_k(int k) { return default_claim_steps(k); }
+
 int stage_levels_for(const kdt_tree *t, int k)
 {
     if (t->stage_levels >= 0)

@@ -44,3 +44,30 @@ def test_binding_names_match_abi():
 def test_last_error_callable_without_gpu(lib):
     lib.kdt_last_error.restype = ctypes.c_char_p
     assert isinstance(lib.kdt_last_error(), bytes)
+
+
+def test_tuning_file_round_trip_without_gpu(lib, tmp_path):
+    """Tuning files are host-only: rows written before the claim / inline
+    fields existed load with the defaults, new rows keep their values, and
+    malformed rows are rejected with KDT_EIO (-7)."""
+    import json
+
+    lib.kdt_tuning_load.argtypes = [ctypes.c_char_p]
+    lib.kdt_tuning_save.argtypes = [ctypes.c_char_p]
+    src = tmp_path / "in.json"
+    src.write_text('[\n'
+                   '  {"gpu": "cpu-test-a", "D": 3, "k_bucket": 3, "log2n": 18, "stage_levels": 4},\n'
+                   '  {"gpu": "cpu-test-b", "D": 2, "k_bucket": 0, "log2n": 20, "stage_levels": 0, '
+                   '"claim_steps": 128, "inline_depth": 0}\n]\n')
+    assert lib.kdt_tuning_load(str(src).encode()) == 0
+    out = tmp_path / "out.json"
+    assert lib.kdt_tuning_save(str(out).encode()) == 0
+    rows = {r["gpu"]: r for r in json.loads(out.read_text())}
+    assert rows["cpu-test-a"]["stage_levels"] == 4
+    assert rows["cpu-test-a"]["claim_steps"] == 64 and rows["cpu-test-a"]["inline_depth"] == 2
+    assert rows["cpu-test-b"]["claim_steps"] == 128 and rows["cpu-test-b"]["inline_depth"] == 0
+    for bad in ('"stage_levels": 99}', '"stage_levels": 0, "claim_steps": 0}',
+                '"stage_levels": 0, "claim_steps": 64, "inline_depth": 3}'):
+        src.write_text('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, ' + bad + '\n]\n')
+        assert lib.kdt_tuning_load(str(src).encode()) == -7
+    assert lib.kdt_tuning_load(str(tmp_path / "missing.json").encode()) == -7

@@ -107,3 +107,33 @@ def test_forest_matches_single_tree_builds(kdt):
         si, sd = kdt.kdt_knn(t, cu(c.queries[c.qoffsets[i]:c.qoffsets[i + 1]]), 8)
         assert torch.equal(si, gi[c.qoffsets[i]:c.qoffsets[i + 1]])
         assert torch.equal(sd, gd[c.qoffsets[i]:c.qoffsets[i + 1]])
+
+
+@pytest.mark.parametrize("k", [1, 8, 32])
+def test_forest_launch_parameters_do_not_change_results(kdt, forest, k):
+    pts, qs, P, Q, off, qoff, f = forest
+    dq = cu(Q)
+    ref_i, ref_d = kdt.kdt_knn_batched(f, dq, qoff, k, flags=kdt.KDT_PER_TREE)
+    for threads in (0, 32, 64, 128):
+        for cs in (0, 1, 16, 256):
+            kdt.kdt_forest_set_launch(f, threads, cs)
+            for flags in (kdt.KDT_MORTON, 0):
+                gi, gd = kdt.kdt_knn_batched(f, dq, qoff, k, flags=flags)
+                assert torch.equal(gi, ref_i) and torch.equal(gd.view(torch.int32), ref_d.view(torch.int32))
+    kdt.kdt_forest_set_launch(f, 0, 0)
+    for bad in ((96 + 64, 0), (48, 0), (0, 257), (-32, 0)):
+        with pytest.raises(kdt.KdtError):
+            kdt.kdt_forest_set_launch(f, *bad)
+
+
+def test_forest_autotune(kdt, forest):
+    pts, qs, P, Q, off, qoff, f = forest
+    dq = cu(Q)
+    ref_i, ref_d = kdt.kdt_knn_batched(f, dq, qoff, 8, flags=kdt.KDT_PER_TREE)
+    th, cs, ms = kdt.kdt_forest_autotune(f, dq, qoff, 8, flags=kdt.KDT_MORTON)
+    assert th in (64, 128) and cs in (16, 32, 64, 128) and ms > 0
+    gi, gd = kdt.kdt_knn_batched(f, dq, qoff, 8, flags=kdt.KDT_MORTON)
+    assert torch.equal(gi, ref_i) and torch.equal(gd.view(torch.int32), ref_d.view(torch.int32))
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_forest_autotune(f, dq, qoff, 8, flags=kdt.KDT_PER_TREE)
+    kdt.kdt_forest_set_launch(f, 0, 0)
