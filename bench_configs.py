@@ -226,7 +226,7 @@ def run_config(args):
         out_d = torch.empty((Q, 8), dtype=torch.float32, device="cuda")
         res = {}
         # the library's batched-launch tuner (block size, claim steps), measured first
-        th, cs, _ = kdt.kdt_forest_autotune(forest, dq, c.qoffsets, 8, math.inf, kdt.KDT_MORTON, out_i, out_d)
+        th, cs, il, _ = kdt.kdt_forest_autotune(forest, dq, c.qoffsets, 8, math.inf, kdt.KDT_MORTON, out_i, out_d)
         for name, fl in (("one persistent graph launch, Morton order", kdt.KDT_MORTON),
                          ("one persistent graph launch", 0),
                          ("one launch per tree", kdt.KDT_PER_TREE)):
@@ -246,6 +246,6 @@ def run_config(args):
         for name, (ms, _, _) in res.items():
             _emit(config=f"batched: 4096 clouds, {int(c.offsets[-1])} points, {Q} queries, kNN k=8", form=name,
                   query_qps=Q / (ms / 1e3), query_ms=ms, forest_build_s=build_s, identical_forms=same,
-                  launch_autotuned={"threads": th, "claim_steps": cs},
+                  launch_autotuned={"threads": th, "claim_steps": cs, "inline_depth": il},
                   bit_exact_sample=ok)
         return

@@ -335,20 +335,21 @@ int kdt_knn_batched(kdt_forest *forest, const float *d_queries, const int64_t *h
 int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids, void *stream);
 
 /* Launch parameters of the batched query: threads per block (0 = 128, else a
- * multiple of 32 up to 128) and traversal steps between two claim rounds of a
- * warp (0 = the default for k, 32 for k = 1 and 64 otherwise; up to 256).
+ * multiple of 32 up to 128), traversal steps between two claim rounds of a
+ * warp (0 = the default for k, 32 for k = 1 and 64 otherwise; up to 256) and
+ * the inline depth (0 = default 2, or 1; see kdt_set_inline_depth).
  * Shared-memory staging does not apply to forests: the lanes of a warp walk
  * different trees.  The next kdt_knn_batched re-captures its graph. */
-int kdt_forest_set_launch(kdt_forest *forest, int threads, int claim_steps);
+int kdt_forest_set_launch(kdt_forest *forest, int threads, int claim_steps, int inline_depth);
 
 /* Time the batched query (kdt_knn_batched with these arguments, graph
- * included; it writes d_ids / d_d2 like that call) for block sizes {128, 64},
- * then claim steps {16, 32, 64, 128}, one warm-up and one timed run each, and
- * keep the fastest on the forest (a candidate must win by 2 %).  Synchronous.
- * *best_threads, *best_claim and *best_ms may be NULL. */
+ * included; it writes d_ids / d_d2 like that call) for inline depths {2, 1},
+ * block sizes {128, 64}, then claim steps {16, 32, 64, 128}, one warm-up and
+ * one timed run each, and keep the fastest on the forest (a candidate must win
+ * by 2 %).  Synchronous.  The out pointers may be NULL. */
 int kdt_forest_autotune(kdt_forest *forest, const float *d_queries, const int64_t *h_query_offsets, int k,
                         float max_radius, int flags, int32_t *d_ids, float *d_d2, int *best_threads,
-                        int *best_claim, float *best_ms, void *stream);
+                        int *best_claim, int *best_inline, float *best_ms, void *stream);
 
 /* Release a forest and its device memory (synchronises the device first). */
 void kdt_forest_free(kdt_forest *forest);

@@ -631,6 +631,7 @@ struct ForestGraph {
     size_t scratch_bytes = 0;
     int threads = 0;           // launch parameters the graph was captured with
     int claim_steps = 0;
+    int inline_depth = 0;
 };
 
 int kdt_build_batched(const float *d_points, const int64_t *h_off, int T, int D, void *stream, kdt_forest **out)
@@ -723,6 +724,7 @@ static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64
     a.q_off = d_qoff;
     a.threads = f->threads;
     a.claim_steps = f->claim_steps > 0 ? f->claim_steps : default_claim_steps_k(k);
+    a.inline_depth = f->inline_depth == 1 ? 1 : 2;
     return launch_query(layout_of(f->f.D), a, !(flags & KDT_UNORDERED), 0, true, s);
 }
 
@@ -798,6 +800,7 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
     }
     const bool same = g->exec && g->q == d_q && g->ids == d_ids && g->d2 == d_d2 && g->k == k && g->r2 == r2 &&
                       g->flags == flags && g->threads == f->threads && g->claim_steps == f->claim_steps &&
+                      g->inline_depth == f->inline_depth &&
                       g->qoff.size() == (size_t)T + 1 &&
                       std::equal(g->qoff.begin(), g->qoff.end(), h_qoff);
     if (!same) {
@@ -822,6 +825,7 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
         g->flags = flags;
         g->threads = f->threads;
         g->claim_steps = f->claim_steps;
+        g->inline_depth = f->inline_depth;
         g->qoff.assign(h_qoff, h_qoff + T + 1);
     }
     Carve c{(char *)g->scratch};
@@ -853,26 +857,29 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
     return KDT_OK;
 }
 
-int kdt_forest_set_launch(kdt_forest *f, int threads, int claim_steps)
+int kdt_forest_set_launch(kdt_forest *f, int threads, int claim_steps, int inline_depth)
 {
     if (!f)
         return set_error(KDT_EINVAL, "forest is NULL");
+    if (inline_depth < 0 || inline_depth > 2)
+        return set_error(KDT_EINVAL, "inline_depth must be 0 (default), 1 or 2 (got %d)", inline_depth);
     if (threads < 0 || threads > REG_THREADS || threads % 32 != 0)
         return set_error(KDT_EINVAL, "threads must be 0 or a multiple of 32 up to %d (got %d)", REG_THREADS, threads);
     if (claim_steps < 0 || claim_steps > 256)
         return set_error(KDT_EINVAL, "claim_steps must be in [0, 256] (got %d)", claim_steps);
     f->threads = threads;
     f->claim_steps = claim_steps;
+    f->inline_depth = inline_depth;
     return KDT_OK;
 }
 
-// Coordinate search over the batched launch: block size {128, 64}, then claim
-// steps {16, 32, 64, 128}; each candidate is the whole batched query (graph
-// included), one warm-up and one timed run, and is taken when it is faster
-// than the best so far by 2 %.
+// Coordinate search over the batched launch: inline depth {2, 1}, block size
+// {128, 64}, then claim steps {16, 32, 64, 128}; each candidate is the whole
+// batched query (graph included), one warm-up and one timed run, and is taken
+// when it is faster than the best so far by 2 %.
 int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int k, float max_radius, int flags,
-                        int32_t *d_ids, float *d_d2, int *best_threads, int *best_claim, float *best_ms,
-                        void *stream)
+                        int32_t *d_ids, float *d_d2, int *best_threads, int *best_claim, int *best_inline,
+                        float *best_ms, void *stream)
 {
     if (!f || !h_qoff || !d_q || !d_ids || !d_d2)
         return set_error(KDT_EINVAL, "NULL forest, query, offset or output pointer");
@@ -882,14 +889,15 @@ int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, 
     cudaEvent_t e0, e1;
     KDT_CUDA(cudaEventCreate(&e0));
     KDT_CUDA(cudaEventCreate(&e1));
-    const int saved_t = f->threads, saved_c = f->claim_steps;
-    int bt = 0, bc = 0, rc = KDT_OK;
+    const int saved_t = f->threads, saved_c = f->claim_steps, saved_i = f->inline_depth;
+    int bt = 0, bc = 0, bi = 2, rc = KDT_OK;
     float best = 3.4e38f;
-    auto trial = [&](int th, int cs) {
+    auto trial = [&](int th, int cs, int inl) {
         if (rc != KDT_OK)
             return;
         f->threads = th;
         f->claim_steps = cs;
+        f->inline_depth = inl;
         rc = kdt_knn_batched(f, d_q, h_qoff, k, max_radius, flags, d_ids, d_d2, stream);
         float ms = 0.f;
         if (rc == KDT_OK && cudaEventRecord(e0, s) != cudaSuccess)
@@ -903,23 +911,30 @@ int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, 
             best = ms;
             bt = th;
             bc = cs;
+            bi = inl;
         }
     };
-    trial(0, 0);
-    trial(64, 0);
+    trial(0, 0, 2);
+    trial(0, 0, 1);
+    const int i_best = bi;
+    trial(64, 0, i_best);
     const int t_best = bt;
     for (int cs : {16, 32, 64, 128})
         if (cs != default_claim_steps_k(k))
-            trial(t_best, cs);
+            trial(t_best, cs, i_best);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != KDT_OK) {
         f->threads = saved_t;
         f->claim_steps = saved_c;
+        f->inline_depth = saved_i;
         return rc;
     }
     f->threads = bt;
     f->claim_steps = bc;
+    f->inline_depth = bi;
+    if (best_inline)
+        *best_inline = bi;
     if (best_threads)
         *best_threads = bt ? bt : REG_THREADS;
     if (best_claim)

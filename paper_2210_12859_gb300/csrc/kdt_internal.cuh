@@ -285,6 +285,7 @@ struct kdt_forest {
     void *graph = nullptr;         // cached graph of the batched query
     int threads = 0;               // block size of the batched kernel (0: default 128)
     int claim_steps = 0;           // traversal steps between claim rounds (0: default for k)
+    int inline_depth = 0;          // bottom-subtree depth per step (0: default 2)
 };
 
 // allocate an empty tree object with device arrays for N nodes of dimension D

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
 // Forest: a lane's query finds its tree by binary search over the query
 // offsets; no shared-memory staging (neighbouring lanes may walk different
 // trees).  Same lane-refill scheme as knn_kernel.
-template <int LAYOUT, int K, bool ORDERED>
+template <int LAYOUT, int K, bool ORDERED, int INLINE>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_forest_kernel(const QueryArgs a)
 {
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         list.s = reinterpret_cast<unsigned long long *>(s_dyn) + threadIdx.x;
         list.stride = blockDim.x;
     }
-    Walker<LAYOUT, ORDERED> w;
+    Walker<LAYOUT, ORDERED, INLINE> w;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
         const int64_t slot = claim_slot(need, a.counter);
@@ -218,9 +218,14 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
     if (batched) {
         if constexpr (LAYOUT == 3)
             return set_error(KDT_EINVAL, "forests store no per-node split dimensions");
+        if (a.inline_depth == 1) {
+            if (ordered)
+                return launch_kernel(knn_forest_kernel<LAYOUT, K, true, 1>, threads, list_bytes, a, s);
+            return launch_kernel(knn_forest_kernel<LAYOUT, K, false, 1>, threads, list_bytes, a, s);
+        }
         if (ordered)
-            return launch_kernel(knn_forest_kernel<LAYOUT, K, true>, threads, list_bytes, a, s);
-        return launch_kernel(knn_forest_kernel<LAYOUT, K, false>, threads, list_bytes, a, s);
+            return launch_kernel(knn_forest_kernel<LAYOUT, K, true, 2>, threads, list_bytes, a, s);
+        return launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2>, threads, list_bytes, a, s);
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
     // staging is paired with depth-2 inlining only (both serve long queries)
