@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(ABL_THREADS) ablation_kernel(const QueryArgs a
                 const int sdim = split_dim_of<LAYOUT>(nd, dim);
                 const float sd = __fsub_rn(select_dim<NC>(q, sdim), select_dim<NC>(nd.c, sdim));
                 const int close = 2 * curr + 1 + (sd > 0.f);
-                const int far = 4 * curr + 3 - close;
+                const int far = 2 * curr + 2 - (sd > 0.f);  // the other child; no 4 * curr (overflows past 2^29)
                 if (far < a.N) {
                     if (sp < STACK_DEPTH) {
                         stk_node[sp] = far;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(ABL_THREADS) ablation_kernel(const QueryArgs a
                 const int sdim = split_dim_of<LAYOUT>(nd, dim);
                 const float sd = __fsub_rn(select_dim<NC>(q, sdim), select_dim<NC>(nd.c, sdim));
                 const int close = 2 * curr + 1 + (sd > 0.f);
-                const int far = 4 * curr + 3 - close;
+                const int far = 2 * curr + 2 - (sd > 0.f);  // the other child; no 4 * curr (overflows past 2^29)
                 const int parent = (curr - 1) >> 1;
                 int next;
                 if (from_parent && close < a.N) {

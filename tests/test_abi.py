@@ -71,3 +71,16 @@ def test_tuning_file_round_trip_without_gpu(lib, tmp_path):
         src.write_text('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, ' + bad + '\n]\n')
         assert lib.kdt_tuning_load(str(src).encode()) == -7
     assert lib.kdt_tuning_load(str(tmp_path / "missing.json").encode()) == -7
+
+
+def test_size_limits_rejected_on_the_host(lib):
+    """N must be in [1, 2^30) and D in [1, 8]: checked before any device
+    access, so a dummy pointer is never touched."""
+    lib.kdt_build_ex.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    for n, d in (((1 << 30), 3), (0, 3), (-5, 3), (100, 0), (100, 9)):
+        assert lib.kdt_build_ex(dummy, n, d, 0, None, ctypes.byref(out)) == -1, (n, d)
+        assert not out.value
+    assert lib.kdt_build_ex(None, 100, 3, 0, None, ctypes.byref(out)) == -1
