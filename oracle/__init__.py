@@ -58,6 +58,8 @@ def _load():
         lib.orc_box_brute.restype = None
         lib.orc_range_stackfree.argtypes = [P, P, P, i64, i32, i32, P, P, i64, f32, P, P, P, P]
         lib.orc_range_stackfree.restype = i32
+        lib.orc_range_visits.argtypes = [P, P, P, i64, i32, i32, P, P, i64, f32, P]
+        lib.orc_range_visits.restype = i32
         lib.orc_range_reduce.argtypes = [P, P, P, i64, i32, P, i64, f32, P, i32, i32, P, P]
         lib.orc_range_reduce.restype = i32
         lib.orc_knn_reduce.argtypes = [P, P, i64, i32, P, i32, i32, P]
@@ -199,6 +201,21 @@ def range_tree(points, node_pid, qa, qb=None, radius: float = 0.0, node_dim=None
     assert lib.orc_range_stackfree(*args, _ptr(counts), _ptr(offsets), _ptr(ids),
                                    None if d2 is None else _ptr(d2)) == 0
     return counts, offsets, ids[: offsets[-1]], (None if d2 is None else d2[: offsets[-1]])
+
+
+def range_visits(points, node_pid, qa, qb=None, radius: float = 0.0, node_dim=None):
+    """Processed nodes of each ball (qb None) or box query's stack-free range traversal."""
+    pts, qa = _f32(points), _f32(qa)
+    N, D = pts.shape
+    Q = qa.shape[0]
+    qb = None if qb is None else _f32(qb)
+    pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    nd = None if node_dim is None else np.ascontiguousarray(node_dim, dtype=np.uint8)
+    v = np.empty(Q, dtype=np.int32)
+    assert _load().orc_range_visits(_ptr(pts), _ptr(pid), None if nd is None else _ptr(nd), N, D,
+                                    0 if qb is None else 1, _ptr(qa), None if qb is None else _ptr(qb), Q,
+                                    float(radius), _ptr(v)) == 0
+    return v
 
 
 REDUCE_SUM, REDUCE_MEAN, REDUCE_DENSITY = 0, 1, 2

@@ -29,7 +29,7 @@
  *   orc_range_stackfree the same queries through the unordered stack-free
  *                       machine with a fixed range (Sec. 3: other primitives
  *                       change only the range test and processNode), hits in
- *                       traversal order
+ *                       traversal order; orc_range_visits its processed nodes
  *   orc_range_reduce    per-query reductions of a per-point payload over those
  *   orc_knn_reduce      hits / over a kNN result (Sec. 3: point types with
  *                       payload such as photon power; the photon-map density
@@ -785,9 +785,10 @@ void orc_box_brute(const float *pts, int64_t N, int D, const float *lo, const fl
  * input indices (and d2 for balls) in traversal order, up to cap of them, and
  * returns their number (or -1 if the step bound was exceeded). */
 static int64_t orc_range_one(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
-                             int kind, const float *a, const float *b, float r2, int32_t *ids, float *d2, int64_t cap)
+                             int kind, const float *a, const float *b, float r2, int32_t *ids, float *d2, int64_t cap,
+                             int64_t *nvisits)
 {
-    int64_t curr = 0, prev = -1, count = 0;
+    int64_t curr = 0, prev = -1, count = 0, visits = 0;
     int64_t bound = 3 * (2 * N + 1) + 8;
     for (int64_t step = 0; step < bound; ++step) {
         int64_t parent = (curr + 1) / 2 - 1;
@@ -799,6 +800,7 @@ static int64_t orc_range_one(const float *pts, const int32_t *node_pid, const ui
         const float *p = pts + (int64_t)node_pid[curr] * D;
         int from_parent = prev < curr;
         if (from_parent) {
+            ++visits;
             int hit;
             float v = 0.0f;
             if (kind == 0) {
@@ -837,8 +839,11 @@ static int64_t orc_range_one(const float *pts, const int32_t *node_pid, const ui
             next = right_in ? rc : parent;
         else
             next = parent;
-        if (next == -1)
+        if (next == -1) {
+            if (nvisits)
+                *nvisits = visits;
             return count;
+        }
         prev = curr;
         curr = next;
     }
@@ -859,13 +864,29 @@ int orc_range_stackfree(const float *pts, const int32_t *node_pid, const uint8_t
         int64_t c;
         if (ids)
             c = orc_range_one(pts, node_pid, node_dim, N, D, kind, qa + q * D, kind ? qb + q * D : NULL, r2,
-                              ids + offsets[q], d2 ? d2 + offsets[q] : NULL, offsets[q + 1] - offsets[q]);
+                              ids + offsets[q], d2 ? d2 + offsets[q] : NULL, offsets[q + 1] - offsets[q], NULL);
         else
             c = orc_range_one(pts, node_pid, node_dim, N, D, kind, qa + q * D, kind ? qb + q * D : NULL, r2,
-                              NULL, NULL, 0);
+                              NULL, NULL, 0, NULL);
         if (c < 0)
             rc = -1;
         counts[q] = (int32_t)c;
+    }
+    return rc;
+}
+
+/* Processed nodes (first visits) of each range query's traversal. */
+int orc_range_visits(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D, int kind,
+                     const float *qa, const float *qb, int64_t Q, float radius, int32_t *visits)
+{
+    float r2 = radius * radius;
+    int rc = 0;
+    for (int64_t q = 0; q < Q; ++q) {
+        int64_t nv = 0;
+        if (orc_range_one(pts, node_pid, node_dim, N, D, kind, qa + q * D, kind ? qb + q * D : NULL, r2, NULL, NULL, 0,
+                          &nv) < 0)
+            rc = -1;
+        visits[q] = (int32_t)nv;
     }
     return rc;
 }
@@ -904,7 +925,7 @@ int orc_range_reduce(const float *pts, const int32_t *node_pid, const uint8_t *n
     int32_t *hits = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
     int rc = 0;
     for (int64_t q = 0; q < Q; ++q) {
-        int64_t n = orc_range_one(pts, node_pid, node_dim, N, D, 0, qs + q * D, NULL, r2, hits, NULL, N);
+        int64_t n = orc_range_one(pts, node_pid, node_dim, N, D, 0, qs + q * D, NULL, r2, hits, NULL, N, NULL);
         if (n < 0) {
             rc = -1;
             n = 0;

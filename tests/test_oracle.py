@@ -702,3 +702,22 @@ def test_close_first_six_point_trace():
     assert tuple(pts[pid[v_root[0]]].tolist()) == (7.0, 2.0)
     assert tuple(pts[pid[v_close[0]]].tolist()) == (8.0, 1.0)
     assert tuple(pts[ids[0]].tolist()) == (8.0, 1.0)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_range_visits_equal_unordered_knn_with_unfillable_list(seed):
+    """A ball query is the unordered kNN traversal whose list never fills
+    (k > N): the cull radius stays r^2, so both process the same nodes."""
+    g = np.random.default_rng(900 + seed)
+    N, D = int(g.integers(1, 120)), int(g.integers(1, 4))
+    pts = g.random((N, D)).astype(np.float32)
+    if seed % 2:
+        pts = g.integers(0, 4, size=(N, D)).astype(np.float32)
+    pid = oracle.build(pts)
+    qs = (g.random((30, D)) * 1.2 - 0.1).astype(np.float32)
+    for r in (0.0, 0.15, 0.5, math.inf):
+        v = oracle.range_visits(pts, pid, qs, radius=r)
+        _, _, kv = oracle.knn_tree(pts, pid, qs, N + 1, r, ordered=False)
+        assert np.array_equal(v, kv), r
+    # r = inf processes every node once
+    assert np.all(oracle.range_visits(pts, pid, qs, radius=math.inf) == N)
