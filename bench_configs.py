@@ -4,6 +4,7 @@ each printed as one JSON line per measured form.  The contract line
 from __future__ import annotations
 
 import json
+import os
 import math
 import statistics
 import time
@@ -185,10 +186,20 @@ def run_config(args):
         _, woff, wids, _ = oracle.radius_brute(pts, qs[sample], r)
         ok = all(np.array_equal(np.sort(idsh[offh[q]:offh[q + 1]]), wids[woff[j]:woff[j + 1]])
                  for j, q in enumerate(sample))
+        visits = kdt.kdt_radius_count(tree, dq, r, F | kdt.KDT_RANGE_VISITS).double().sum().item()
+        # algorithmic bytes of the fill pass: query 12 B + 16 B per processed
+        # node + 8 B per hit (id, d2) + 16 B of offsets, against measured HBM
+        fill_bytes = nq * (12 + 16) + 16.0 * visits + 8.0 * total
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
         _emit(config=f"range: gmm N=2^24, Q=2^22 (90% mixture, 10% uniform), ball r={r}", form="ball count / offsets / fill",
               queries_per_s=nq / ((cnt_ms + off_ms + fill_ms) / 1e3), hits=int(total), hits_per_query=total / nq,
               hits_per_s=total / ((cnt_ms + off_ms + fill_ms) / 1e3), count_ms=cnt_ms, offsets_ms=off_ms,
-              fill_ms=fill_ms, oracle_sample_sets_equal=ok)
+              fill_ms=fill_ms, visits_per_query=visits / nq,
+              roofline_fill={"bound": "hbm", "achieved": fill_bytes / (fill_ms / 1e3) / 1e9, "peak": hbm,
+                             "unit": "GB/s", "frac": fill_bytes / (fill_ms / 1e3) / 1e9 / hbm,
+                             "bytes_per_query": fill_bytes / nq},
+              oracle_sample_sets_equal=ok)
         lo, hi = (dq - r).contiguous(), (dq + r).contiguous()
         bc_ms = timeit(lambda: kdt.kdt_box_count(tree, lo, hi, F), 3)
         bcounts = kdt.kdt_box_count(tree, lo, hi, F)

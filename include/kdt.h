@@ -166,7 +166,8 @@ int kdt_knn_visits(const kdt_tree *tree, const float *d_queries, int64_t Q, int 
  * writes query q's point ids (and, for balls, squared distances if d_d2 is not
  * NULL) to [offsets[q], offsets[q+1]) in traversal order, the same on every
  * call.  flags: 0 or KDT_MORTON (queries run in Morton order; results are the
- * same); any other bit is KDT_EINVAL.  A fill whose hits do not match its
+ * same), plus KDT_RANGE_VISITS for the count calls; any other bit is
+ * KDT_EINVAL.  A fill whose hits do not match its
  * offsets writes nothing outside the query's slice and is reported by
  * kdt_status.  Buffers are the caller's; nothing is kept after the call. */
 int kdt_radius_count(const kdt_tree *tree, const float *d_queries, int64_t Q, float radius, int flags,
@@ -177,6 +178,11 @@ int kdt_box_count(const kdt_tree *tree, const float *d_lo, const float *d_hi, in
                   int32_t *d_counts, void *stream);
 int kdt_box_fill(const kdt_tree *tree, const float *d_lo, const float *d_hi, int64_t Q, int flags,
                  const int64_t *d_offsets, int32_t *d_ids, void *stream);
+/* flags bit for kdt_radius_count / kdt_box_count only: write each query's
+ * number of processed nodes (first visits of the traversal) instead of its
+ * number of hits (the per-query work, for measurement). */
+#define KDT_RANGE_VISITS 0x200
+
 /* Exclusive prefix sum of counts into d_offsets int64 [Q+1]; if h_total is not
  * NULL the stream is synchronised and *h_total receives offsets[Q]. */
 int kdt_offsets(const int32_t *d_counts, int64_t Q, int64_t *d_offsets, int64_t *h_total, void *stream);

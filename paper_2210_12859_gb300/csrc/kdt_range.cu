@@ -47,6 +47,7 @@ struct RangeArgs {
     int C;
     int mode;              // KDT_REDUCE_*
     float *out;            // [Q][C] (ACT_REDUCE)
+    bool count_visits;     // ACT_COUNT: count processed nodes instead of hits
     int *err;
     unsigned long long *counter;
 };
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
     float acc[KDT_PAYLOAD_MAX_C];
     int curr = 0, prev = -1, dim = 0;
     uint32_t steps = 0;
-    int64_t count = 0, base = 0, limit = 0;
+    int64_t count = 0, base = 0, limit = 0, visits = 0;
     const uint32_t cap = 3u * (uint32_t)a.N + 3u;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                 dim = 0;
                 steps = 0;
                 count = 0;
+                visits = 0;
                 if (ACT == ACT_FILL) {
                     base = a.offsets[qi];
                     limit = a.offsets[qi + 1] - base;
@@ -130,6 +132,8 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
             const NodeVal<LAYOUT> nd = fetch<LAYOUT, false>(a.nodes, nullptr, 0, curr);
             const bool from_parent = prev < curr;
             if (from_parent) {
+                if (ACT == ACT_COUNT)
+                    ++visits;
                 bool hit;
                 float d2 = 0.f;
                 if constexpr (KIND == 0) {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                 atomicOr(a.err, ERR_RANGE);
         } else {
             if (a.counts)
-                a.counts[qi] = (int32_t)count;
+                a.counts[qi] = (int32_t)(ACT == ACT_COUNT && a.count_visits ? visits : count);
             if (ACT == ACT_REDUCE) {
 #pragma unroll
                 for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
@@ -325,8 +329,9 @@ int check_range(const kdt_tree *t, int64_t Q, const void *a, const void *b, bool
         return set_error(KDT_EINVAL, "Q must be in [0, 2^32)");
     if (Q > 0 && (!a || (need_b && !b)))
         return set_error(KDT_EINVAL, "NULL query pointer");
-    if (flags & ~KDT_MORTON)
-        return set_error(KDT_EINVAL, "range queries take no flag but KDT_MORTON (got %#x)", flags);
+    if (flags & ~(KDT_MORTON | KDT_RANGE_VISITS))
+        return set_error(KDT_EINVAL, "range queries take no flag but KDT_MORTON and KDT_RANGE_VISITS (got %#x)",
+                         flags);
     return KDT_OK;
 }
 
@@ -365,6 +370,7 @@ int kdt_radius_count(const kdt_tree *t, const float *d_q, int64_t Q, float radiu
     a.Q = Q;
     a.r2 = radius * radius;
     a.counts = d_counts;
+    a.count_visits = flags & KDT_RANGE_VISITS;
     return run_range(t, 0, ACT_COUNT, flags, a, (cudaStream_t)stream);
 }
 
@@ -372,6 +378,8 @@ int kdt_radius_fill(const kdt_tree *t, const float *d_q, int64_t Q, float radius
                     int32_t *d_ids, float *d_d2, void *stream)
 {
     KDT_TRY(check_range(t, Q, d_q, nullptr, false, flags));
+    if (flags & KDT_RANGE_VISITS)
+        return set_error(KDT_EINVAL, "KDT_RANGE_VISITS applies to the count calls only");
     KDT_TRY(check_radius(radius));
     if (Q > 0 && (!d_offsets || !d_ids))
         return set_error(KDT_EINVAL, "NULL offsets / ids");
@@ -400,6 +408,7 @@ int kdt_box_count(const kdt_tree *t, const float *d_lo, const float *d_hi, int64
     a.b = d_hi;
     a.Q = Q;
     a.counts = d_counts;
+    a.count_visits = flags & KDT_RANGE_VISITS;
     return run_range(t, 1, ACT_COUNT, flags, a, (cudaStream_t)stream);
 }
 
@@ -407,6 +416,8 @@ int kdt_box_fill(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_
                  const int64_t *d_offsets, int32_t *d_ids, void *stream)
 {
     KDT_TRY(check_range(t, Q, d_lo, d_hi, true, flags));
+    if (flags & KDT_RANGE_VISITS)
+        return set_error(KDT_EINVAL, "KDT_RANGE_VISITS applies to the count calls only");
     if (Q > 0 && (!d_offsets || !d_ids))
         return set_error(KDT_EINVAL, "NULL offsets / ids");
     if (Q == 0)
@@ -477,6 +488,8 @@ int kdt_radius_reduce(const kdt_tree *t, const float *d_q, int64_t Q, float radi
                       int32_t *d_counts, void *stream)
 {
     KDT_TRY(check_range(t, Q, d_q, nullptr, false, flags));
+    if (flags & KDT_RANGE_VISITS)
+        return set_error(KDT_EINVAL, "KDT_RANGE_VISITS applies to the count calls only");
     KDT_TRY(check_radius(radius));
     if (mode < KDT_REDUCE_SUM || mode > KDT_REDUCE_DENSITY)
         return set_error(KDT_EINVAL, "unknown reduction mode %d", mode);

@@ -42,6 +42,7 @@ KDT_COST_ORDER = 0x20
 KDT_PLAIN_STEP = 0x40
 KDT_CLOSE_FIRST = 0x80
 KDT_STACK = 0x100
+KDT_RANGE_VISITS = 0x200
 KDT_BUILD_ASYNC = 0x1
 KDT_REDUCE_SUM, KDT_REDUCE_MEAN, KDT_REDUCE_DENSITY = 0, 1, 2
 KDT_PAYLOAD_MAX_C = 8

@@ -213,3 +213,24 @@ def test_full_size_sampled(kdt):
         assert np.array_equal(ids[a:b][order], want_ids[wa:wb]), q
         assert np.array_equal(bits(d2[a:b][order]), bits(want_d2[wa:wb])), q
     assert off[-1] > len(qs)
+
+
+@pytest.mark.parametrize("D,N,widest", [(3, 20000, 0), (2, 5000, 1), (4, 8000, 0), (6, 3000, 0)])
+def test_range_visits_equal_oracle(kdt, D, N, widest):
+    """KDT_RANGE_VISITS: the count calls report processed nodes, equal to the
+    oracle's range traversal, for balls and boxes."""
+    g = np.random.default_rng(D + N)
+    pts = synth.uniform(N, D, seed=D * 3 + N)
+    qs = (g.random((200, D)) * 1.2 - 0.1).astype(np.float32)
+    r = radius_for(pts, 15)
+    tree = build(kdt, pts, widest)
+    pid, dims = oracle_tree(pts, widest)
+    for flags in (kdt.KDT_RANGE_VISITS, kdt.KDT_RANGE_VISITS | kdt.KDT_MORTON):
+        v = kdt.kdt_radius_count(tree, cu(qs), r, flags).cpu().numpy()
+        assert np.array_equal(v, oracle.range_visits(pts, pid, qs, radius=r, node_dim=dims))
+        lo, hi = qs - np.float32(r), qs + np.float32(r)
+        vb = kdt.kdt_box_count(tree, cu(lo), cu(hi), flags).cpu().numpy()
+        assert np.array_equal(vb, oracle.range_visits(pts, pid, lo, hi, node_dim=dims))
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_radius_fill(tree, cu(qs), r, torch.zeros(201, dtype=torch.int64, device="cuda"), 0,
+                            flags=kdt.KDT_RANGE_VISITS)
