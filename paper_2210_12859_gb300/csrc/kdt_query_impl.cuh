@@ -11,12 +11,12 @@ namespace kdt {
 // runs queries back to back: when its query ends it claims the next one
 // (persistent threads with replacement), so a lane never idles while a slow
 // neighbour in its warp is still traversing, until the work runs out.
-// Register-list kernels with k <= 8 are built for 6 resident blocks per SM
-// (at most 85 registers a thread): the depth-2 kernel otherwise takes 82
-// registers and only 5 blocks fit (measured: 5.4 % faster on the clustered
-// 2^24 workload, no spills; a bound of 8 blocks spills and is slower; k = 16
-// lists would spill under the bound of 6).  The learned radius's bounded
-// kernel runs best at 7 blocks (a small spill; measured 2.7 % faster than 6).
+// Register-list kernels with k <= 8 are built for at least 6 resident blocks
+// per SM (at most 85 registers a thread; without the bound the depth-2 kernel
+// once took 82 registers and 5 blocks fit); the learned radius's bounded
+// kernel for 7.  With the bottom subtrees handled as scalar keys the depth-2
+// kernel needs 64 registers (8 blocks) and the bounded one 72, both without
+// spills, so the bounds now only guard against regressions.
 template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
                                   K <= 8 ? (MODE == MODE_BOUNDED ? 7 : 6) : 1)
@@ -68,6 +68,10 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         bool fin = false;
         for (int s = 0; s < a.claim_steps && !fin; ++s)
             fin = w.template step<STAGE>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits, overflow);
+        if (!fin && w.steps > 3u * (uint32_t)a.N + 3u) {
+            overflow = true;
+            fin = true;
+        }
         if (!fin)
             continue;
         // query finished
@@ -165,6 +169,10 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         bool fin = false;
         for (int s = 0; s < a.claim_steps && !fin; ++s)
             fin = w.template step<false>(nodes, ids, nullptr, 0, N, a.D, q, list, visits, overflow);
+        if (!fin && w.steps > 3u * (uint32_t)N + 3u) {
+            overflow = true;
+            fin = true;
+        }
         if (!fin)
             continue;
         if (overflow)

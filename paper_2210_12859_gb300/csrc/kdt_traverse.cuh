@@ -327,18 +327,62 @@ struct Walker {
         }
     }
 
-    // one step; returns true when the traversal has finished (or exceeded
-    // its step bound, reported through *overflow).  STAGE: the first
+    // Whole bottom subtrees: the keys (d2, id) of all their nodes and the
+    // children's split offsets are computed first, from the values loaded at
+    // once; the machine's order is then followed on these scalars (a node's
+    // key is offered to the list when the machine would process it), which
+    // needs far fewer registers and selects than carrying whole node values.
+    __device__ __forceinline__ static unsigned long long node_key(const NodeVal<LAYOUT> &nd, int n,
+                                                                   const int32_t *__restrict__ ids,
+                                                                   const float (&q)[NC])
+    {
+        const float d2 = dist2<NC>(nd.c, q);
+        const uint32_t id = LAYOUT == 0 ? nd.id : (LAYOUT == 3 ? (nd.id & NODE_ID_MASK) : (uint32_t)__ldg(ids + n));
+        return pack_key(d2, id);
+    }
+    template <class List>
+    __device__ __forceinline__ static void offer(List &list, unsigned long long k)
+    {
+        if (k < list.worst())
+            list.insert(k);
+    }
+    template <class List>
+    __device__ __forceinline__ static void eager_leaf_pair(float sdc, float sdc2, int lcc, unsigned long long ka,
+                                                           unsigned long long kb, int N, List &list, int &visits)
+    {
+        const bool rf = sdc > 0.f;
+        const bool rcc_ok = lcc + 1 < N;
+        if (!rf || rcc_ok) {
+            ++visits;
+            offer(list, rf ? kb : ka);
+        }
+        if ((rf || rcc_ok) && sdc2 <= list.cull()) {
+            ++visits;
+            offer(list, rf ? ka : kb);
+        }
+    }
+    template <class List>
+    __device__ __forceinline__ static void eager_leaf_parent(int c, unsigned long long kc, float sdc,
+                                                             unsigned long long ka, unsigned long long kb, int N,
+                                                             List &list, int &visits)
+    {
+        ++visits;
+        offer(list, kc);
+        const int lcc = 2 * c + 1;
+        if (lcc < N)
+            eager_leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ka, kb, N, list, visits);
+    }
+
+    // one step; returns true when the traversal has finished.  The caller
+    // bounds a traversal by checking `steps` against 3N + 3 once per claim
+    // round (and reports an overrun through *overflow).  STAGE: the first
     // `staged` nodes are read from shared memory.
     template <bool STAGE, class List>
     __device__ __forceinline__ bool step(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
                                          const float4 *s_nodes, int staged, int N, int D, const float (&q)[NC],
                                          List &list, int &visits, bool &overflow)
     {
-        if (++steps > 3u * (uint32_t)N + 3u) {
-            overflow = true;
-            return true;
-        }
+        ++steps;
         const NodeVal<LAYOUT> nd = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, curr);
         const bool from_parent = prev < curr;
         if (from_parent) {
@@ -370,12 +414,20 @@ struct Walker {
             const bool rc_ok = rc < N;
             if constexpr (ORDERED) {
                 const bool right_first = sd > 0.f;
+                const unsigned long long k_c0 = node_key(c0, lc, ids, q), k_c1 = node_key(c1, min(rc, last), ids, q);
+                const unsigned long long k_g00 = node_key(g00, g0, ids, q);
+                const unsigned long long k_g01 = node_key(g01, min(g0 + 1, last), ids, q);
+                const unsigned long long k_g10 = node_key(g10, min(g0 + 2, last), ids, q);
+                const unsigned long long k_g11 = node_key(g11, min(g0 + 3, last), ids, q);
+                const int d0 = split_dim_of<LAYOUT>(c0, dim1), d1 = split_dim_of<LAYOUT>(c1, dim1);
+                const float sdc0 = __fsub_rn(select_dim<NC>(q, d0), select_dim<NC>(c0.c, d0));
+                const float sdc1 = __fsub_rn(select_dim<NC>(q, d1), select_dim<NC>(c1.c, d1));
                 if (!right_first || rc_ok)
-                    leaf_parent(right_first ? rc : lc, dim1, pick(right_first, c1, c0), pick(right_first, g10, g00),
-                                pick(right_first, g11, g01), ids, N, q, list, visits);
+                    eager_leaf_parent(right_first ? rc : lc, right_first ? k_c1 : k_c0, right_first ? sdc1 : sdc0,
+                                      right_first ? k_g10 : k_g00, right_first ? k_g11 : k_g01, N, list, visits);
                 if ((right_first || rc_ok) && sd2 <= list.cull())
-                    leaf_parent(right_first ? lc : rc, dim1, pick(right_first, c0, c1), pick(right_first, g00, g10),
-                                pick(right_first, g01, g11), ids, N, q, list, visits);
+                    eager_leaf_parent(right_first ? lc : rc, right_first ? k_c0 : k_c1, right_first ? sdc0 : sdc1,
+                                      right_first ? k_g00 : k_g10, right_first ? k_g01 : k_g11, N, list, visits);
             } else {
                 if (sd <= 0.f || sd2 <= list.cull())
                     leaf_parent(lc, dim1, c0, g00, g01, ids, N, q, list, visits);
@@ -388,7 +440,11 @@ struct Walker {
             // loads first
             const NodeVal<LAYOUT> a = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
             const NodeVal<LAYOUT> b = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(rc, N - 1));
-            leaf_pair(sd, sd2, lc, a, b, ids, N, q, list, visits);
+            if constexpr (ORDERED)
+                eager_leaf_pair(sd, sd2, lc, node_key(a, lc, ids, q), node_key(b, min(rc, N - 1), ids, q), N, list,
+                                visits);
+            else
+                leaf_pair(sd, sd2, lc, a, b, ids, N, q, list, visits);
             next = parent;
         } else {
             const float cull = list.cull();
@@ -427,21 +483,6 @@ struct Walker {
     }
 };
 
-// Whole traversal of one query; returns the number of processed nodes (first
-// visits), or -1 if the step bound was exceeded (impossible for a valid tree).
-template <int LAYOUT, bool ORDERED, class List>
-__device__ __forceinline__ int traverse(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
-                                        const float4 *s_nodes, int staged, int N, int D,
-                                        const float (&q)[LayoutTraits<LAYOUT>::NC], List &list)
-{
-    Walker<LAYOUT, ORDERED> w;
-    w.start();
-    int visits = 0;
-    bool overflow = false;
-    while (!w.template step<true>(nodes, ids, s_nodes, staged, N, D, q, list, visits, overflow)) {
-    }
-    return overflow ? -1 : visits;
-}
 
 template <int LAYOUT>
 __device__ __forceinline__ void load_query(const float *__restrict__ queries, int64_t qi, int D,
