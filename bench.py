@@ -263,7 +263,7 @@ def main():
     # measured on 2^20 of the queries before anything is timed
     if not args.no_tune:
         kdt.kdt_autotune(tree, dq, K_NN, flags)
-    tuned = dict(zip(("stage_levels", "claim_steps", "inline_depth"), kdt.kdt_tuned_params(tree, K_NN)))
+    tuned = dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"), kdt.kdt_tuned_params(tree, K_NN)))
 
     def step():
         kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC)

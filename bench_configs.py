@@ -86,7 +86,7 @@ def run_config(args):
             v = kdt.kdt_knn_visits(tree, dq, 16, flags=kdt.KDT_MORTON).double().mean().item()
             _emit(config="dims N=Q=2^22 kNN k=16 ordered", form=name, query_qps=n / (ms / 1e3), query_ms=ms,
                   default_launch_query_ms=default_ms,
-                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth"), tuned)),
+                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"), tuned)),
                   build_ms=build_ms, visits_per_query=v,
                   bit_exact_sample=_exact(oracle, pts, qs, gi.cpu().numpy(), gd.cpu().numpy(), 16))
             del tree
@@ -148,12 +148,13 @@ def run_config(args):
             ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, base, out_i, out_d), 2)
             same = bool(torch.equal(out_i, ref_i) and torch.equal(out_d.view(torch.int32), ref_d.view(torch.int32)))
             _emit(config=cname, form="production, autotuned launch", query_qps=len(q_) / (ms / 1e3), query_ms=ms,
-                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth"), tuned)),
+                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"), tuned)),
                   identical_to_production=same)
             # the forms below run at the untuned defaults
             kdt.kdt_set_stage_levels(tree, 0)
             kdt.kdt_set_claim_steps(tree, 32 if k <= 1 else 64)
             kdt.kdt_set_inline_depth(tree, 2)
+            kdt.kdt_set_light_run(tree, 1)
             for name, fl in forms:
                 ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, base | fl, out_i, out_d), 2)
                 same = bool(torch.equal(out_i, ref_i) and torch.equal(out_d.view(torch.int32), ref_d.view(torch.int32)))
@@ -237,7 +238,7 @@ def run_config(args):
         out_d = torch.empty((Q, 8), dtype=torch.float32, device="cuda")
         res = {}
         # the library's batched-launch tuner (block size, claim steps), measured first
-        th, cs, il, _ = kdt.kdt_forest_autotune(forest, dq, c.qoffsets, 8, math.inf, kdt.KDT_MORTON, out_i, out_d)
+        th, cs, il, lr, _ = kdt.kdt_forest_autotune(forest, dq, c.qoffsets, 8, math.inf, kdt.KDT_MORTON, out_i, out_d)
         for name, fl in (("one persistent graph launch, Morton order", kdt.KDT_MORTON),
                          ("one persistent graph launch", 0),
                          ("one launch per tree", kdt.KDT_PER_TREE)):
@@ -257,6 +258,6 @@ def run_config(args):
         for name, (ms, _, _) in res.items():
             _emit(config=f"batched: 4096 clouds, {int(c.offsets[-1])} points, {Q} queries, kNN k=8", form=name,
                   query_qps=Q / (ms / 1e3), query_ms=ms, forest_build_s=build_s, identical_forms=same,
-                  launch_autotuned={"threads": th, "claim_steps": cs, "inline_depth": il},
+                  launch_autotuned={"threads": th, "claim_steps": cs, "inline_depth": il, "light_run": lr},
                   bit_exact_sample=ok)
         return

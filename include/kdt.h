@@ -342,20 +342,22 @@ int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids,
 
 /* Launch parameters of the batched query: threads per block (0 = 128, else a
  * multiple of 32 up to 128), traversal steps between two claim rounds of a
- * warp (0 = the default for k, 32 for k = 1 and 64 otherwise; up to 256) and
- * the inline depth (0 = default 2, or 1; see kdt_set_inline_depth).
+ * warp (0 = the default for k, 32 for k = 1 and 64 otherwise; up to 256), the
+ * inline depth (0 = default 2, or 1; see kdt_set_inline_depth) and the light
+ * run (0 = default 1, up to 64; see kdt_set_light_run).
  * Shared-memory staging does not apply to forests: the lanes of a warp walk
  * different trees.  The next kdt_knn_batched re-captures its graph. */
-int kdt_forest_set_launch(kdt_forest *forest, int threads, int claim_steps, int inline_depth);
+int kdt_forest_set_launch(kdt_forest *forest, int threads, int claim_steps, int inline_depth, int light_run);
 
 /* Time the batched query (kdt_knn_batched with these arguments, graph
  * included; it writes d_ids / d_d2 like that call) for inline depths {2, 1},
- * block sizes {128, 64}, then claim steps {16, 32, 64, 128}, one warm-up and
+ * light runs {1, 4, 8}, block sizes {128, 64}, then claim steps {16, 32, 64,
+ * 128}, one warm-up and
  * one timed run each, and keep the fastest on the forest (a candidate must win
  * by 2 %).  Synchronous.  The out pointers may be NULL. */
 int kdt_forest_autotune(kdt_forest *forest, const float *d_queries, const int64_t *h_query_offsets, int k,
                         float max_radius, int flags, int32_t *d_ids, float *d_d2, int *best_threads,
-                        int *best_claim, int *best_inline, float *best_ms, void *stream);
+                        int *best_claim, int *best_inline, int *best_light, float *best_ms, void *stream);
 
 /* Release a forest and its device memory (synchronises the device first). */
 void kdt_forest_free(kdt_forest *forest);
@@ -385,15 +387,26 @@ int kdt_set_claim_steps(kdt_tree *tree, int steps);
  * processed nodes are the same for every depth. */
 int kdt_set_inline_depth(kdt_tree *tree, int depth);
 
+/* Traversal steps a lane may take in one call while they are light (a heavy
+ * step enters a node whose bottom subtree is processed whole): with values
+ * above 1 the heavy steps of a warp's lanes tend to start their calls
+ * together.  1 (default) suits long queries; 4 or 8 pay for short ones.  -1
+ * restores the tuned or default value.  Range 1..64.  Results and processed
+ * nodes are the same for every value. */
+int kdt_set_light_run(kdt_tree *tree, int steps);
+
 /* The launch parameters kdt_knn uses for this tree and k: set on the tree,
  * else tuned for its shape (kdt_autotune / kdt_tuning_load), else defaults
- * (no staging, 32 claim steps for k = 1 and 64 otherwise, inline depth 2). */
-int kdt_tuned_params(const kdt_tree *tree, int k, int *stage_levels, int *claim_steps, int *inline_depth);
+ * (no staging, 32 claim steps for k = 1 and 64 otherwise, inline depth 2,
+ * light run 1).  Any out pointer may be NULL. */
+int kdt_tuned_params(const kdt_tree *tree, int k, int *stage_levels, int *claim_steps, int *inline_depth,
+                     int *light_run);
 
 /* Time the plain traversal of up to 2^20 of the given queries and remember
  * the fastest launch parameters for this tree's shape (GPU name, D, k bucket,
- * floor(log2 N)): a coordinate search over the inline depth {2, 1, 0}, then
- * the claim steps {16, 32, 64, 128}, then the staging depth {0, 4, 6, 8}, each
+ * floor(log2 N)): a coordinate search over the inline depth {2, 1, 0}, the
+ * light run {1, 4, 8}, then the claim steps {16, 32, 64, 128}, then the
+ * staging depth {0, 4, 6, 8}, each
  * candidate timed over two launches after a warm-up and taken only when it is
  * faster than the best so far by 2 % (staging: 5 %).  Later queries on trees of that shape use the choice unless
  * the kdt_set_* calls override.  Synchronous.  *best_levels and *best_ms (may

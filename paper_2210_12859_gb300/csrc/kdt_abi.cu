@@ -234,6 +234,7 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.counter = counter;
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.claim_steps = claim_steps_for(t, k);
+    a.light_run = light_run_for(t, k);
     a.inline_depth = inline_depth_for(t, k);
     cudaEvent_t stop;
     KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
@@ -632,6 +633,7 @@ struct ForestGraph {
     int threads = 0;           // launch parameters the graph was captured with
     int claim_steps = 0;
     int inline_depth = 0;
+    int light_run = 0;
 };
 
 int kdt_build_batched(const float *d_points, const int64_t *h_off, int T, int D, void *stream, kdt_forest **out)
@@ -725,6 +727,7 @@ static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64
     a.threads = f->threads;
     a.claim_steps = f->claim_steps > 0 ? f->claim_steps : default_claim_steps_k(k);
     a.inline_depth = f->inline_depth == 1 ? 1 : 2;
+    a.light_run = f->light_run > 0 ? f->light_run : 1;
     return launch_query(layout_of(f->f.D), a, !(flags & KDT_UNORDERED), 0, true, s);
 }
 
@@ -800,7 +803,7 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
     }
     const bool same = g->exec && g->q == d_q && g->ids == d_ids && g->d2 == d_d2 && g->k == k && g->r2 == r2 &&
                       g->flags == flags && g->threads == f->threads && g->claim_steps == f->claim_steps &&
-                      g->inline_depth == f->inline_depth &&
+                      g->inline_depth == f->inline_depth && g->light_run == f->light_run &&
                       g->qoff.size() == (size_t)T + 1 &&
                       std::equal(g->qoff.begin(), g->qoff.end(), h_qoff);
     if (!same) {
@@ -826,6 +829,7 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
         g->threads = f->threads;
         g->claim_steps = f->claim_steps;
         g->inline_depth = f->inline_depth;
+        g->light_run = f->light_run;
         g->qoff.assign(h_qoff, h_qoff + T + 1);
     }
     Carve c{(char *)g->scratch};
@@ -857,12 +861,14 @@ int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int 
     return KDT_OK;
 }
 
-int kdt_forest_set_launch(kdt_forest *f, int threads, int claim_steps, int inline_depth)
+int kdt_forest_set_launch(kdt_forest *f, int threads, int claim_steps, int inline_depth, int light_run)
 {
     if (!f)
         return set_error(KDT_EINVAL, "forest is NULL");
     if (inline_depth < 0 || inline_depth > 2)
         return set_error(KDT_EINVAL, "inline_depth must be 0 (default), 1 or 2 (got %d)", inline_depth);
+    if (light_run < 0 || light_run > 64)
+        return set_error(KDT_EINVAL, "light_run must be in [0, 64] (got %d)", light_run);
     if (threads < 0 || threads > REG_THREADS || threads % 32 != 0)
         return set_error(KDT_EINVAL, "threads must be 0 or a multiple of 32 up to %d (got %d)", REG_THREADS, threads);
     if (claim_steps < 0 || claim_steps > 256)
@@ -870,16 +876,18 @@ int kdt_forest_set_launch(kdt_forest *f, int threads, int claim_steps, int inlin
     f->threads = threads;
     f->claim_steps = claim_steps;
     f->inline_depth = inline_depth;
+    f->light_run = light_run;
     return KDT_OK;
 }
 
-// Coordinate search over the batched launch: inline depth {2, 1}, block size
-// {128, 64}, then claim steps {16, 32, 64, 128}; each candidate is the whole
+// Coordinate search over the batched launch: inline depth {2, 1}, light run
+// {1, 4, 8}, block size {128, 64}, then claim steps {16, 32, 64, 128}; each
+// candidate is the whole
 // batched query (graph included), one warm-up and one timed run, and is taken
 // when it is faster than the best so far by 2 %.
 int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int k, float max_radius, int flags,
                         int32_t *d_ids, float *d_d2, int *best_threads, int *best_claim, int *best_inline,
-                        float *best_ms, void *stream)
+                        int *best_light, float *best_ms, void *stream)
 {
     if (!f || !h_qoff || !d_q || !d_ids || !d_d2)
         return set_error(KDT_EINVAL, "NULL forest, query, offset or output pointer");
@@ -889,15 +897,16 @@ int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, 
     cudaEvent_t e0, e1;
     KDT_CUDA(cudaEventCreate(&e0));
     KDT_CUDA(cudaEventCreate(&e1));
-    const int saved_t = f->threads, saved_c = f->claim_steps, saved_i = f->inline_depth;
-    int bt = 0, bc = 0, bi = 2, rc = KDT_OK;
+    const int saved_t = f->threads, saved_c = f->claim_steps, saved_i = f->inline_depth, saved_l = f->light_run;
+    int bt = 0, bc = 0, bi = 2, bl = 1, rc = KDT_OK;
     float best = 3.4e38f;
-    auto trial = [&](int th, int cs, int inl) {
+    auto trial = [&](int th, int cs, int inl, int lr) {
         if (rc != KDT_OK)
             return;
         f->threads = th;
         f->claim_steps = cs;
         f->inline_depth = inl;
+        f->light_run = lr;
         rc = kdt_knn_batched(f, d_q, h_qoff, k, max_radius, flags, d_ids, d_d2, stream);
         float ms = 0.f;
         if (rc == KDT_OK && cudaEventRecord(e0, s) != cudaSuccess)
@@ -912,29 +921,37 @@ int kdt_forest_autotune(kdt_forest *f, const float *d_q, const int64_t *h_qoff, 
             bt = th;
             bc = cs;
             bi = inl;
+            bl = lr;
         }
     };
-    trial(0, 0, 2);
-    trial(0, 0, 1);
+    trial(0, 0, 2, 1);
+    trial(0, 0, 1, 1);
     const int i_best = bi;
-    trial(64, 0, i_best);
+    trial(0, 0, i_best, 4);
+    trial(0, 0, i_best, 8);
+    const int l_best = bl;
+    trial(64, 0, i_best, l_best);
     const int t_best = bt;
     for (int cs : {16, 32, 64, 128})
         if (cs != default_claim_steps_k(k))
-            trial(t_best, cs, i_best);
+            trial(t_best, cs, i_best, l_best);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != KDT_OK) {
         f->threads = saved_t;
         f->claim_steps = saved_c;
         f->inline_depth = saved_i;
+        f->light_run = saved_l;
         return rc;
     }
     f->threads = bt;
     f->claim_steps = bc;
     f->inline_depth = bi;
+    f->light_run = bl;
     if (best_inline)
         *best_inline = bi;
+    if (best_light)
+        *best_light = bl;
     if (best_threads)
         *best_threads = bt ? bt : REG_THREADS;
     if (best_claim)

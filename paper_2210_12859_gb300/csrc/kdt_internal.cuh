@@ -265,6 +265,8 @@ struct kdt_tree {
     // depth of the bottom subtrees a traversal step processes whole (1 or 2;
     // -1: tuned or default)
     int inline_depth = -1;
+    // steps a lane may take per call while they are light (-1: tuned or 1)
+    int light_run = -1;
     // per-point payload in node order [N][payload_c] and node_of[input index]
     // (kdt_tree_set_payload; dropped by a rebuild)
     float *payload = nullptr;
@@ -286,6 +288,7 @@ struct kdt_forest {
     int threads = 0;               // block size of the batched kernel (0: default 128)
     int claim_steps = 0;           // traversal steps between claim rounds (0: default for k)
     int inline_depth = 0;          // bottom-subtree depth per step (0: default 2)
+    int light_run = 0;             // light steps per call (0: default 1)
 };
 
 // allocate an empty tree object with device arrays for N nodes of dimension D
@@ -299,6 +302,7 @@ int claim_steps_for(const kdt_tree *t, int k);
 // default claim steps for k neighbours (no tuning)
 int default_claim_steps_k(int k);
 int inline_depth_for(const kdt_tree *t, int k);
+int light_run_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,
 // D <= 3), stored in the node (layout 3); else level mod D

@@ -29,6 +29,7 @@ struct QueryArgs {
     int claim_steps = STEPS_PER_CLAIM; // traversal steps a lane takes between two claim rounds
     int inline_depth = 2;              // bottom-subtree depth processed within one step (1 or 2)
     int threads = 0;                   // block size of the forest kernel (0: the kernel's default)
+    int light_run = 1;                 // steps a lane may take per call while they are light
     unsigned long long *counter = nullptr;  // dynamic work counter, zeroed before launch
     // batched forests
     int T = 1;

@@ -17,7 +17,7 @@ namespace kdt {
 // kernel for 7.  With the bottom subtrees handled as scalar keys the depth-2
 // kernel needs 64 registers (8 blocks) and the bounded one 72, both without
 // spills, so the bounds now only guard against regressions.
-template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE>
+template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE, bool RUNS = false>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
                                   K <= 8 ? (MODE == MODE_BOUNDED ? 7 : 6) : 1)
     knn_kernel(const QueryArgs a)
@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         bool overflow = false;
         bool fin = false;
         for (int s = 0; s < a.claim_steps && !fin; ++s)
-            fin = w.template step<STAGE>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits, overflow);
+            fin = w.template step<STAGE, RUNS>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits,
+                                               overflow, a.light_run);
         if (!fin && w.steps > 3u * (uint32_t)a.N + 3u) {
             overflow = true;
             fin = true;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
 // Forest: a lane's query finds its tree by binary search over the query
 // offsets; no shared-memory staging (neighbouring lanes may walk different
 // trees).  Same lane-refill scheme as knn_kernel.
-template <int LAYOUT, int K, bool ORDERED, int INLINE>
+template <int LAYOUT, int K, bool ORDERED, int INLINE, bool RUNS = false>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
     knn_forest_kernel(const QueryArgs a)
 {
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS)
         bool overflow = false;
         bool fin = false;
         for (int s = 0; s < a.claim_steps && !fin; ++s)
-            fin = w.template step<false>(nodes, ids, nullptr, 0, N, a.D, q, list, visits, overflow);
+            fin = w.template step<false, RUNS>(nodes, ids, nullptr, 0, N, a.D, q, list, visits, overflow, a.light_run);
         if (!fin && w.steps > 3u * (uint32_t)N + 3u) {
             overflow = true;
             fin = true;
@@ -211,6 +212,17 @@ inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, 
             return set_error(KDT_EINVAL, "the learned radius path needs D <= 3");
         }
     default:
+        // light runs (tuned for short queries) have their own instantiation
+        // so that the default kernel keeps its single-step code
+        if constexpr (!STAGE) {
+            if (a.light_run > 1) {
+                if (ordered)
+                    return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, false, INLINE, true>, threads,
+                                         smem, a, s);
+                return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, false, INLINE, true>, threads, smem,
+                                     a, s);
+            }
+        }
         if (ordered)
             return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, STAGE, INLINE>, threads, smem, a, s);
         return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, STAGE, INLINE>, threads, smem, a, s);
@@ -226,14 +238,19 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
     if (batched) {
         if constexpr (LAYOUT == 3)
             return set_error(KDT_EINVAL, "forests store no per-node split dimensions");
+        const bool runs = a.light_run > 1;
         if (a.inline_depth == 1) {
-            if (ordered)
-                return launch_kernel(knn_forest_kernel<LAYOUT, K, true, 1>, threads, list_bytes, a, s);
-            return launch_kernel(knn_forest_kernel<LAYOUT, K, false, 1>, threads, list_bytes, a, s);
+            if (runs)
+                return ordered ? launch_kernel(knn_forest_kernel<LAYOUT, K, true, 1, true>, threads, list_bytes, a, s)
+                               : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 1, true>, threads, list_bytes, a, s);
+            return ordered ? launch_kernel(knn_forest_kernel<LAYOUT, K, true, 1>, threads, list_bytes, a, s)
+                           : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 1>, threads, list_bytes, a, s);
         }
-        if (ordered)
-            return launch_kernel(knn_forest_kernel<LAYOUT, K, true, 2>, threads, list_bytes, a, s);
-        return launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2>, threads, list_bytes, a, s);
+        if (runs)
+            return ordered ? launch_kernel(knn_forest_kernel<LAYOUT, K, true, 2, true>, threads, list_bytes, a, s)
+                           : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2, true>, threads, list_bytes, a, s);
+        return ordered ? launch_kernel(knn_forest_kernel<LAYOUT, K, true, 2>, threads, list_bytes, a, s)
+                       : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2>, threads, list_bytes, a, s);
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
     // staging is paired with depth-2 inlining only (both serve long queries)

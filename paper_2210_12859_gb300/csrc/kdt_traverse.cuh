@@ -373,15 +373,21 @@ struct Walker {
             eager_leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ka, kb, N, list, visits);
     }
 
-    // one step; returns true when the traversal has finished.  The caller
-    // bounds a traversal by checking `steps` against 3N + 3 once per claim
-    // round (and reports an overrun through *overflow).  STAGE: the first
-    // `staged` nodes are read from shared memory.
-    template <bool STAGE, class List>
+    // One or more steps; returns true when the traversal has finished.  With
+    // RUNS and light_run > 1 a call continues with further steps while the next one is
+    // light (not entering a node whose bottom subtree is processed whole), at
+    // most light_run steps, so the heavy steps of a warp's lanes tend to
+    // start their calls together (the same steps in the same order; pays for
+    // short queries, not for long ones: tuned).  The caller bounds a
+    // traversal by checking `steps` against 3N + 3 once per claim round (and
+    // reports an overrun through *overflow).  STAGE: the first `staged` nodes
+    // are read from shared memory.
+    template <bool STAGE, bool RUNS, class List>
     __device__ __forceinline__ bool step(const float4 *__restrict__ nodes, const int32_t *__restrict__ ids,
                                          const float4 *s_nodes, int staged, int N, int D, const float (&q)[NC],
-                                         List &list, int &visits, bool &overflow)
+                                         List &list, int &visits, bool &overflow, int light_run = 1)
     {
+      for (int g = 0;; ++g) {
         ++steps;
         const NodeVal<LAYOUT> nd = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, curr);
         const bool from_parent = prev < curr;
@@ -479,7 +485,18 @@ struct Walker {
             dim = dim + 1 == D ? 0 : dim + 1;
         prev = curr;
         curr = next;
-        return false;
+        if constexpr (!RUNS)
+            return false;
+        if (g + 1 >= light_run)
+            return false;
+        // stop before a heavy step (entering a node whose bottom subtree is
+        // processed whole), so that it starts the next call
+        const int lcn = 2 * curr + 1;
+        if (curr > prev && lcn < N &&
+            ((INLINE >= 2 && 2u * (2u * (uint32_t)lcn + 1u) + 1u >= (uint32_t)N) ||
+             (INLINE == 1 && 2 * lcn + 1 >= N)))
+            return false;
+      }
     }
 };
 

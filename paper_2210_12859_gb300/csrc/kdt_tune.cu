@@ -10,7 +10,10 @@
 //   * inline_depth: depth of the bottom subtrees one step processes whole
 //     (2 saves steps on long queries; 1 avoids the extra up-front loads that
 //     short queries rarely use; 0 selects the simplest kernel, one node per
-//     step, where it applies: ordered, k <= 16, D <= 4, no staging).
+//     step, where it applies: ordered, k <= 16, D <= 4, no staging);
+//   * light_run: steps a lane takes per call while they are light, so that
+//     the heavy steps (whole bottom subtrees) of a warp's lanes coincide
+//     (1 for long queries; 4 or 8 pay for short ones).
 // kdt_autotune measures them on the caller's queries and remembers the best
 // per shape (GPU, D, k bucket, floor(log2 N)), in memory and optionally in a
 // JSON file; without a tuning the defaults below apply.
@@ -31,6 +34,7 @@ namespace {
 
 constexpr int DEFAULT_STAGE_LEVELS = 0;
 constexpr int DEFAULT_INLINE_DEPTH = 2;
+constexpr int DEFAULT_LIGHT_RUN = 1;
 // measured on GB300: 64 steps per claim round is best for k >= 2 on every
 // workload tried, 32 for fcp
 int default_claim_steps(int k) { return k <= 1 ? 32 : 64; }
@@ -39,6 +43,7 @@ struct Tuned {
     int stage_levels;
     int claim_steps;
     int inline_depth;
+    int light_run;
 };
 
 using ShapeKey = std::tuple<std::string, int, int, int>;  // gpu, D, k bucket, log2 N
@@ -118,6 +123,14 @@ int claim_steps_for(const kdt_tree *t, int k)
     return tuned_for(t, k, &v) ? v.claim_steps : default_claim_steps(k);
 }
 
+int light_run_for(const kdt_tree *t, int k)
+{
+    if (t->light_run > 0)
+        return t->light_run;
+    Tuned v;
+    return tuned_for(t, k, &v) ? v.light_run : DEFAULT_LIGHT_RUN;
+}
+
 int inline_depth_for(const kdt_tree *t, int k)
 {
     if (t->inline_depth >= 0)
@@ -164,7 +177,18 @@ int kdt_set_inline_depth(kdt_tree *t, int depth)
     return KDT_OK;
 }
 
-int kdt_tuned_params(const kdt_tree *t, int k, int *stage_levels, int *claim_steps, int *inline_depth)
+int kdt_set_light_run(kdt_tree *t, int steps)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (steps < -1 || steps == 0 || steps > 64)
+        return set_error(KDT_EINVAL, "steps must be -1 or in [1, 64] (got %d)", steps);
+    t->light_run = steps;
+    return KDT_OK;
+}
+
+int kdt_tuned_params(const kdt_tree *t, int k, int *stage_levels, int *claim_steps, int *inline_depth,
+                     int *light_run)
 {
     if (!t || k < 1 || k > 64)
         return set_error(KDT_EINVAL, "bad tree or k");
@@ -174,10 +198,12 @@ int kdt_tuned_params(const kdt_tree *t, int k, int *stage_levels, int *claim_ste
         *claim_steps = claim_steps_for(t, k);
     if (inline_depth)
         *inline_depth = inline_depth_for(t, k);
+    if (light_run)
+        *light_run = light_run_for(t, k);
     return KDT_OK;
 }
 
-// Coordinate search: inline depth, then claim steps, then staging depth, each
+// Coordinate search: inline depth, light run, then claim steps, then staging depth, each
 // over its candidates with the others at their best so far; every candidate is
 // timed over two launches on up to 2^20 of the queries after one warm-up, and
 // replaces the best so far only if it is faster by a margin (2 %; 5 % for
@@ -200,13 +226,15 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     KDT_CUDA(cudaEventCreate(&e0));
     KDT_CUDA(cudaEventCreate(&e1));
     const int saved_stage = t->stage_levels, saved_claim = t->claim_steps, saved_inline = t->inline_depth;
-    Tuned best{DEFAULT_STAGE_LEVELS, default_claim_steps(k), DEFAULT_INLINE_DEPTH};
+    const int saved_light = t->light_run;
+    Tuned best{DEFAULT_STAGE_LEVELS, default_claim_steps(k), DEFAULT_INLINE_DEPTH, DEFAULT_LIGHT_RUN};
     float best_t = 3.4e38f;
     int rc = KDT_OK;
     auto measure = [&](const Tuned &c, float *out) {
         t->stage_levels = c.stage_levels;
         t->claim_steps = c.claim_steps;
         t->inline_depth = c.inline_depth;
+        t->light_run = c.light_run;
         for (int rep = 0; rep < 3 && rc == KDT_OK; ++rep) {
             rc = run_query(t, d_q, n, k, INFINITY, flags & ~KDT_NO_STAGE, MODE_RESULTS, ids, d2, nullptr, s);
             if (rc == KDT_OK && rep == 0)
@@ -234,6 +262,12 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
         if (rc == KDT_OK && (d > 0 || simple_ok))
             consider(c, 0.02f);
     }
+    for (int lr : {4, 8}) {
+        Tuned c = best;
+        c.light_run = lr;
+        if (rc == KDT_OK && best.inline_depth > 0)
+            consider(c, 0.02f);
+    }
     for (int cs : {16, 32, 64, 128}) {
         Tuned c = best;
         c.claim_steps = cs;
@@ -251,6 +285,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     t->stage_levels = saved_stage;
     t->claim_steps = saved_claim;
     t->inline_depth = saved_inline;
+    t->light_run = saved_light;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(ids, s);
@@ -286,9 +321,9 @@ int kdt_tuning_save(const char *path)
         const Tuned &v = rows[i].second;
         ok = fprintf(f,
                      "  {\"gpu\": \"%s\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d, "
-                     "\"claim_steps\": %d, \"inline_depth\": %d}%s\n",
+                     "\"claim_steps\": %d, \"inline_depth\": %d, \"light_run\": %d}%s\n",
                      std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), v.stage_levels,
-                     v.claim_steps, v.inline_depth, i + 1 < rows.size() ? "," : "") > 0;
+                     v.claim_steps, v.inline_depth, v.light_run, i + 1 < rows.size() ? "," : "") > 0;
     }
     ok = ok && fprintf(f, "]\n") > 0;
     ok = (fclose(f) == 0) && ok;
@@ -296,7 +331,7 @@ int kdt_tuning_save(const char *path)
 }
 
 // reads the format kdt_tuning_save writes (one object per line); rows without
-// claim_steps / inline_depth take the defaults
+// claim_steps / inline_depth / light_run take the defaults
 int kdt_tuning_load(const char *path)
 {
     if (!path)
@@ -313,7 +348,7 @@ int kdt_tuning_load(const char *path)
             continue;
         g += 8;
         const char *ge = strchr(g, '"');
-        int D, kb, l2, lv, cs = -1, inl = -1;
+        int D, kb, l2, lv, cs = -1, inl = -1, lr = -1;
         if (!ge || sscanf(ge, "\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d", &D, &kb, &l2,
                           &lv) != 4 || lv < 0 || lv > 16 || kb < 0 || kb > 5) {
             bad = true;
@@ -321,14 +356,17 @@ int kdt_tuning_load(const char *path)
         }
         const char *c = strstr(ge, "\"claim_steps\": ");
         const char *d = strstr(ge, "\"inline_depth\": ");
+        const char *r = strstr(ge, "\"light_run\": ");
         if ((c && (sscanf(c + 15, "%d", &cs) != 1 || cs < 1 || cs > 256)) ||
-            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 2))) {
+            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 2)) ||
+            (r && (sscanf(r + 13, "%d", &lr) != 1 || lr < 1 || lr > 64))) {
             bad = true;
             break;
         }
         const int k_rep = kb == 0 ? 1 : (1 << kb);
         rows.emplace_back(ShapeKey(std::string(g, ge - g), D, kb, l2),
-                          Tuned{lv, c ? cs : default_claim_steps(k_rep), d ? inl : DEFAULT_INLINE_DEPTH});
+                          Tuned{lv, c ? cs : default_claim_steps(k_rep), d ? inl : DEFAULT_INLINE_DEPTH,
+                                r ? lr : DEFAULT_LIGHT_RUN});
     }
     fclose(f);
     if (bad)

@@ -107,14 +107,15 @@ _sig("kdt_build_batched", [_P, _P, _I, _I, _P, ctypes.POINTER(_P)])
 _sig("kdt_knn_batched", [_P, _P, _P, _I, _F, _I, _P, _P, _P])
 _sig("kdt_forest_export", [_P, _P, _P, _P])
 _sig("kdt_forest_free", [_P], None)
-_sig("kdt_forest_set_launch", [_P, _I, _I, _I])
+_sig("kdt_forest_set_launch", [_P, _I, _I, _I, _I])
 _sig("kdt_forest_autotune", [_P, _P, _P, _I, _F, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
-                              ctypes.POINTER(_F), _P])
+                              ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_profile_enable", [_P, _I])
 _sig("kdt_set_stage_levels", [_P, _I])
 _sig("kdt_set_claim_steps", [_P, _I])
 _sig("kdt_set_inline_depth", [_P, _I])
-_sig("kdt_tuned_params", [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)])
+_sig("kdt_set_light_run", [_P, _I])
+_sig("kdt_tuned_params", [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)])
 _sig("kdt_autotune", [_P, _P, _I64, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_tuning_save", [ctypes.c_char_p])
 _sig("kdt_tuning_load", [ctypes.c_char_p])
@@ -471,11 +472,15 @@ def kdt_set_inline_depth(tree: Tree, depth: int) -> None:
     _check(_lib.kdt_set_inline_depth(tree.handle, depth))
 
 
+def kdt_set_light_run(tree: Tree, steps: int) -> None:
+    _check(_lib.kdt_set_light_run(tree.handle, steps))
+
+
 def kdt_tuned_params(tree: Tree, k: int):
-    """(stage_levels, claim_steps, inline_depth) that kdt_knn uses for this tree and k."""
-    a, b, c = _I(), _I(), _I()
-    _check(_lib.kdt_tuned_params(tree.handle, k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    """(stage_levels, claim_steps, inline_depth, light_run) that kdt_knn uses for this tree and k."""
+    a, b, c, d = _I(), _I(), _I(), _I()
+    _check(_lib.kdt_tuned_params(tree.handle, k, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
 
 
 def kdt_set_stage_levels(tree: Tree, levels: int) -> None:
@@ -535,24 +540,25 @@ def kdt_knn_batched(forest: Forest, queries: torch.Tensor, qoffsets, k: int, max
     return out_ids, out_d2
 
 
-def kdt_forest_set_launch(forest: Forest, threads: int = 0, claim_steps: int = 0, inline_depth: int = 0) -> None:
-    _check(_lib.kdt_forest_set_launch(forest.handle, threads, claim_steps, inline_depth))
+def kdt_forest_set_launch(forest: Forest, threads: int = 0, claim_steps: int = 0, inline_depth: int = 0,
+                          light_run: int = 0) -> None:
+    _check(_lib.kdt_forest_set_launch(forest.handle, threads, claim_steps, inline_depth, light_run))
 
 
 def kdt_forest_autotune(forest: Forest, queries: torch.Tensor, query_offsets, k: int, max_radius: float = math.inf,
                         flags: int = 0, out_ids=None, out_d2=None, stream=None):
-    """Tune inline depth, block size and claim steps of the batched query;
-    returns (threads, claim_steps, inline_depth, ms)."""
+    """Tune inline depth, light run, block size and claim steps of the batched
+    query; returns (threads, claim_steps, inline_depth, light_run, ms)."""
     qoff = np.ascontiguousarray(query_offsets, dtype=np.int64)
     Q = int(qoff[-1])
     out_ids, out_d2 = _outputs(Q, k, out_ids, out_d2, queries.device)
-    th, cs, il, ms = _I(), _I(), _I(), _F()
+    th, cs, il, lr, ms = _I(), _I(), _I(), _I(), _F()
     _check(_lib.kdt_forest_autotune(forest.handle, _dev(queries, torch.float32, "queries", (Q, forest.D)),
                                     ctypes.c_void_p(qoff.ctypes.data), k, float(max_radius), flags,
                                     ctypes.c_void_p(out_ids.data_ptr()), ctypes.c_void_p(out_d2.data_ptr()),
-                                    ctypes.byref(th), ctypes.byref(cs), ctypes.byref(il), ctypes.byref(ms),
-                                    _stream(stream)))
-    return th.value, cs.value, il.value, ms.value
+                                    ctypes.byref(th), ctypes.byref(cs), ctypes.byref(il), ctypes.byref(lr),
+                                    ctypes.byref(ms), _stream(stream)))
+    return th.value, cs.value, il.value, lr.value, ms.value
 
 
 def kdt_forest_export(forest: Forest, stream=None):

@@ -58,7 +58,7 @@ def test_tuning_file_round_trip_without_gpu(lib, tmp_path):
     src.write_text('[\n'
                    '  {"gpu": "cpu-test-a", "D": 3, "k_bucket": 3, "log2n": 18, "stage_levels": 4},\n'
                    '  {"gpu": "cpu-test-b", "D": 2, "k_bucket": 0, "log2n": 20, "stage_levels": 0, '
-                   '"claim_steps": 128, "inline_depth": 0}\n]\n')
+                   '"claim_steps": 128, "inline_depth": 0, "light_run": 8}\n]\n')
     assert lib.kdt_tuning_load(str(src).encode()) == 0
     out = tmp_path / "out.json"
     assert lib.kdt_tuning_save(str(out).encode()) == 0
@@ -66,7 +66,8 @@ def test_tuning_file_round_trip_without_gpu(lib, tmp_path):
     assert rows["cpu-test-a"]["stage_levels"] == 4
     assert rows["cpu-test-a"]["claim_steps"] == 64 and rows["cpu-test-a"]["inline_depth"] == 2
     assert rows["cpu-test-b"]["claim_steps"] == 128 and rows["cpu-test-b"]["inline_depth"] == 0
-    for bad in ('"stage_levels": 99}', '"stage_levels": 0, "claim_steps": 0}',
+    assert rows["cpu-test-b"]["light_run"] == 8 and rows["cpu-test-a"]["light_run"] == 1
+    for bad in ('"stage_levels": 99}', '"stage_levels": 0, "claim_steps": 0}', '"stage_levels": 0, "light_run": 0}',
                 '"stage_levels": 0, "claim_steps": 64, "inline_depth": 3}'):
         src.write_text('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, ' + bad + '\n]\n')
         assert lib.kdt_tuning_load(str(src).encode()) == -7

@@ -114,14 +114,14 @@ def test_forest_launch_parameters_do_not_change_results(kdt, forest, k):
     pts, qs, P, Q, off, qoff, f = forest
     dq = cu(Q)
     ref_i, ref_d = kdt.kdt_knn_batched(f, dq, qoff, k, flags=kdt.KDT_PER_TREE)
-    for threads, inl in ((0, 0), (32, 1), (64, 2), (128, 1)):
+    for threads, inl, lr in ((0, 0, 0), (32, 1, 4), (64, 2, 8), (128, 1, 1)):
         for cs in (0, 1, 16, 256):
-            kdt.kdt_forest_set_launch(f, threads, cs, inl)
+            kdt.kdt_forest_set_launch(f, threads, cs, inl, lr)
             for flags in (kdt.KDT_MORTON, 0):
                 gi, gd = kdt.kdt_knn_batched(f, dq, qoff, k, flags=flags)
                 assert torch.equal(gi, ref_i) and torch.equal(gd.view(torch.int32), ref_d.view(torch.int32))
     kdt.kdt_forest_set_launch(f, 0, 0)
-    for bad in ((96 + 64, 0), (48, 0), (0, 257), (-32, 0), (0, 0, 3)):
+    for bad in ((96 + 64, 0), (48, 0), (0, 257), (-32, 0), (0, 0, 3), (0, 0, 0, 65)):
         with pytest.raises(kdt.KdtError):
             kdt.kdt_forest_set_launch(f, *bad)
 
@@ -130,8 +130,8 @@ def test_forest_autotune(kdt, forest):
     pts, qs, P, Q, off, qoff, f = forest
     dq = cu(Q)
     ref_i, ref_d = kdt.kdt_knn_batched(f, dq, qoff, 8, flags=kdt.KDT_PER_TREE)
-    th, cs, il, ms = kdt.kdt_forest_autotune(f, dq, qoff, 8, flags=kdt.KDT_MORTON)
-    assert th in (64, 128) and cs in (16, 32, 64, 128) and il in (1, 2) and ms > 0
+    th, cs, il, lr, ms = kdt.kdt_forest_autotune(f, dq, qoff, 8, flags=kdt.KDT_MORTON)
+    assert th in (64, 128) and cs in (16, 32, 64, 128) and il in (1, 2) and lr in (1, 4, 8) and ms > 0
     gi, gd = kdt.kdt_knn_batched(f, dq, qoff, 8, flags=kdt.KDT_MORTON)
     assert torch.equal(gi, ref_i) and torch.equal(gd.view(torch.int32), ref_d.view(torch.int32))
     with pytest.raises(kdt.KdtError):

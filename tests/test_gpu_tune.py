@@ -49,22 +49,25 @@ def test_claim_steps_and_inline_depth_identical(kdt, k):
     dq = torch.from_numpy(qs).cuda()
     ref = kdt.kdt_knn(tree, dq, k, flags=kdt.KDT_MORTON)
     ref_v = kdt.kdt_knn_visits(tree, dq, k)
-    for depth in (0, 1, 2):
+    for depth, lr in ((0, 1), (1, 4), (2, 1), (2, 8), (1, 64)):
         for cs in (1, 7, 16, 64, 256):
             kdt.kdt_set_inline_depth(tree, depth)
             kdt.kdt_set_claim_steps(tree, cs)
-            assert kdt.kdt_tuned_params(tree, k)[1:] == (cs, depth)
+            kdt.kdt_set_light_run(tree, lr)
+            assert kdt.kdt_tuned_params(tree, k)[1:] == (cs, depth, lr)
             for flags in (kdt.KDT_MORTON, kdt.KDT_UNORDERED, 0):
                 r = kdt.kdt_knn(tree, dq, k, flags=flags)
                 assert torch.equal(r[0], ref[0]) and torch.equal(r[1], ref[1]), (depth, cs, flags)
             assert torch.equal(kdt.kdt_knn_visits(tree, dq, k), ref_v)
-    for bad in ((kdt.kdt_set_inline_depth, 3), (kdt.kdt_set_claim_steps, 0), (kdt.kdt_set_claim_steps, 257)):
+    for bad in ((kdt.kdt_set_inline_depth, 3), (kdt.kdt_set_claim_steps, 0), (kdt.kdt_set_claim_steps, 257),
+                (kdt.kdt_set_light_run, 0), (kdt.kdt_set_light_run, 65)):
         with pytest.raises(kdt.KdtError):
             bad[0](tree, bad[1])
     kdt.kdt_set_inline_depth(tree, -1)
     kdt.kdt_set_claim_steps(tree, -1)
-    assert kdt.kdt_tuned_params(tree, 1) == (0, 32, 2)
-    assert kdt.kdt_tuned_params(tree, 8) == (0, 64, 2)
+    kdt.kdt_set_light_run(tree, -1)
+    assert kdt.kdt_tuned_params(tree, 1) == (0, 32, 2, 1)
+    assert kdt.kdt_tuned_params(tree, 8) == (0, 64, 2, 1)
 
 
 def test_autotune_and_tuning_file(kdt, tmp_path):
@@ -73,13 +76,13 @@ def test_autotune_and_tuning_file(kdt, tmp_path):
     dq = torch.from_numpy(qs).cuda()
     lv, ms = kdt.kdt_autotune(tree, dq, 8, kdt.KDT_MORTON)
     assert lv in (0, 4, 6, 8) and ms > 0
-    tlv, cs, depth = kdt.kdt_tuned_params(tree, 8)
-    assert tlv == lv and cs in (16, 32, 64, 128) and depth in (0, 1, 2)
+    tlv, cs, depth, lr = kdt.kdt_tuned_params(tree, 8)
+    assert tlv == lv and cs in (16, 32, 64, 128) and depth in (0, 1, 2) and lr in (1, 4, 8)
     path = os.path.join(tmp_path, "tuning.json")
     kdt.kdt_tuning_save(path)
     rows = json.load(open(path))
     assert any(r["D"] == 3 and r["log2n"] == 18 and r["stage_levels"] == lv and r["claim_steps"] == cs and
-               r["inline_depth"] == depth for r in rows)
+               r["inline_depth"] == depth and r["light_run"] == lr for r in rows)
     kdt.kdt_tuning_load(path)
     a = kdt.kdt_knn(tree, dq, 8, flags=kdt.KDT_MORTON)
     kdt.kdt_set_stage_levels(tree, 0)
