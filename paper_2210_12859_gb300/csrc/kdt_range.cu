@@ -26,6 +26,8 @@ namespace kdt {
 namespace {
 
 constexpr int RANGE_THREADS = 128;
+// traversal steps between two claim rounds of a warp (as for kNN, 64 beats 16)
+constexpr int RANGE_CLAIM_STEPS = 64;
 enum : int { ACT_COUNT = 0, ACT_FILL = 1, ACT_REDUCE = 2 };
 // binary32 rounding of pi
 constexpr float PI_F = 3.14159265358979323846f;
@@ -77,7 +79,8 @@ __device__ __forceinline__ float finish_reduce(float s, int64_t n, int mode, flo
 
 // KIND 0: ball of squared radius r2 around a[q]; KIND 1: box [a[q], b[q]].
 // Persistent blocks; every lane claims its next query when its current one
-// ends (checked every STEPS_PER_CLAIM steps), as in the kNN kernel.
+// ends (checked every RANGE_CLAIM_STEPS steps), as in the kNN kernel; the step
+// bound 3N + 3 is checked once per round.
 template <int LAYOUT, int KIND, int ACT>
 __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
 {
@@ -123,12 +126,12 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
         if (qi < 0)
             continue;
         bool done = false;
-        for (int s = 0; s < STEPS_PER_CLAIM && !done; ++s) {
-            if (++steps > cap) {
-                atomicOr(a.err, ERR_TRAVERSAL);
-                done = true;
-                break;
-            }
+        if (steps > cap) {
+            atomicOr(a.err, ERR_TRAVERSAL);
+            done = true;
+        }
+        for (int s = 0; s < RANGE_CLAIM_STEPS && !done; ++s) {
+            ++steps;
             const NodeVal<LAYOUT> nd = fetch<LAYOUT, false>(a.nodes, nullptr, 0, curr);
             const bool from_parent = prev < curr;
             if (from_parent) {
