@@ -264,69 +264,6 @@ struct Walker {
         steps = 0;
     }
 
-    template <class T>
-    __device__ __forceinline__ static T pick(bool c, const T &x, const T &y)
-    {
-        T r;
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-            r.c[j] = c ? x.c[j] : y.c[j];
-        r.id = c ? x.id : y.id;
-        return r;
-    }
-
-    // Leaves lc (value a) and lc+1 (value b, valid iff lc+1 < N) below a node
-    // whose split offset is sd: process them in the order the machine visits
-    // them.  The values were loaded before, both at once.
-    template <class List>
-    __device__ __forceinline__ void leaf_pair(float sd, float sd2, int lc, const NodeVal<LAYOUT> &a,
-                                              const NodeVal<LAYOUT> &b, const int32_t *__restrict__ ids, int N,
-                                              const float (&q)[NC], List &list, int &visits)
-    {
-        const int rc = lc + 1;
-        const bool rc_ok = rc < N;
-        if constexpr (ORDERED) {
-            const bool right_first = sd > 0.f;
-            const NodeVal<LAYOUT> first = pick(right_first, b, a);
-            const NodeVal<LAYOUT> second = pick(right_first, a, b);
-            if (!right_first || rc_ok) {
-                ++visits;
-                process<LAYOUT>(first, right_first ? rc : lc, ids, q, list);
-            }
-            if ((right_first || rc_ok) && sd2 <= list.cull()) {
-                ++visits;
-                process<LAYOUT>(second, right_first ? lc : rc, ids, q, list);
-            }
-        } else {
-            if (sd <= 0.f || sd2 <= list.cull()) {
-                ++visits;
-                process<LAYOUT>(a, lc, ids, q, list);
-            }
-            if (rc_ok && (sd > 0.f || sd2 <= list.cull())) {
-                ++visits;
-                process<LAYOUT>(b, rc, ids, q, list);
-            }
-        }
-    }
-
-    // node c (value nc, split dimension dimc) whose children are leaves (values
-    // ga, gb, loaded before): process it, then its children
-    template <class List>
-    __device__ __forceinline__ void leaf_parent(int c, int dimc, const NodeVal<LAYOUT> &nc,
-                                                const NodeVal<LAYOUT> &ga, const NodeVal<LAYOUT> &gb,
-                                                const int32_t *__restrict__ ids, int N, const float (&q)[NC],
-                                                List &list, int &visits)
-    {
-        ++visits;
-        process<LAYOUT>(nc, c, ids, q, list);
-        const int lcc = 2 * c + 1;
-        if (lcc < N) {
-            const int dc = split_dim_of<LAYOUT>(nc, dimc);
-            const float sdc = __fsub_rn(select_dim<NC>(q, dc), select_dim<NC>(nc.c, dc));
-            leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ga, gb, ids, N, q, list, visits);
-        }
-    }
-
     // Whole bottom subtrees: the keys (d2, id) of all their nodes and the
     // children's split offsets are computed first, from the values loaded at
     // once; the machine's order is then followed on these scalars (a node's
@@ -346,19 +283,34 @@ struct Walker {
         if (k < list.worst())
             list.insert(k);
     }
+    // leaves lcc (key ka) and lcc + 1 (key kb, valid iff lcc + 1 < N) below a
+    // node whose split offset is sdc, in the machine's order: ordered, close
+    // leaf first and the far one if the plane is still within the cull
+    // radius; unordered, left then right, each if on the query's side or in range
     template <class List>
     __device__ __forceinline__ static void eager_leaf_pair(float sdc, float sdc2, int lcc, unsigned long long ka,
                                                            unsigned long long kb, int N, List &list, int &visits)
     {
-        const bool rf = sdc > 0.f;
         const bool rcc_ok = lcc + 1 < N;
-        if (!rf || rcc_ok) {
-            ++visits;
-            offer(list, rf ? kb : ka);
-        }
-        if ((rf || rcc_ok) && sdc2 <= list.cull()) {
-            ++visits;
-            offer(list, rf ? ka : kb);
+        if constexpr (ORDERED) {
+            const bool rf = sdc > 0.f;
+            if (!rf || rcc_ok) {
+                ++visits;
+                offer(list, rf ? kb : ka);
+            }
+            if ((rf || rcc_ok) && sdc2 <= list.cull()) {
+                ++visits;
+                offer(list, rf ? ka : kb);
+            }
+        } else {
+            if (sdc <= 0.f || sdc2 <= list.cull()) {
+                ++visits;
+                offer(list, ka);
+            }
+            if (rcc_ok && (sdc > 0.f || sdc2 <= list.cull())) {
+                ++visits;
+                offer(list, kb);
+            }
         }
     }
     template <class List>
@@ -418,16 +370,16 @@ struct Walker {
             const NodeVal<LAYOUT> g11 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 3, last));
             const int dim1 = dim + 1 == D ? 0 : dim + 1;
             const bool rc_ok = rc < N;
+            const unsigned long long k_c0 = node_key(c0, lc, ids, q), k_c1 = node_key(c1, min(rc, last), ids, q);
+            const unsigned long long k_g00 = node_key(g00, g0, ids, q);
+            const unsigned long long k_g01 = node_key(g01, min(g0 + 1, last), ids, q);
+            const unsigned long long k_g10 = node_key(g10, min(g0 + 2, last), ids, q);
+            const unsigned long long k_g11 = node_key(g11, min(g0 + 3, last), ids, q);
+            const int d0 = split_dim_of<LAYOUT>(c0, dim1), d1 = split_dim_of<LAYOUT>(c1, dim1);
+            const float sdc0 = __fsub_rn(select_dim<NC>(q, d0), select_dim<NC>(c0.c, d0));
+            const float sdc1 = __fsub_rn(select_dim<NC>(q, d1), select_dim<NC>(c1.c, d1));
             if constexpr (ORDERED) {
                 const bool right_first = sd > 0.f;
-                const unsigned long long k_c0 = node_key(c0, lc, ids, q), k_c1 = node_key(c1, min(rc, last), ids, q);
-                const unsigned long long k_g00 = node_key(g00, g0, ids, q);
-                const unsigned long long k_g01 = node_key(g01, min(g0 + 1, last), ids, q);
-                const unsigned long long k_g10 = node_key(g10, min(g0 + 2, last), ids, q);
-                const unsigned long long k_g11 = node_key(g11, min(g0 + 3, last), ids, q);
-                const int d0 = split_dim_of<LAYOUT>(c0, dim1), d1 = split_dim_of<LAYOUT>(c1, dim1);
-                const float sdc0 = __fsub_rn(select_dim<NC>(q, d0), select_dim<NC>(c0.c, d0));
-                const float sdc1 = __fsub_rn(select_dim<NC>(q, d1), select_dim<NC>(c1.c, d1));
                 if (!right_first || rc_ok)
                     eager_leaf_parent(right_first ? rc : lc, right_first ? k_c1 : k_c0, right_first ? sdc1 : sdc0,
                                       right_first ? k_g10 : k_g00, right_first ? k_g11 : k_g01, N, list, visits);
@@ -436,9 +388,9 @@ struct Walker {
                                       right_first ? k_g00 : k_g10, right_first ? k_g01 : k_g11, N, list, visits);
             } else {
                 if (sd <= 0.f || sd2 <= list.cull())
-                    leaf_parent(lc, dim1, c0, g00, g01, ids, N, q, list, visits);
+                    eager_leaf_parent(lc, k_c0, sdc0, k_g00, k_g01, N, list, visits);
                 if (rc_ok && (sd > 0.f || sd2 <= list.cull()))
-                    leaf_parent(rc, dim1, c1, g10, g11, ids, N, q, list, visits);
+                    eager_leaf_parent(rc, k_c1, sdc1, k_g10, k_g11, N, list, visits);
             }
             next = parent;
         } else if (INLINE >= 1 && from_parent && lc < N && 2 * lc + 1 >= N) {
@@ -446,11 +398,8 @@ struct Walker {
             // loads first
             const NodeVal<LAYOUT> a = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
             const NodeVal<LAYOUT> b = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(rc, N - 1));
-            if constexpr (ORDERED)
-                eager_leaf_pair(sd, sd2, lc, node_key(a, lc, ids, q), node_key(b, min(rc, N - 1), ids, q), N, list,
-                                visits);
-            else
-                leaf_pair(sd, sd2, lc, a, b, ids, N, q, list, visits);
+            eager_leaf_pair(sd, sd2, lc, node_key(a, lc, ids, q), node_key(b, min(rc, N - 1), ids, q), N, list,
+                            visits);
             next = parent;
         } else {
             const float cull = list.cull();
