@@ -419,6 +419,18 @@ int kdt_autotune(kdt_tree *tree, const float *d_queries, int64_t Q, int k, int f
 int kdt_tuning_save(const char *path);
 int kdt_tuning_load(const char *path);
 
+/* ---- failure injection (tests) ------------------------------------------
+ * Host-side hooks that make the library's error paths reachable without a
+ * device fault.  kdt_debug_fail_allocs(n): the next n device allocations the
+ * library makes (tree arrays, per-call scratch) fail with KDT_ENOMEM; 0
+ * clears.  kdt_debug_set_step_cap(tree, cap): traversals of kdt_knn /
+ * kdt_fcp / kdt_knn_visits on this tree stop after about cap steps (the bound
+ * is checked once per claim round) and report KDT_ETRAVERSAL through
+ * kdt_status, as a traversal exceeding the 3N + 3 bound would; 0 restores
+ * the bound.  No paper counterpart. */
+int kdt_debug_fail_allocs(int n);
+int kdt_debug_set_step_cap(kdt_tree *tree, uint32_t cap);
+
 /* ---- profiling ----------------------------------------------------------- */
 
 /* Accumulate device time of the traversal kernels launched by kdt_knn /

@@ -61,6 +61,17 @@ int grid_for_kernel(const void *fn, int threads, size_t smem)
 
 static bool bad_radius(float r) { return !(r >= 0.f); }
 
+static std::atomic<int> g_fail_allocs{0};
+
+bool debug_alloc_fails()
+{
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1))
+            return true;
+    return false;
+}
+
 // ---------------------------------------------------------------- Morton order
 
 __device__ __forceinline__ uint32_t spread3(uint32_t x)
@@ -235,6 +246,7 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
+    a.step_cap = t->debug_step_cap;
     a.inline_depth = inline_depth_for(t, k);
     cudaEvent_t stop;
     KDT_TRY(prof_begin(const_cast<kdt_tree *>(t), s, &stop));
@@ -338,6 +350,10 @@ __attribute__((visibility("hidden"))) int kdt_tree_alloc_internal(int64_t N, int
     t->layout = layout_of(D);
     cudaGetDevice(&t->device);
     t->prof = new Prof();
+    if (debug_alloc_fails()) {
+        kdt_free(t);
+        return set_error(KDT_ENOMEM, "device allocation failed (injected)");
+    }
     const int nf = float4_per_node(D);
     cudaError_t e = cudaMalloc(&t->nodes_alloc, ((size_t)N * nf + (nf == 1 ? 1 : 0)) * sizeof(float4));
     t->nodes = t->nodes_alloc + (nf == 1 ? 1 : 0);
@@ -430,6 +446,22 @@ int kdt_rebuild(kdt_tree *t, const float *d_points, int opts, void *stream)
     int64_t off[2] = {0, t->N};
     KDT_TRY(build_forest(d_points, off, 1, t->D, t->nodes, t->ids, t->bbox, t->err, s, t->layout == 3));
     return finish_build(t, opts, s);
+}
+
+int kdt_debug_fail_allocs(int n)
+{
+    if (n < 0)
+        return set_error(KDT_EINVAL, "n must be >= 0");
+    g_fail_allocs.store(n);
+    return KDT_OK;
+}
+
+int kdt_debug_set_step_cap(kdt_tree *t, uint32_t cap)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    t->debug_step_cap = cap;
+    return KDT_OK;
 }
 
 int kdt_tree_info(const kdt_tree *t, int64_t *N, int *D)

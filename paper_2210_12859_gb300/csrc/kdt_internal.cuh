@@ -168,6 +168,10 @@ size_t morton_scratch_bytes(int64_t Q);
 
 // ---------------------------------------------------------------- scratch
 
+// failure injection for tests: true while kdt_debug_fail_allocs has failures
+// left (each call consumes one)
+bool debug_alloc_fails();
+
 inline void pool_setup_once()
 {
     static bool done[64] = {false};
@@ -192,6 +196,8 @@ struct Scratch {
     explicit Scratch(cudaStream_t s_) : s(s_) {}
     int alloc(size_t bytes)
     {
+        if (debug_alloc_fails())
+            return set_error(KDT_ENOMEM, "device allocation failed (injected)");
         KDT_CUDA(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s));
         return KDT_OK;
     }
@@ -267,6 +273,8 @@ struct kdt_tree {
     int inline_depth = -1;
     // steps a lane may take per call while they are light (-1: tuned or 1)
     int light_run = -1;
+    // test hook: traversal step bound (0: 3N + 3)
+    uint32_t debug_step_cap = 0;
     // per-point payload in node order [N][payload_c] and node_of[input index]
     // (kdt_tree_set_payload; dropped by a rebuild)
     float *payload = nullptr;

@@ -30,6 +30,7 @@ struct QueryArgs {
     int inline_depth = 2;              // bottom-subtree depth processed within one step (1 or 2)
     int threads = 0;                   // block size of the forest kernel (0: the kernel's default)
     int light_run = 1;                 // steps a lane may take per call while they are light
+    uint32_t step_cap = 0;             // traversal step bound (0: 3N + 3; a test hook lowers it)
     unsigned long long *counter = nullptr;  // dynamic work counter, zeroed before launch
     // batched forests
     int T = 1;

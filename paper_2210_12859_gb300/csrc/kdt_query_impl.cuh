@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         for (int s = 0; s < a.claim_steps && !fin; ++s)
             fin = w.template step<STAGE, RUNS>(a.nodes, a.ids, s_nodes, a.staged, a.N, a.D, q, list, visits,
                                                overflow, a.light_run);
-        if (!fin && w.steps > 3u * (uint32_t)a.N + 3u) {
+        if (!fin && w.steps > (a.step_cap ? a.step_cap : 3u * (uint32_t)a.N + 3u)) {
             overflow = true;
             fin = true;
         }

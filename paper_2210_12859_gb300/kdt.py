@@ -111,6 +111,8 @@ _sig("kdt_forest_set_launch", [_P, _I, _I, _I, _I])
 _sig("kdt_forest_autotune", [_P, _P, _P, _I, _F, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_profile_enable", [_P, _I])
+_sig("kdt_debug_fail_allocs", [_I])
+_sig("kdt_debug_set_step_cap", [_P, ctypes.c_uint32])
 _sig("kdt_set_stage_levels", [_P, _I])
 _sig("kdt_set_claim_steps", [_P, _I])
 _sig("kdt_set_inline_depth", [_P, _I])
@@ -504,6 +506,16 @@ def kdt_tuning_save(path: str) -> None:
 
 def kdt_tuning_load(path: str) -> None:
     _check(_lib.kdt_tuning_load(os.fsencode(path)))
+
+
+def kdt_debug_fail_allocs(n: int) -> None:
+    """Make the library's next n device allocations fail with KDT_ENOMEM (tests)."""
+    _check(_lib.kdt_debug_fail_allocs(n))
+
+
+def kdt_debug_set_step_cap(tree: Tree, cap: int) -> None:
+    """Lower the traversal step bound of a tree (0 restores 3N + 3; tests)."""
+    _check(_lib.kdt_debug_set_step_cap(tree.handle, cap))
 
 
 def kdt_profile_enable(tree: Tree, enable: bool = True) -> None:

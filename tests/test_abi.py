@@ -85,3 +85,17 @@ def test_size_limits_rejected_on_the_host(lib):
         assert lib.kdt_build_ex(dummy, n, d, 0, None, ctypes.byref(out)) == -1, (n, d)
         assert not out.value
     assert lib.kdt_build_ex(None, 100, 3, 0, None, ctypes.byref(out)) == -1
+
+
+def test_injected_allocation_failure_without_gpu(lib):
+    """kdt_debug_fail_allocs makes a build fail with KDT_ENOMEM (-3) before any
+    device access; the hook counts down and clears."""
+    lib.kdt_debug_fail_allocs.argtypes = [ctypes.c_int]
+    lib.kdt_build_ex.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    assert lib.kdt_debug_fail_allocs(1) == 0
+    assert lib.kdt_build_ex(ctypes.c_void_p(16), 100, 3, 0, None, ctypes.byref(out)) == -3
+    assert not out.value
+    assert lib.kdt_debug_fail_allocs(-1) == -1
+    assert lib.kdt_debug_fail_allocs(0) == 0
