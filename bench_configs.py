@@ -191,8 +191,11 @@ def run_config(args):
         # algorithmic bytes of the fill pass: query 12 B + 16 B per processed
         # node + 8 B per hit (id, d2) + 16 B of offsets, against measured HBM
         fill_bytes = nq * (12 + 16) + 16.0 * visits + 8.0 * total
-        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        try:
+            peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+            hbm = float(peaks.get("hbm_gbs", 6800.0))
+        except (OSError, ValueError):
+            hbm = 6800.0  # the fallback peak when no measured peaks are available
         _emit(config=f"range: gmm N=2^24, Q=2^22 (90% mixture, 10% uniform), ball r={r}", form="ball count / offsets / fill",
               queries_per_s=nq / ((cnt_ms + off_ms + fill_ms) / 1e3), hits=int(total), hits_per_query=total / nq,
               hits_per_s=total / ((cnt_ms + off_ms + fill_ms) / 1e3), count_ms=cnt_ms, offsets_ms=off_ms,
