@@ -47,7 +47,8 @@ def parse():
                          "(profiling runs whose first traversal launch must be a full one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--config", default="gmm_large",
-                    choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched", "ablation", "range"],
+                    choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched", "ablation", "range",
+                             "variants"],
                     help="gmm_large: the contract line; the others print one JSON line per measured form")
     return ap.parse_args()
 

@@ -230,6 +230,44 @@ def run_config(args):
                                                                                             want.view(np.uint32))))
         return
 
+    if args.config == "variants":
+        # the other forms of the clustered 2^24 workload (fcp, k = 32 / 64, a
+        # bounded radius) and the stored split dimension on surface data
+        n = 1 << 24
+        pts, qs = synth.gmm_large(n, n, seed=synth.BASE_SEED + 2)
+        dp, dq = cu(pts), cu(qs)
+        tree = kdt.kdt_build(dp)
+        F = kdt.KDT_MORTON | kdt.KDT_COST_ORDER
+        for k, r in ((1, math.inf), (32, math.inf), (64, math.inf), (8, 0.005)):
+            kdt.kdt_autotune(tree, dq, k, F)
+            gi, gd = kdt.kdt_knn(tree, dq, k, r, F)
+            ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, r, F, gi, gd), 2)
+            v = kdt.kdt_knn_visits(tree, dq, k, r, F).double().mean().item()
+            _emit(config="gmm_large N=Q=2^24", form=f"{'fcp' if k == 1 else f'kNN k={k}'}, r={r}",
+                  query_qps=n / (ms / 1e3), query_ms=ms, visits_per_query=v,
+                  launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"),
+                                            kdt.kdt_tuned_params(tree, k))),
+                  bit_exact_sample=_exact(oracle, pts, qs, gi.cpu().numpy(), gd.cpu().numpy(), k, r, n=32))
+            del gi, gd
+        del tree, dp, dq
+        sh = synth.surface_shapes(256, synth.BASE_SEED + 4)
+        pts = synth.surface_sample(sh, n, synth.BASE_SEED + 41)
+        qs = synth.surface_sample(sh, n, synth.BASE_SEED + 43)
+        dp, dq = cu(pts), cu(qs)
+        res = {}
+        for name, opts in (("level split", 0), ("stored split dimension (widest extent)", kdt.KDT_BUILD_WIDEST)):
+            tree = kdt.kdt_build(dp, opts=opts)
+            gi, gd = kdt.kdt_knn(tree, dq, 8, math.inf, kdt.KDT_MORTON)
+            ms = timeit(lambda: kdt.kdt_knn(tree, dq, 8, math.inf, kdt.KDT_MORTON, gi, gd), 3)
+            v = kdt.kdt_knn_visits(tree, dq, 8, math.inf, kdt.KDT_MORTON).double().mean().item()
+            res[name] = (gi.clone(), gd.clone())
+            _emit(config="surface N=Q=2^24 kNN k=8", form=name, query_qps=n / (ms / 1e3), query_ms=ms,
+                  visits_per_query=v,
+                  identical_to_level_split=bool(torch.equal(gi, res["level split"][0]) and
+                                                torch.equal(gd, res["level split"][1])))
+            del tree
+        return
+
     if args.config == "batched":
         c = synth.clouds(4096, seed=synth.BASE_SEED + 5)
         dp, dq = cu(c.points), cu(c.queries)
