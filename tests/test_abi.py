@@ -99,3 +99,30 @@ def test_injected_allocation_failure_without_gpu(lib):
     assert not out.value
     assert lib.kdt_debug_fail_allocs(-1) == -1
     assert lib.kdt_debug_fail_allocs(0) == 0
+
+
+def test_binding_rejects_host_tensors_no_cpu_fallback():
+    """The product path has no CPU fallback: host tensors are refused before
+    any library call."""
+    torch = pytest.importorskip("torch")
+    from paper_2210_12859_gb300 import kdt
+
+    pts = torch.rand((64, 3))
+    with pytest.raises(TypeError):
+        kdt.kdt_build(pts)
+    with pytest.raises(TypeError):
+        kdt.kdt_offsets(torch.zeros(4, dtype=torch.int32))
+
+
+def test_binding_without_library_raises(tmp_path):
+    """Importing the binding where libkdt.so is missing raises ImportError."""
+    import importlib.util
+    import shutil
+
+    pytest.importorskip("torch")
+    src = os.path.join(ROOT, "paper_2210_12859_gb300", "kdt.py")
+    shutil.copy(src, tmp_path / "kdt_copy.py")
+    spec = importlib.util.spec_from_file_location("kdt_copy", tmp_path / "kdt_copy.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)
