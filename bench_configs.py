@@ -100,10 +100,12 @@ def run_config(args):
         qs = synth.surface_sample(sh, n, synth.BASE_SEED + 43)
         dp, dq, dt = cu(pts), cu(qs), cu(train)
         tree = kdt.kdt_build(dp)
-        for k in (8, 32):
+        for k, margin in ((8, 0.0), (32, 0.0), (8, 1.25), (32, 1.25)):
+            # margin 0: calibrated by the library; 1.25: the fixed margin of the configuration
             t0 = time.perf_counter()
-            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1)
+            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1, margin=margin)
             train_s = time.perf_counter() - t0
+            used_margin = kdt.kdt_radius_model_get(tree)[2]
             out_i = torch.empty((n, k), dtype=torch.int32, device="cuda")
             out_d = torch.empty((n, k), dtype=torch.float32, device="cuda")
             li = torch.empty_like(out_i)
@@ -114,7 +116,9 @@ def run_config(args):
             pv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON).double().mean().item()
             lv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON | kdt.KDT_LEARNED).double().mean().item()
             same = bool(torch.equal(li, out_i) and torch.equal(ld.view(torch.int32), out_d.view(torch.int32)))
-            _emit(config="surface_learned N=Q=2^24 (256 spheres/tori)", form=f"kNN k={k} plain vs learned",
+            _emit(config="surface_learned N=Q=2^24 (256 spheres/tori)",
+                  form=f"kNN k={k} plain vs learned ({'margin 1.25 as configured' if margin else 'calibrated margin'})",
+                  margin=used_margin,
                   plain_qps=n / (plain_ms / 1e3), learned_qps=n / (learned_ms / 1e3),
                   speedup=plain_ms / learned_ms, fallback_rate=fb / n, radius_ratio=ratio,
                   plain_visits=pv, learned_visits=lv, identical=same, train_s=train_s, train_loss=loss,

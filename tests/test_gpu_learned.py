@@ -147,6 +147,23 @@ def test_training_fits_radii(kdt, uniform_weights):
         assert learned < 1.05 * plain, (learned, plain)
 
 
+def test_fixed_margin_as_configured(kdt, surface):
+    """The learned-radius configuration fixes the cull radius at 1.25 x the
+    prediction: a margin given to the training is kept as is (no
+    calibration), and the results stay those of the plain method."""
+    pts, qs, _ = surface
+    tree = kdt.kdt_build(cu(pts))  # its own tree: the module's tree keeps its model
+    kdt.kdt_radius_model_train(tree, cu(qs[: 1 << 14]), 8, epochs=4, batch=1024, seed=5, margin=1.25)
+    _, _, margin = kdt.kdt_radius_model_get(tree)
+    assert margin == 1.25
+    q = cu(qs[1 << 15:])
+    for k in (8, 32):
+        pi, pd = kdt.kdt_knn(tree, q, k, flags=kdt.KDT_MORTON)
+        li, ld = kdt.kdt_knn(tree, q, k, flags=kdt.KDT_MORTON | kdt.KDT_LEARNED)
+        assert torch.equal(pi, li) and torch.equal(pd.view(torch.int32), ld.view(torch.int32))
+    kdt.kdt_status(tree)
+
+
 @pytest.mark.parametrize("k", [8, 32])
 @pytest.mark.parametrize("flags_name", ["MORTON", "ORDERED"])
 def test_learned_equals_plain(kdt, surface, trained, k, flags_name):
