@@ -50,7 +50,9 @@ __host__ __device__ inline bool is_weight(int i)
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__global__ void round_params_kernel(const float *__restrict__ master, float *__restrict__ rounded)
+// master and rounded may be the same buffer (element-wise, in place), so
+// neither pointer is restrict-qualified
+__global__ void round_params_kernel(const float *master, float *rounded)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P)
