@@ -721,3 +721,20 @@ def test_range_visits_equal_unordered_knn_with_unfillable_list(seed):
         assert np.array_equal(v, kv), r
     # r = inf processes every node once
     assert np.all(oracle.range_visits(pts, pid, qs, radius=math.inf) == N)
+
+
+def test_radius_brute_against_fp64_up_to_boundary_ties():
+    """The ball query's FP32 hit sets equal the FP64 definition except for points
+    whose distance lies within a few float ulps of the radius."""
+    g = np.random.default_rng(31)
+    pts = g.random((4000, 3)).astype(np.float32)
+    qs = g.random((50, 3)).astype(np.float32)
+    r = 0.11
+    counts, off, ids, d2 = oracle.radius_brute(pts, qs, r)
+    r2_64 = float(np.float32(r) * np.float32(r))
+    for q in range(len(qs)):
+        d64 = ((pts.astype(np.float64) - qs[q].astype(np.float64)) ** 2).sum(1)
+        want = set(np.nonzero(d64 <= r2_64)[0].tolist())
+        got = set(ids[off[q]:off[q + 1]].tolist())
+        for i in want ^ got:
+            assert abs(d64[i] - r2_64) <= 8 * np.spacing(np.float32(r2_64)), (q, i)
