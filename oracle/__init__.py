@@ -19,8 +19,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "kdt_oracle.c")
-_LIB = os.path.join(_HERE, "libkdt_oracle.so")
+# KDT_ORACLE_SRC points the module at another copy of the C source (the
+# mutation tests compile deliberately broken copies and check that the pins
+# reject each of them); the shared object is built next to that copy.
+_SRC = os.path.abspath(os.environ.get("KDT_ORACLE_SRC") or os.path.join(_HERE, "kdt_oracle.c"))
+_LIB = os.path.join(os.path.dirname(_SRC), "libkdt_oracle.so")
 _lock = threading.Lock()
 _lib = None
 

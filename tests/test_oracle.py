@@ -193,6 +193,24 @@ def test_one_dimension_is_sorted_array_search():
         assert pts[ids[i, 0], 0] == xs[best]
 
 
+def test_fp64_brute_matches_lexicographic_selection_on_ties():
+    """On small integer coordinates every squared distance is an exact integer
+    in both precisions, so equal distances are common and the FP64 selection
+    must be the k smallest (d2, index) pairs, as the FP32 one is."""
+    g = np.random.default_rng(11)
+    pts = g.integers(-3, 4, size=(300, 3)).astype(np.float32)
+    qs = g.integers(-3, 4, size=(60, 3)).astype(np.float32)
+    exact = ((pts[None, :, :].astype(np.int64) - qs[:, None, :].astype(np.int64)) ** 2).sum(axis=2)
+    for k in (1, 7, 40, 301):
+        i64, d64 = oracle.knn_brute_f64(pts, qs, k)
+        for q in range(len(qs)):
+            order = np.lexsort((np.arange(len(pts)), exact[q]))[:k]
+            n = len(order)
+            assert i64[q, :n].tolist() == order.tolist()
+            assert d64[q, :n].tolist() == exact[q, order].astype(np.float64).tolist()
+            assert (i64[q, n:] == -1).all() and np.isinf(d64[q, n:]).all()
+
+
 def test_fp32_matches_fp64_up_to_rounding():
     g = np.random.default_rng(10)
     pts = g.random((3000, 3)).astype(np.float32)
@@ -237,6 +255,15 @@ def _cases():
         else:
             pts = g.random((N, D)).astype(np.float32)
         qs = (g.random((25, D)) * 1.4 - 0.2).astype(np.float32)
+        yield seed, pts, qs
+    # integer grids: queries on the splitting planes (sd == 0, where the close
+    # side is the left child), and many equal distances
+    for seed in range(12, 16):
+        g = np.random.default_rng(200 + seed)
+        N = int(g.integers(2, 90))
+        D = int(g.integers(1, 4))
+        pts = g.integers(0, 3, size=(N, D)).astype(np.float32)
+        qs = g.integers(-1, 4, size=(25, D)).astype(np.float32)
         yield seed, pts, qs
 
 
