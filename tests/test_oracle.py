@@ -420,6 +420,26 @@ def test_mlp_bf16_activation_forward_rounds_hidden_layer():
     assert oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0] == 1.0
 
 
+def test_mlp_bf16_activation_layer1_rounds_once_per_term():
+    """Layer 1 of the device-path forward is a fused multiply-add chain: each
+    term w*x + a is rounded to FP32 once.  With w = 1 + 2^-13, x = 1 + 2^-11 -
+    2^-13 + 2^-19 and bias -1 the exact w*x - 1 is M + d, M = 2^-11 + 2^-19 and
+    d = 2^-24 - 2^-26 + 2^-32 (exact in FP32 at that magnitude).  Rounded once
+    it stays above M, the midpoint of the bfloat16 neighbours 2^-11 and
+    2^-11 + 2^-18, and rounds up; rounding the product first (its d is below
+    half an FP32 ulp at 1) lands exactly on M, which ties to even: 2^-11."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0 + 2.0 ** -13                   # W1[0][0]
+    p[4] = -1.0                               # b1
+    p[5] = 1.0                                # W2
+    p[7] = 1.0                                # w3
+    x = np.array([[1.0 + 2.0 ** -11 - 2.0 ** -13 + 2.0 ** -19, 0, 0, 0]])
+    assert np.float32(p[0]) == p[0] and np.float32(x[0, 0]) == x[0, 0]
+    y = oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0]
+    assert y == 2.0 ** -11 + 2.0 ** -18
+
+
 # ---------------------------------------------------------------- stored split dimension
 
 def _check_widest_tree(pts, node_pid, node_dim):
@@ -639,6 +659,24 @@ def test_payload_reductions_integer_payload_exact():
             R2 = float(kd[q][len(v) - 1])
             assert R2 == float(kd[q][ki[q] >= 0].max())
             assert np.allclose(kdn[q] * np.pi * R2, want, rtol=1e-5, atol=1e-5)
+
+
+def test_payload_reductions_of_empty_sets_are_zero():
+    """A query with no hit reduces to 0 in every mode (no 0/0 for the mean, nor
+    for the kNN density, whose disc has radius 0 when nothing was found)."""
+    g = np.random.default_rng(19)
+    N, C = 500, 3
+    pts = g.random((N, 3)).astype(np.float32)
+    pay = g.integers(1, 9, size=(N, C)).astype(np.float32)
+    pid = oracle.build(pts)
+    qs = np.array([[5.0, 5.0, 5.0], [-3.0, 0.5, 0.5], [0.5, 0.5, 9.0]], dtype=np.float32)
+    for mode in (oracle.REDUCE_SUM, oracle.REDUCE_MEAN, oracle.REDUCE_DENSITY):
+        out, cnt = oracle.range_reduce(pts, pid, qs, 0.25, pay, mode)
+        assert cnt.tolist() == [0, 0, 0]
+        assert np.array_equal(out, np.zeros((3, C), dtype=np.float32)), mode
+        ki, kd = oracle.knn_brute(pts, qs, 4, 0.25)
+        assert (ki == -1).all()
+        assert np.array_equal(oracle.knn_reduce(ki, kd, pay, mode), np.zeros((3, C), dtype=np.float32)), mode
 
 
 def test_payload_sum_float_within_rounding_bound():

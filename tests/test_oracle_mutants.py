@@ -178,6 +178,69 @@ MUTANTS = {
     "reduce_density_unsquared": [(
         "s = s / (ORC_PI_F * R2);",
         "s = s / (ORC_PI_F * sqrtf(R2));")],
+    # tree level off by one below the root (builder and traversals agree with
+    # each other, so only the pins on the tree itself can see it)
+    "level_formula": [(
+        "    while (v > 1) {",
+        "    while (v > 2) {")],
+    # widest-extent builder: the upper end of the extent never grows
+    "widest_extent_upper_end": [(
+        "            if (v > hi)",
+        "            if (v < hi)")],
+    # recursion, unordered: the right child needs the query on its side
+    "rec_unordered_right_no_overlap": [(
+        "if (sd > 0.0f || sd * sd <= orc_list_cull(T->L)) {",
+        "if (sd > 0.0f) {")],
+    # learned-radius feature: the descent splits every level in dimension 0
+    "descent_dim_zero": [(
+        "        int dim = orc_level(node) % D;",
+        "        int dim = 0;")],
+    # result emission: empty slots marked with id 0
+    "empty_slot_id_zero": [(
+        "            ids[i] = -1;\n            d2[i] = INFINITY;\n        }\n    }\n}",
+        "            ids[i] = 0;\n            d2[i] = INFINITY;\n        }\n    }\n}")],
+    # MLP forward: the first layer's bias dropped
+    "mlp_forward_b1_dropped": [(
+        "        for (int i = 0; i < H; ++i) {\n            double a = b1[i];\n            for (int j = 0; j < 4; ++j)\n"
+        "                a += W1[i * 4 + j] * xs[j];\n            h1[i] = a > 0.0 ? a : 0.0;",
+        "        for (int i = 0; i < H; ++i) {\n            double a = 0.0;\n            for (int j = 0; j < 4; ++j)\n"
+        "                a += W1[i * 4 + j] * xs[j];\n            h1[i] = a > 0.0 ? a : 0.0;")],
+    # MLP loss: the sum not divided by the sample count
+    "mlp_loss_not_mean": [(
+        "return loss / (double)n;",
+        "return loss;")],
+    # MLP backward: the first bias takes the second layer's gradient
+    "grad_b1_from_layer2": [(
+        "gb1[i] += g1[i];",
+        "gb1[i] += g2[i];")],
+    # BF16-activation forward: layer 1 rounded per operation instead of fused
+    "bf16act_layer1_unfused": [(
+        "a = fmaf(W1[i * 4 + j], xs[j], a);",
+        "a = W1[i * 4 + j] * xs[j] + a;")],
+    # ball definition: exclusive radius
+    "radius_brute_exclusive": [(
+        "            if (v <= r2) {",
+        "            if (v < r2) {")],
+    # box definition: exclusive upper corner
+    "box_brute_upper_exclusive": [(
+        "if (!(lo[q * D + j] <= v && v <= hi[q * D + j])) {",
+        "if (!(lo[q * D + j] <= v && v < hi[q * D + j])) {")],
+    # range machine: the box's right-subtree test exclusive
+    "range_box_right_exclusive": [(
+        "right_in = b[dim] >= split;",
+        "right_in = b[dim] > split;")],
+    # range machine: hit distances not stored
+    "range_d2_not_stored": [(
+        "                        d2[count] = v;\n",
+        "                        d2[count] = 0.0f;\n")],
+    # payload reductions: no special case for an empty hit set
+    "reduce_empty_not_zero": [(
+        "        if (n == 0)\n            s = 0.0f;\n        else if (mode == 1)",
+        "        if (mode == 1)")],
+    # kNN reductions: the empty slots counted as neighbours
+    "knn_reduce_counts_empty": [(
+        "while (n < k && ids[q * k + n] >= 0)",
+        "while (n < k && ids[q * k + n] >= -1)")],
     # kNN reductions: the disc through the nearest neighbour, not the farthest
     "knn_reduce_nearest_disc": [(
         "float R2 = n ? d2[q * k + n - 1] : 0.0f;",
