@@ -155,6 +155,19 @@ def test_brute_matches_numpy_definition(seed):
             assert np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
 
+@pytest.mark.parametrize("threads", [1, 3, 7, 64])
+def test_threaded_brute_equals_single_call(threads):
+    """The threaded entry splits the queries into ragged ranges (and has more
+    threads than queries at 64): the same bits as one call over all queries."""
+    g = np.random.default_rng(41)
+    pts = g.random((700, 3)).astype(np.float32)
+    qs = g.random((50, 3)).astype(np.float32)
+    for k, r in ((1, math.inf), (8, 0.1)):
+        a = oracle.knn_brute(pts, qs, k, r)
+        b = oracle.knn_brute_threaded(pts, qs, k, r, threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
+
 def test_zero_radius_returns_exact_duplicates_only():
     g = np.random.default_rng(7)
     pts = g.integers(0, 3, size=(60, 2)).astype(np.float32)
