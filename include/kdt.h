@@ -110,11 +110,16 @@ int64_t kdt_launch_count(void);
  * Synchronises `stream` once to report KDT_ENONFINITE. */
 int kdt_build(const float *d_points, int64_t N, int D, void *stream, kdt_tree **out);
 
-/* As kdt_build; opts = 0 or KDT_BUILD_ASYNC (no synchronisation). */
+/* As kdt_build; opts = 0 or a combination of KDT_BUILD_ASYNC (no
+ * synchronisation) and KDT_BUILD_WIDEST (stored split dimensions, D <= 3;
+ * KDT_EINVAL for D > 3). */
 int kdt_build_ex(const float *d_points, int64_t N, int D, int opts, void *stream, kdt_tree **out);
 
 /* Rebuild `tree` in place from new points with the same N and D, reusing its
- * device memory (a trained radius model is kept).  opts as for kdt_build_ex. */
+ * device memory (a trained radius model is kept; a payload set with
+ * kdt_tree_set_payload is dropped, as it follows the old node order).  The
+ * split-dimension rule is the tree's own (KDT_BUILD_WIDEST in opts is
+ * ignored); opts as for kdt_build_ex otherwise. */
 int kdt_rebuild(kdt_tree *tree, const float *d_points, int opts, void *stream);
 
 /* Split dimension of every level-order node: d_dims uint8 [N] (level mod D, or
