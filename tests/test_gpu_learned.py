@@ -75,6 +75,8 @@ def test_descent_features_match_oracle(kdt, surface):
     _, node_ids = kdt.kdt_tree_export(tree)
     d2 = oracle.descent_leaf_d2(pts, node_ids.cpu().numpy(), sub)
     want = np.log(np.maximum(d2, np.float32(1e-30)).astype(np.float64))
+    # same d2 bits on both sides; the device's logf (documented error 1 ulp)
+    # against FP64 log: allow about 30 FP32 ulps of the largest feature
     assert np.allclose(f[:, 3], want, rtol=0, atol=4e-6 * np.maximum(1.0, np.abs(want)).max())
 
 
@@ -88,6 +90,8 @@ def test_mlp_forward_matches_oracle(kdt):
     x = g.standard_normal((5000, 4)).astype(np.float32)
     y = kdt.kdt_mlp_forward(p, cu(x)).cpu().numpy()
     want = oracle.mlp_forward_bf16act(rounded(p).astype(np.float32), H, x)
+    # two 64-term sums accumulated in FP32 (exact BF16 products) against FP64:
+    # at most 64u each relative to the sum of magnitudes, 2 * 64u = 7.6e-6
     assert np.allclose(y, want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
     # and close to the exact model (BF16 activations change it only slightly)
     exact = oracle.mlp_forward(rounded(p), H, x.astype(np.float64))
@@ -102,6 +106,8 @@ def test_mlp_gradients_match_oracle(kdt):
     lab = g.standard_normal(n).astype(np.float32)
     loss, grad = kdt.kdt_mlp_loss_grad(p, cu(x), cu(lab))
     wl, wg = oracle.mlp_loss_grad(rounded(p), H, x.astype(np.float64), lab.astype(np.float64))
+    # FP32 sums over 1000 samples against FP64: rounding errors of random sign
+    # grow like sqrt(n) u = 2e-6 (worst case n u = 6e-5 is not approached)
     assert math.isclose(loss, wl, rel_tol=1e-5)
     scale = np.abs(wg).max()
     assert np.allclose(grad, wg, rtol=1e-4, atol=1e-5 * scale)
