@@ -2,8 +2,9 @@
 
 The proposal must never change a result: learned == plain, bit for bit.  Its
 parts are checked against the oracle: descent features (exact coordinates,
-log of the oracle's leaf distance within 2 ulp), MLP forward and gradients
-(FP64 oracle on the same BF16-rounded weights, FP32 accumulation tolerance).
+log of the oracle's leaf distance within the rounding of logf), MLP forward
+and gradients (FP64 oracle on the same BF16-rounded weights, FP32
+accumulation tolerance).
 """
 import math
 import os
