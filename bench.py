@@ -154,6 +154,19 @@ def cpu_oracle_qps(points, queries, k, n_queries, seed=5):
     return n_queries / dt, threads, idx, ids, d2
 
 
+def cpu_oracle_qps_1thread(points, queries, k, n_queries, seed=6):
+    """The same brute force in one host thread, on a smaller sample of the
+    workload's queries; returns queries/s."""
+    import oracle
+
+    oracle.ensure_built()
+    g = np.random.default_rng(seed)
+    idx = np.sort(g.choice(len(queries), size=n_queries, replace=False))
+    t0 = time.perf_counter()
+    oracle.knn_brute(points, queries[idx], k, math.inf)
+    return n_queries / (time.perf_counter() - t0)
+
+
 def reference_arm(args, world, rank):
     """The oracle timed as it stands on the host cores (rank 0 only)."""
     if rank != 0:
@@ -172,13 +185,16 @@ def reference_arm(args, world, rank):
         times.append(per_step / qps)
     ms = 1000.0 * statistics.median(times)
     value = per_step / (ms / 1000.0)
-    sample = f"{per_step} of the 2^{args.log2n} queries per step, brute force over all N points"
+    sample = (f"{per_step} of the 2^{args.log2n} queries per step, brute force over all N points, threads over "
+              "queries; value_1thread: 16 queries in one thread")
+    one = cpu_oracle_qps_1thread(pts, qs, K_NN, 16)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.log2n),
-        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "value_1thread": one},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -326,7 +342,8 @@ def main():
                                                                        wd.view(np.uint32)))
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{len(idx)} random queries of the workload, brute force over all 2^{args.log2n} points "
-                         "(plain definition, FP32), threads over queries"}
+                         "(plain definition, FP32), threads over queries; value_1thread: 16 queries in one thread",
+               "value_1thread": cpu_oracle_qps_1thread(pts, qs, K_NN, 16)}
 
     # ---- roofline of the dominant kernel (the traversal)
     peaks = {}

@@ -42,9 +42,28 @@ def test_reference_arm_prints_one_contract_line():
     assert "workload" in line["config"] and line["config"]["N"] == 1 << 12
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
+    assert cpu["value_1thread"] > 0
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_oracle_helpers_time_the_oracle():
+    """The GPU arm's CPU leg: the threaded brute force returns its sample and
+    the oracle's results for it, and the one-thread figure is a rate."""
+    import numpy as np
+
+    import bench
+    import oracle
+
+    g = np.random.default_rng(1)
+    pts = g.random((2000, 3)).astype(np.float32)
+    qs = g.random((300, 3)).astype(np.float32)
+    qps, threads, idx, wi, wd = bench.cpu_oracle_qps(pts, qs, 8, 40)
+    assert qps > 0 and threads >= 1 and len(idx) == 40 and len(set(idx.tolist())) == 40
+    bi, bd = oracle.knn_brute(pts, qs[idx], 8)
+    assert np.array_equal(wi, bi) and np.array_equal(wd, bd)
+    assert bench.cpu_oracle_qps_1thread(pts, qs, 8, 16) > 0
 
 
 def test_reference_arm_other_ranks_exit_quietly():
