@@ -154,6 +154,20 @@ def cpu_oracle_qps(points, queries, k, n_queries, seed=5):
     return n_queries / dt, threads, idx, ids, d2
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else its architecture."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def cpu_oracle_qps_1thread(points, queries, k, n_queries, seed=6):
     """The same brute force in one host thread, on a smaller sample of the
     workload's queries; returns queries/s."""
@@ -194,7 +208,7 @@ def reference_arm(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.log2n),
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads, "kind": "oracle", "sample": sample,
-                         "value_1thread": one},
+                         "value_1thread": one, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -343,7 +357,7 @@ def main():
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": threads, "kind": "oracle",
                "sample": f"{len(idx)} random queries of the workload, brute force over all 2^{args.log2n} points "
                          "(plain definition, FP32), threads over queries; value_1thread: 16 queries in one thread",
-               "value_1thread": cpu_oracle_qps_1thread(pts, qs, K_NN, 16)}
+               "value_1thread": cpu_oracle_qps_1thread(pts, qs, K_NN, 16), "cpu": cpu_model()}
 
     # ---- roofline of the dominant kernel (the traversal)
     peaks = {}

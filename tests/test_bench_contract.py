@@ -42,7 +42,7 @@ def test_reference_arm_prints_one_contract_line():
     assert "workload" in line["config"] and line["config"]["N"] == 1 << 12
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
-    assert cpu["value_1thread"] > 0
+    assert cpu["value_1thread"] > 0 and cpu["cpu"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
