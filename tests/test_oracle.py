@@ -323,6 +323,42 @@ def test_unordered_unbounded_visits_every_node_once_in_preorder(N):
     assert counts.max() <= 3
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_state_machine_steps_follow_the_three_cases(seed):
+    """Sec. 3.2: a valid node is reached first from its parent (processed,
+    then the close child), second from its close child (then the far child if
+    in range, else the parent), third from its far child (then the parent); a
+    missing node is left for its parent at once.  So in the step log every
+    processed node occurs two or three times, first after its parent, and
+    every other occurrence follows one of its children."""
+    g = np.random.default_rng(600 + seed)
+    N, D = int(g.integers(20, 300)), int(g.integers(1, 4))
+    pts = g.random((N, D)).astype(np.float32)
+    pid = oracle.build(pts)
+    for q in g.random((10, D)).astype(np.float32):
+        for k, r in ((1, math.inf), (5, math.inf), (3, 0.2)):
+            _, _, visits, steps = oracle.knn_stackfree(pts, pid, q, k, r)
+            steps = steps.tolist()
+            assert steps[0] == 0 and steps[-1] == 0
+            seen = {}
+            for i, n in enumerate(steps):
+                seen.setdefault(n, []).append(i)
+            for n, at in seen.items():
+                if n >= N:
+                    # stepped into and straight back out to the parent
+                    assert all(steps[i - 1] == (n - 1) // 2 and steps[i + 1] == (n - 1) // 2 for i in at)
+                    continue
+                assert len(at) in (2, 3), (n, at)
+                assert at[0] == 0 if n == 0 else steps[at[0] - 1] == (n - 1) // 2
+                for i in at[1:]:
+                    assert steps[i - 1] in (2 * n + 1, 2 * n + 2)
+                if len(at) == 3:
+                    # the second and third arrivals come from different children
+                    assert steps[at[1] - 1] != steps[at[2] - 1]
+            # processed nodes are exactly the valid nodes reached, in first-arrival order
+            assert visits.tolist() == [n for n in dict.fromkeys(steps) if n < N]
+
+
 def test_ordered_visit_counts_uniform_3d():
     """Batch entry agrees with per-query entry; visit counts are positive and
     the ordered traversal processes far fewer nodes than there are points."""
