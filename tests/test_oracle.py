@@ -389,6 +389,20 @@ def test_descent_leaf_is_first_leaf_of_ordered_traversal():
         assert leaf_d2[i] == np.float32(np.float32(t[0] + t[1]) + t[2])
 
 
+@pytest.mark.parametrize("N", [2, 3, 10, 255, 256, 1000])
+def test_descent_from_a_leaf_point_ends_on_it(N):
+    """With distinct coordinates every split separates strictly, so a query
+    equal to the point stored at a leaf follows the close child down to that
+    leaf (the last node N - 1 included) and finds distance 0."""
+    g = np.random.default_rng(N)
+    pts = g.random((N, 3)).astype(np.float32)
+    pid = oracle.build(pts)
+    leaves = [n for n in range(N) if 2 * n + 1 >= N]
+    assert N - 1 in leaves
+    d2 = oracle.descent_leaf_d2(pts, pid, pts[pid[leaves]])
+    assert (d2 == 0).all()
+
+
 # ---------------------------------------------------------------- MLP
 
 def test_bf16_rounding_matches_torch():

@@ -241,6 +241,51 @@ MUTANTS = {
     "knn_reduce_counts_empty": [(
         "while (n < k && ids[q * k + n] >= 0)",
         "while (n < k && ids[q * k + n] >= -1)")],
+    # widest-extent builder: the extent taken as the upper end alone
+    "widest_extent_not_difference": [(
+        "        float ext = hi - lo;",
+        "        float ext = hi;")],
+    # k-best list: the "greater" branch of the pair order dropped
+    "pair_less_missing_branch": [(
+        "    if (db < da)\n        return 0;\n",
+        "")],
+    # recursion, unordered: the left child needs the query on its side
+    "rec_unordered_left_no_overlap": [(
+        "if (sd <= 0.0f || sd * sd <= orc_list_cull(T->L)) {",
+        "if (sd <= 0.0f) {")],
+    # unordered machine: from the parent, the right child is never taken
+    # when the left one is out of range
+    "unordered_from_parent_skips_right": [(
+        "            if (from_parent)\n                next = left_in ? lc : (right_in ? rc : parent);\n"
+        "            else if (prev == lc)\n                next = right_in ? rc : parent;\n            else\n"
+        "                next = parent;\n        }\n        if (next == -1)\n            return 0;",
+        "            if (from_parent)\n                next = left_in ? lc : parent;\n"
+        "            else if (prev == lc)\n                next = right_in ? rc : parent;\n            else\n"
+        "                next = parent;\n        }\n        if (next == -1)\n            return 0;")],
+    # learned-radius feature: the descent stops one node early
+    "descent_stops_early": [(
+        "        if (child >= N)\n            break;",
+        "        if (child >= N - 1)\n            break;")],
+    # bfloat16 rounding: the tie-breaking bit taken one place too low
+    "bf16_lsb_position": [(
+        "uint32_t lsb = (u >> 16) & 1u;",
+        "uint32_t lsb = (u >> 15) & 1u;")],
+    # MLP backward: W2's gradient against the pre-activations
+    "grad_w2_preactivation": [(
+        "gW2[(int64_t)i * H + j] += g2[i] * h1[j];",
+        "gW2[(int64_t)i * H + j] += g2[i] * z1[j];")],
+    # BF16-activation forward: the hidden activations not rounded
+    "bf16act_not_rounded": [(
+        "h1[i] = (double)orc_round_bf16(a);",
+        "h1[i] = (double)a;")],
+    # payload reductions: the payload row stride dropped
+    "reduce_payload_stride": [(
+        "s = s + payload[(int64_t)hits[i] * C + c];",
+        "s = s + payload[(int64_t)hits[i] + c];")],
+    # kNN reductions: the output row stride off by one
+    "knn_reduce_output_stride": [(
+        "orc_reduce_one(payload, C, ids + q * k, n, mode, R2, out + q * C);",
+        "orc_reduce_one(payload, C, ids + q * k, n, mode, R2, out + q * (C > 1 ? C - 1 : C));")],
     # kNN reductions: the disc through the nearest neighbour, not the farthest
     "knn_reduce_nearest_disc": [(
         "float R2 = n ? d2[q * k + n - 1] : 0.0f;",
