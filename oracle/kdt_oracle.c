@@ -402,65 +402,80 @@ static void orc_rec(orc_trav *T, int64_t node)
     }
 }
 
-/* Sec. 3.2: only the current and the previous node are kept.  The ordered
- * branch follows the published step logic; the unordered branch is the same
- * machine with the child order fixed to (left, right).  With ordered == 2 a
- * node is processed when the machine comes back from its close child, and
- * the far child is then judged against the radius that processing left. */
+/* Sec. 3.2: the traversal keeps only the node it is at and the node it came
+ * from; the pair says which of three situations it is in.
+ *
+ *   arrived from the parent   the node is processed (unless ordered == 2),
+ *                             then the first child is entered if it is in
+ *                             range, else the second, else back to the parent
+ *   back from the first child the second child is entered if it is in range,
+ *                             else back to the parent
+ *   back from the second      back to the parent
+ *
+ * The two children of a node are ranked per node: the ordered traversal puts
+ * the child on the query's side of the plane first, the unordered one puts
+ * the left child first.  Either way a child is in range iff the query lies on
+ * its side of the plane or the plane is within the current cull radius, so
+ * the ordered traversal always enters its first child.  Entering a missing
+ * child (index >= N) is one step down and one straight back up.  Going up
+ * from the root ends the traversal.  With ordered == 2 a node is processed
+ * when the machine is back from its first child, and the second child is then
+ * judged against the radius that processing left. */
+enum { ORC_FROM_PARENT, ORC_FROM_FIRST, ORC_FROM_SECOND };
+
+/* whether the machine enters `child` of a node whose plane lies at signed
+ * distance sd from the query (sd > 0: the query is on the right) */
+static int orc_enters(const orc_trav *T, int64_t child, int64_t left, float sd)
+{
+    int query_side = child == left ? sd <= 0.0f : sd > 0.0f;
+    return query_side || sd * sd <= orc_list_cull(T->L);
+}
+
 static int orc_stackfree(orc_trav *T)
 {
-    int64_t curr = 0;
-    int64_t prev = -1;
-    int64_t cap = 3 * (2 * T->N + 1) + 8;
-    for (int64_t step = 0; step < cap; ++step) {
-        orc_log(T->steps, &T->nsteps, T->scap, curr);
-        int64_t parent = (curr + 1) / 2 - 1;
-        if (curr >= T->N) {
-            prev = curr;
-            curr = parent;
+    int64_t at = 0;
+    int64_t from = -1;
+    int64_t bound = 3 * (2 * T->N + 1) + 8;
+    for (int64_t step = 0; step < bound; ++step) {
+        orc_log(T->steps, &T->nsteps, T->scap, at);
+        int64_t up = at == 0 ? -1 : (at - 1) / 2;
+        if (at >= T->N) {
+            from = at;
+            at = up;
             continue;
         }
-        int from_parent = prev < curr;
-        if (from_parent && T->ordered != 2)
-            orc_process(T, curr);
-        float cull = orc_list_cull(T->L);
-        int dim = orc_split_dim(T, curr);
-        float split = T->pts[(int64_t)T->node_pid[curr] * T->D + dim];
-        float sd = T->q[dim] - split;
-        int64_t next;
-        if (T->ordered) {
-            int close_side = sd > 0.0f;
-            int64_t close_child = 2 * curr + 1 + close_side;
-            int64_t far_child = 2 * curr + 2 - close_side;
-            if (from_parent) {
-                next = close_child;
-            } else if (prev == close_child) {
-                if (T->ordered == 2) {
-                    orc_process(T, curr);
-                    cull = orc_list_cull(T->L);
-                }
-                next = sd * sd <= cull ? far_child : parent;
-            } else {
-                next = parent;
-            }
-        } else {
-            int64_t lc = 2 * curr + 1;
-            int64_t rc = 2 * curr + 2;
-            int left_in = sd <= 0.0f || sd * sd <= cull;
-            int right_in = sd > 0.0f || sd * sd <= cull;
-            if (from_parent)
-                next = left_in ? lc : (right_in ? rc : parent);
-            else if (prev == lc)
-                next = right_in ? rc : parent;
-            else
-                next = parent;
+        int dim = orc_split_dim(T, at);
+        float sd = T->q[dim] - T->pts[(int64_t)T->node_pid[at] * T->D + dim];
+        int64_t left = 2 * at + 1;
+        int64_t right = left + 1;
+        int64_t first = T->ordered && sd > 0.0f ? right : left;
+        int64_t second = first == left ? right : left;
+        int arrival = from == up ? ORC_FROM_PARENT : (from == first ? ORC_FROM_FIRST : ORC_FROM_SECOND);
+        int64_t next = up;
+        switch (arrival) {
+        case ORC_FROM_PARENT:
+            if (T->ordered != 2)
+                orc_process(T, at);
+            if (orc_enters(T, first, left, sd))
+                next = first;
+            else if (orc_enters(T, second, left, sd))
+                next = second;
+            break;
+        case ORC_FROM_FIRST:
+            if (T->ordered == 2)
+                orc_process(T, at);
+            if (orc_enters(T, second, left, sd))
+                next = second;
+            break;
+        default: /* ORC_FROM_SECOND */
+            break;
         }
-        if (next == -1)
+        if (next < 0)
             return 0;
-        prev = curr;
-        curr = next;
+        from = at;
+        at = next;
     }
-    return -1; /* step cap exceeded: cannot happen for a correct machine */
+    return -1; /* step bound exceeded: cannot happen for a correct machine */
 }
 
 static int orc_knn_tree(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,

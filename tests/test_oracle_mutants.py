@@ -91,40 +91,47 @@ MUTANTS = {
          "        orc_rec(T, far_child);\n"),
         ("            orc_rec(T, far_child);\n",
          "            orc_rec(T, close_child);\n")],
-    # stack-free machine: close side flips on sd == 0
+    # stack-free machine: the close side flips on sd == 0
     "stackfree_close_side_ge": [(
-        "int close_side = sd > 0.0f;\n            int64_t close_child = 2 * curr + 1 + close_side;",
-        "int close_side = sd >= 0.0f;\n            int64_t close_child = 2 * curr + 1 + close_side;")],
-    # stack-free machine: the far child computed as the close child
-    "stackfree_far_is_close": [(
-        "int64_t far_child = 2 * curr + 2 - close_side;",
-        "int64_t far_child = 2 * curr + 1 + close_side;")],
-    # stack-free machine: the far-child cull exclusive
+        "int64_t first = T->ordered && sd > 0.0f ? right : left;",
+        "int64_t first = T->ordered && sd >= 0.0f ? right : left;")],
+    # stack-free machine: the second child taken as the right one always
+    "stackfree_second_always_right": [(
+        "int64_t second = first == left ? right : left;",
+        "int64_t second = right;")],
+    # stack-free machine: the cull test exclusive
     "stackfree_cull_exclusive": [(
-        "next = sd * sd <= cull ? far_child : parent;",
-        "next = sd * sd < cull ? far_child : parent;")],
-    # stack-free machine: parent index wrong at the root
+        "return query_side || sd * sd <= orc_list_cull(T->L);",
+        "return query_side || sd * sd < orc_list_cull(T->L);")],
+    # stack-free machine: the query's side of the plane swapped
+    "stackfree_side_swapped": [(
+        "int query_side = child == left ? sd <= 0.0f : sd > 0.0f;",
+        "int query_side = child == left ? sd > 0.0f : sd <= 0.0f;")],
+    # stack-free machine: the root's parent index (C division rounds -1/2 to 0)
     "stackfree_parent_formula": [(
-        "        orc_log(T->steps, &T->nsteps, T->scap, curr);\n        int64_t parent = (curr + 1) / 2 - 1;",
-        "        orc_log(T->steps, &T->nsteps, T->scap, curr);\n        int64_t parent = (curr - 1) / 2;")],
+        "int64_t up = at == 0 ? -1 : (at - 1) / 2;",
+        "int64_t up = (at - 1) / 2;")],
+    # stack-free machine: back from the second child read as back from the first
+    "stackfree_arrival_second": [(
+        "(from == first ? ORC_FROM_FIRST : ORC_FROM_SECOND)",
+        "(from == second ? ORC_FROM_FIRST : ORC_FROM_SECOND)")],
     # close-first machine: processing on arrival switched off for the wrong
     # variant.  (Judging the far child against the radius from before the
     # node was processed is not a mistake a pin can catch: the node lies on
     # its own splitting plane, so its distance is at least fl(sd^2), and
     # accepting it never shrinks the radius below fl(sd^2).)
     "close_first_flag_typo": [(
-        "if (from_parent && T->ordered != 2)",
-        "if (from_parent && T->ordered != 1)")],
-    # unordered machine: the right child needs the query on its side
-    "unordered_right_no_overlap": [(
-        "int right_in = sd > 0.0f || sd * sd <= cull;",
-        "int right_in = sd > 0.0f;")],
-    # unordered machine: no step from the left child to the right one
-    "unordered_skips_right_after_left": [(
-        "            else if (prev == lc)\n                next = right_in ? rc : parent;\n            else\n"
-        "                next = parent;\n        }\n        if (next == -1)\n            return 0;",
-        "            else if (prev == lc)\n                next = parent;\n            else\n"
-        "                next = parent;\n        }\n        if (next == -1)\n            return 0;")],
+        "            if (T->ordered != 2)\n                orc_process(T, at);",
+        "            if (T->ordered != 1)\n                orc_process(T, at);")],
+    # stack-free machine: a child needs the query on its side (no overlap test)
+    "stackfree_no_overlap": [(
+        "return query_side || sd * sd <= orc_list_cull(T->L);",
+        "return query_side;")],
+    # stack-free machine: no step from the first child to the second one
+    "stackfree_skips_second_after_first": [(
+        "            if (orc_enters(T, second, left, sd))\n                next = second;\n            break;\n"
+        "        default:",
+        "            break;\n        default:")],
     # learned-radius feature: the descent goes to the far child
     "descent_far_child": [(
         "int64_t child = 2 * node + 1 + (sd > 0.0f);",
@@ -253,15 +260,11 @@ MUTANTS = {
     "rec_unordered_left_no_overlap": [(
         "if (sd <= 0.0f || sd * sd <= orc_list_cull(T->L)) {",
         "if (sd <= 0.0f) {")],
-    # unordered machine: from the parent, the right child is never taken
-    # when the left one is out of range
-    "unordered_from_parent_skips_right": [(
-        "            if (from_parent)\n                next = left_in ? lc : (right_in ? rc : parent);\n"
-        "            else if (prev == lc)\n                next = right_in ? rc : parent;\n            else\n"
-        "                next = parent;\n        }\n        if (next == -1)\n            return 0;",
-        "            if (from_parent)\n                next = left_in ? lc : parent;\n"
-        "            else if (prev == lc)\n                next = right_in ? rc : parent;\n            else\n"
-        "                next = parent;\n        }\n        if (next == -1)\n            return 0;")],
+    # unordered machine: from the parent, the second (right) child is never
+    # taken when the first one is out of range
+    "unordered_from_parent_skips_second": [(
+        "            else if (orc_enters(T, second, left, sd))\n                next = second;\n",
+        "")],
     # learned-radius feature: the descent stops one node early
     "descent_stops_early": [(
         "        if (child >= N)\n            break;",
