@@ -245,10 +245,13 @@ int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_queries
  * process exits), so Q is limited to KDT_STATIC_MAX_Q per call; larger Q gives
  * KDT_EINVAL.  KDT_LEARNED is not accepted.  Same arguments, results and
  * flags as kdt_knn otherwise.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call reuses the same array: calls whose GPU work overlaps (other streams,
- * other host threads) race and must be serialised. */
+ * Every call looks up the array's device address in the current device's
+ * context (cudaGetSymbolAddress, which allocates nothing); on a device whose
+ * module is not loaded yet, make the first call before any stream capture.
+ * Every call reuses the same array: calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised.  The work counter
+ * is cleared by each call; the rest is overwritten before it is read.
+ * kdt_profile_enable / kdt_profile_read do not time these calls. */
 #define KDT_STATIC_MAX_Q (1 << 18)
 int kdt_knn_static(const kdt_tree *tree, const float *d_queries, int64_t Q, int k, float max_radius,
                    int flags, int32_t *d_ids, float *d_d2, void *stream);
@@ -399,6 +402,18 @@ int kdt_set_inline_depth(kdt_tree *tree, int depth);
  * restores the tuned or default value.  Range 1..64.  Results and processed
  * nodes are the same for every value. */
 int kdt_set_light_run(kdt_tree *tree, int steps);
+
+/* Heavy-step quorum of the traversal (no paper counterpart: a scheduling
+ * choice of the GPU kernel).  The lanes of a warp take their steps in turns
+ * of one kind: a turn is heavy (only the lanes whose next step enters a node
+ * whose bottom subtree is processed whole take it) once at least eighths / 8
+ * of the warp's live lanes are ready for one, or all are; otherwise only the
+ * other lanes take a light step.  0 lets every lane step every turn; -1
+ * restores the tuned or default value.  Range -1..8.  Results and processed
+ * nodes are the same for every value.  kdt_heavy_quorum returns the value
+ * kdt_knn uses for this tree and k. */
+int kdt_set_heavy_quorum(kdt_tree *tree, int eighths);
+int kdt_heavy_quorum(const kdt_tree *tree, int k, int *eighths);
 
 /* The launch parameters kdt_knn uses for this tree and k: set on the tree,
  * else tuned for its shape (kdt_autotune / kdt_tuning_load), else defaults

@@ -219,12 +219,33 @@ struct Carve {
     }
 };
 
-inline size_t carve_size(std::initializer_list<size_t> bytes)
+constexpr size_t carve_size(std::initializer_list<size_t> bytes)
 {
     size_t s = 0;
     for (size_t b : bytes)
         s += (b + 255) & ~(size_t)255;
     return s;
+}
+
+// Tile sizes of the device-wide scan and radix sort (kdt_sort.cu), here so
+// that scratch sizes can be computed at compile time.
+constexpr int SCAN_TILE_ELEMS = 2048;   // elements per tile of the exclusive scan
+constexpr int RADIX_TILE_KEYS = 2048;   // keys per tile of the radix sort
+constexpr size_t scan_scratch_elems_of(int64_t n)
+{
+    return (size_t)((n + SCAN_TILE_ELEMS - 1) / SCAN_TILE_ELEMS) + 1;
+}
+constexpr size_t radix_scratch_elems_of(int64_t n)
+{
+    const int64_t tiles = (n + RADIX_TILE_KEYS - 1) / RADIX_TILE_KEYS;
+    const size_t h = (size_t)256 * (size_t)(tiles > 1 ? tiles : 1);
+    return h + scan_scratch_elems_of((int64_t)h);
+}
+// Morton keys, permutation and two sort temporaries of Q u32 each, plus the
+// radix sort's histograms and scan partials
+constexpr size_t morton_scratch_bytes_of(int64_t Q)
+{
+    return carve_size({(size_t)Q * 4, (size_t)Q * 4, (size_t)Q * 4, (size_t)Q * 4, radix_scratch_elems_of(Q) * 4});
 }
 
 
@@ -273,6 +294,9 @@ struct kdt_tree {
     int inline_depth = -1;
     // steps a lane may take per call while they are light (-1: tuned or 1)
     int light_run = -1;
+    // heavy-step quorum of the traversal's turns in eighths of a warp's live
+    // lanes (0: every lane steps every turn; -1: tuned or default)
+    int quorum8 = -1;
     // test hook: traversal step bound (0: 3N + 3)
     uint32_t debug_step_cap = 0;
     // per-point payload in node order [N][payload_c] and node_of[input index]
@@ -311,6 +335,7 @@ int claim_steps_for(const kdt_tree *t, int k);
 int default_claim_steps_k(int k);
 int inline_depth_for(const kdt_tree *t, int k);
 int light_run_for(const kdt_tree *t, int k);
+int quorum_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,
 // D <= 3), stored in the node (layout 3); else level mod D

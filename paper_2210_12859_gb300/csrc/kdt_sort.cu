@@ -15,10 +15,12 @@ namespace {
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+static_assert(SCAN_TILE == SCAN_TILE_ELEMS, "scan tile and the scratch-size formula disagree");
 
 constexpr int RADIX_THREADS = 256;
 constexpr int RADIX_ITEMS = 8;
 constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;
+static_assert(RADIX_TILE == RADIX_TILE_KEYS, "radix tile and the scratch-size formula disagree");
 constexpr int RADIX_WARPS = RADIX_THREADS / 32;
 
 template <typename T>
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) radix_scatter_kernel(
 
 size_t scan_scratch_elems(int64_t n)
 {
-    return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1;
+    return scan_scratch_elems_of(n);
 }
 
 int exclusive_scan_u32(uint32_t *data, int64_t n, uint32_t *scratch, cudaStream_t s)
@@ -236,9 +238,7 @@ int exclusive_scan_u64(unsigned long long *data, int64_t n, unsigned long long *
 
 size_t radix_scratch_elems(int64_t n)
 {
-    int64_t tiles = (n + RADIX_TILE - 1) / RADIX_TILE;
-    size_t h = (size_t)256 * (size_t)std::max<int64_t>(tiles, 1);
-    return h + scan_scratch_elems((int64_t)h);
+    return radix_scratch_elems_of(n);
 }
 
 int radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k, uint32_t *tmp_v, int64_t n, int bits,

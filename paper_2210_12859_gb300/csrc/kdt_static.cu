@@ -14,8 +14,6 @@
 // work counter) and overwrites the rest before reading it.  Two calls whose
 // work overlaps on the GPU (different streams, or host threads racing) use
 // the same bytes and race; serialise them.
-#include <mutex>
-
 #include "kdt_query.cuh"
 
 namespace kdt {
@@ -25,38 +23,25 @@ namespace {
 
 constexpr int64_t STATIC_MAX_Q = KDT_STATIC_MAX_Q;
 constexpr size_t STATIC_COUNTER_BYTES = 256;
-// four u32 arrays of Q entries (keys, permutation, two sort temporaries) plus
-// the radix histograms (256 per 2048-key tile) and their scan partials, each
-// piece rounded up to 256 bytes, plus the counter block
-constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t STATIC_TILES = (size_t)(STATIC_MAX_Q + 2047) / 2048;
-constexpr size_t STATIC_BYTES =
-    STATIC_COUNTER_BYTES + 4 * round256((size_t)STATIC_MAX_Q * 4) +
-    round256((256 * STATIC_TILES + (256 * STATIC_TILES + 2047) / 2048 + 1) * 4) + 256;
+// the work counter block, then the Morton keys, permutation and radix-sort
+// temporaries of the largest call (the same formula run_query sizes its
+// scratch with, evaluated at compile time)
+constexpr size_t STATIC_BYTES = STATIC_COUNTER_BYTES + morton_scratch_bytes_of(STATIC_MAX_Q);
+static_assert(STATIC_BYTES < (size_t)8 << 20, "static scratch grew beyond its documented few MB");
 
 __device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
 
-std::mutex g_mu;
-void *g_addr[64] = {nullptr};
-
-// Device address of g_static_scratch on the current device.  In host code the
-// symbol name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// Device address of g_static_scratch in the current device's context.  In
+// host code the symbol name is only a host-side stand-in, so the address is
+// looked up on every call (cheap, allocates nothing) rather than cached: a
+// cached pointer would go stale if the context were torn down and recreated.
 int static_scratch(void **out)
 {
-    int dev = 0;
-    KDT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64)
-        return set_error(KDT_EINVAL, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+        return cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
+    *out = p;
     return KDT_OK;
 }
 
@@ -111,6 +96,7 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
+    a.quorum8 = quorum_for(t, k);
     a.step_cap = t->debug_step_cap;
     a.inline_depth = inline_depth_for(t, k) == 2 ? 2 : 1;  // depth 0 is plain-query only
     return launch_query(t->layout, a, !(flags & KDT_UNORDERED), MODE_RESULTS, false, s);

@@ -31,6 +31,8 @@ def lib():
     L.kdt_knn_static.argtypes = [P, P, I64, I, F, I, P, P, P]
     L.kdt_knn_static.restype = I
     L.kdt_last_error.restype = ctypes.c_char_p
+    L.kdt_debug_fail_allocs.argtypes = [I]
+    L.kdt_debug_fail_allocs.restype = I
     return L, kdt
 
 
@@ -76,3 +78,47 @@ def test_static_rejects_too_many_queries(lib):
                           ctypes.c_void_p(out_i.data_ptr()), ctypes.c_void_p(out_d.data_ptr()), None)
     assert rc == kdt.KDT_EINVAL
     assert b"at most" in L.kdt_last_error()
+
+
+def test_static_allocates_nothing(lib):
+    """With the library's allocation hook armed, any device allocation the
+    call made would fail with KDT_ENOMEM; the static entry point must succeed
+    (and the same call through kdt_knn, which allocates its scratch, must
+    fail, which shows the hook is armed)."""
+    L, kdt = lib
+    pts, qs = synth.uniform_small(1 << 12, 5000)
+    tree = kdt.kdt_build(torch.from_numpy(pts).cuda())
+    dq = torch.from_numpy(qs).cuda()
+    want_i, want_d = kdt.kdt_knn(tree, dq, 8, math.inf, kdt.KDT_MORTON)
+    torch.cuda.synchronize()
+    try:
+        assert L.kdt_debug_fail_allocs(1) == 0
+        gi, gd = static_knn(L, tree, dq, 8, math.inf, kdt.KDT_MORTON | kdt.KDT_COST_ORDER)
+        torch.cuda.synchronize()
+        with pytest.raises(kdt.KdtError) as e:
+            kdt.kdt_knn(tree, dq, 8, math.inf, kdt.KDT_MORTON)
+        assert e.value.code == kdt.KDT_ENOMEM
+    finally:
+        L.kdt_debug_fail_allocs(0)
+    assert torch.equal(gi, want_i)
+    assert torch.equal(gd.view(torch.int32), want_d.view(torch.int32))
+    kdt.kdt_status(tree)
+
+
+def test_static_at_max_queries(lib):
+    """Q = KDT_STATIC_MAX_Q, the size the fixed scratch array is dimensioned
+    for, with the cost-class Morton order (the largest scratch use)."""
+    L, kdt = lib
+    pts, _ = synth.uniform_small(1 << 16, 1)
+    Q = kdt.KDT_STATIC_MAX_Q
+    qs = synth.uniform_small(1, Q, seed=synth.BASE_SEED + 991)[1]
+    tree = kdt.kdt_build(torch.from_numpy(pts).cuda())
+    dq = torch.from_numpy(qs).cuda()
+    flags = kdt.KDT_MORTON | kdt.KDT_COST_ORDER
+    want_i, want_d = kdt.kdt_knn(tree, dq, 8, math.inf, flags)
+    for _ in range(2):
+        gi, gd = static_knn(L, tree, dq, 8, math.inf, flags)
+        torch.cuda.synchronize()
+        assert torch.equal(gi, want_i)
+        assert torch.equal(gd.view(torch.int32), want_d.view(torch.int32))
+    kdt.kdt_status(tree)
