@@ -403,18 +403,6 @@ int kdt_set_inline_depth(kdt_tree *tree, int depth);
  * nodes are the same for every value. */
 int kdt_set_light_run(kdt_tree *tree, int steps);
 
-/* Heavy-step quorum of the traversal (no paper counterpart: a scheduling
- * choice of the GPU kernel).  The lanes of a warp take their steps in turns
- * of one kind: a turn is heavy (only the lanes whose next step enters a node
- * whose bottom subtree is processed whole take it) once at least eighths / 8
- * of the warp's live lanes are ready for one, or all are; otherwise only the
- * other lanes take a light step.  0 lets every lane step every turn; -1
- * restores the tuned or default value.  Range -1..8.  Results and processed
- * nodes are the same for every value.  kdt_heavy_quorum returns the value
- * kdt_knn uses for this tree and k. */
-int kdt_set_heavy_quorum(kdt_tree *tree, int eighths);
-int kdt_heavy_quorum(const kdt_tree *tree, int k, int *eighths);
-
 /* The launch parameters kdt_knn uses for this tree and k: set on the tree,
  * else tuned for its shape (kdt_autotune / kdt_tuning_load), else defaults
  * (no staging, 32 claim steps for k = 1 and 64 otherwise, inline depth 2,

@@ -246,7 +246,6 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
-    a.quorum8 = quorum_for(t, k);
     a.step_cap = t->debug_step_cap;
     a.inline_depth = inline_depth_for(t, k);
     cudaEvent_t stop;

@@ -294,9 +294,6 @@ struct kdt_tree {
     int inline_depth = -1;
     // steps a lane may take per call while they are light (-1: tuned or 1)
     int light_run = -1;
-    // heavy-step quorum of the traversal's turns in eighths of a warp's live
-    // lanes (0: every lane steps every turn; -1: tuned or default)
-    int quorum8 = -1;
     // test hook: traversal step bound (0: 3N + 3)
     uint32_t debug_step_cap = 0;
     // per-point payload in node order [N][payload_c] and node_of[input index]
@@ -335,7 +332,6 @@ int claim_steps_for(const kdt_tree *t, int k);
 int default_claim_steps_k(int k);
 int inline_depth_for(const kdt_tree *t, int k);
 int light_run_for(const kdt_tree *t, int k);
-int quorum_for(const kdt_tree *t, int k);
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,
 // D <= 3), stored in the node (layout 3); else level mod D

@@ -96,7 +96,6 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     a.staged = (flags & KDT_NO_STAGE) ? 0 : staged_for_levels(t->N, stage_levels_for(t, k));
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
-    a.quorum8 = quorum_for(t, k);
     a.step_cap = t->debug_step_cap;
     a.inline_depth = inline_depth_for(t, k) == 2 ? 2 : 1;  // depth 0 is plain-query only
     return launch_query(t->layout, a, !(flags & KDT_UNORDERED), MODE_RESULTS, false, s);
