@@ -387,12 +387,15 @@ int kdt_set_stage_levels(kdt_tree *tree, int levels);
  * otherwise).  Range 1..256. */
 int kdt_set_claim_steps(kdt_tree *tree, int steps);
 
-/* Depth of the bottom subtrees one traversal step processes whole, with all
- * their loads issued at once: 2 (default) saves steps on long queries, 1
- * avoids loads that short queries rarely use, 0 selects the simplest kernel
- * (one node per step; ordered kNN with k <= 16 and D <= 4 without staging,
- * else depth 1 is used); -1 restores the tuned or default value.  Results and
- * processed nodes are the same for every depth. */
+/* Depth of the bottom subtrees one traversal step processes whole, with their
+ * loads issued together: 2 (default) saves steps on long queries; 3 also
+ * takes the node above two such subtrees into the same step (the second
+ * subtree's loads issued when the traversal enters it), saving the steps
+ * between them; 1 avoids loads that short queries rarely use; 0 selects the
+ * simplest kernel (one node per step; ordered kNN with k <= 16 and D <= 4
+ * without staging, else depth 1 is used); -1 restores the tuned or default
+ * value.  Staged launches use depth 2.  Results and processed nodes are the
+ * same for every depth. */
 int kdt_set_inline_depth(kdt_tree *tree, int depth);
 
 /* Traversal steps a lane may take in one call while they are light (a heavy

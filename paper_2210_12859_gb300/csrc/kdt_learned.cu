@@ -481,7 +481,7 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
     a.step_cap = t->debug_step_cap;
-    a.inline_depth = inline_depth_for(t, k) == 2 ? 2 : 1;  // depth 0 is plain-query only
+    a.inline_depth = inline_depth_for(t, k) >= 2 ? inline_depth_for(t, k) : 1;  // depth 0 is plain-query only
     a.r2q = r2q;
     a.fb_count = (unsigned long long *)t->stats;
     a.ratio_sum = (double *)(t->stats + 1);

@@ -27,7 +27,7 @@ struct QueryArgs {
     int *err = nullptr;
     int staged = 0;                    // nodes staged in shared memory
     int claim_steps = STEPS_PER_CLAIM; // traversal steps a lane takes between two claim rounds
-    int inline_depth = 2;              // bottom-subtree depth processed within one step (1 or 2)
+    int inline_depth = 2;              // bottom-subtree depth processed within one step (1, 2 or 3)
     int threads = 0;                   // block size of the forest kernel (0: the kernel's default)
     int light_run = 1;                 // steps a lane may take per call while they are light
     uint32_t step_cap = 0;             // traversal step bound (0: 3N + 3; a test hook lowers it)

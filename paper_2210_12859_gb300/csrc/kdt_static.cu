@@ -97,6 +97,6 @@ extern "C" int kdt_knn_static(const kdt_tree *t, const float *d_q, int64_t Q, in
     a.claim_steps = claim_steps_for(t, k);
     a.light_run = light_run_for(t, k);
     a.step_cap = t->debug_step_cap;
-    a.inline_depth = inline_depth_for(t, k) == 2 ? 2 : 1;  // depth 0 is plain-query only
+    a.inline_depth = inline_depth_for(t, k) >= 2 ? inline_depth_for(t, k) : 1;  // depth 0 is plain-query only
     return launch_query(t->layout, a, !(flags & KDT_UNORDERED), MODE_RESULTS, false, s);
 }

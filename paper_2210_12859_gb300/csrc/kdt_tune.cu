@@ -8,9 +8,9 @@
 //     warp (long runs amortise the warp vote; a lane whose query has ended
 //     waits for the round);
 //   * inline_depth: depth of the bottom subtrees one step processes whole
-//     (2 saves steps on long queries; 1 avoids the extra up-front loads that
-//     short queries rarely use; 0 selects the simplest kernel, one node per
-//     step, where it applies: ordered, k <= 16, D <= 4, no staging);
+//     (2 or 3 save steps on long queries; 1 avoids the extra up-front loads
+//     that short queries rarely use; 0 selects the simplest kernel, one node
+//     per step, where it applies: ordered, k <= 16, D <= 4, no staging);
 //   * light_run: steps a lane takes per call while they are light, so that
 //     the heavy steps (whole bottom subtrees) of a warp's lanes coincide
 //     (1 for long queries; 4 or 8 pay for short ones).
@@ -171,8 +171,8 @@ int kdt_set_inline_depth(kdt_tree *t, int depth)
 {
     if (!t)
         return set_error(KDT_EINVAL, "tree is NULL");
-    if (depth < -1 || depth > 2)
-        return set_error(KDT_EINVAL, "depth must be -1, 0, 1 or 2 (got %d)", depth);
+    if (depth < -1 || depth > 3)
+        return set_error(KDT_EINVAL, "depth must be -1, 0, 1, 2 or 3 (got %d)", depth);
     t->inline_depth = depth;
     return KDT_OK;
 }
@@ -256,7 +256,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     };
     const bool simple_ok = !(flags & KDT_UNORDERED) && k <= 16 && t->layout != 2;
     consider(best, 0.f);
-    for (int d : {1, 0}) {
+    for (int d : {3, 1, 0}) {
         Tuned c = best;
         c.inline_depth = d;
         if (rc == KDT_OK && (d > 0 || simple_ok))
@@ -358,7 +358,7 @@ int kdt_tuning_load(const char *path)
         const char *d = strstr(ge, "\"inline_depth\": ");
         const char *r = strstr(ge, "\"light_run\": ");
         if ((c && (sscanf(c + 15, "%d", &cs) != 1 || cs < 1 || cs > 256)) ||
-            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 2)) ||
+            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 3)) ||
             (r && (sscanf(r + 13, "%d", &lr) != 1 || lr < 1 || lr > 64))) {
             bad = true;
             break;
