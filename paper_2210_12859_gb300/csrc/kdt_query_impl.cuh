@@ -260,6 +260,8 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
         return launch_mode<LAYOUT, K, false, 1>(a, ordered, mode, threads, smem, s);
     if (a.inline_depth == 3)
         return launch_mode<LAYOUT, K, false, 3>(a, ordered, mode, threads, smem, s);
+    if (a.inline_depth == 4)
+        return launch_mode<LAYOUT, K, false, 4>(a, ordered, mode, threads, smem, s);
     return launch_mode<LAYOUT, K, false, 2>(a, ordered, mode, threads, smem, s);
 }
 

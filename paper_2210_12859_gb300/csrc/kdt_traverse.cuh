@@ -244,9 +244,9 @@ __device__ __forceinline__ void process(const NodeVal<LAYOUT> &nd, int n, const 
 //    if in range), and the step returns to the parent - the same processed
 //    nodes in the same order, without the steps into and out of them.
 // Depth of the bottom subtrees processed inside one step (1: a node whose
-// children are leaves; 2: also a node whose grandchildren are leaves; 3: also
-// a node whose great-grandchildren are leaves, as its two depth-2 halves, the
-// second loaded only when the machine enters it).  Depth 2 pays when queries
+// children are leaves; 2: also a node whose grandchildren are leaves; 3 and 4:
+// also a node whose subtree below is three or four levels deep, as blocks of
+// depth 2 whose seven loads are issued when the machine enters them).  Depth 2 pays when queries
 // process many nodes; for short queries the four extra up-front loads cost
 // more than the steps they save, and depth 1 is faster; depth 3 saves the two
 // steps between the halves (the tuner measures which).
@@ -327,17 +327,18 @@ struct Walker {
             eager_leaf_pair(sdc, __fmul_rn(sdc, sdc), lcc, ka, kb, N, list, visits);
     }
 
-    // The subtree below a node x of depth 1 or 2 (x's children exist, their
-    // children are leaves or missing) as scalars: the keys of x's two children
-    // and four grandchildren and the children's split offsets.  The six node
-    // indices follow from x alone, so all loads are issued first (indices
-    // clamped to N - 1; values of missing nodes are never used).  dim1: the
-    // split dimension of x's children (level mod D).
+    // The subtree below a node x of depth at most 2 (x's grandchildren are
+    // leaves or missing) as scalars: the keys of x's two children and four
+    // grandchildren and the children's split offsets.  The six node indices
+    // follow from x alone, so all loads are issued first (indices clamped to
+    // N - 1; values of missing nodes are never used).  dim1: the split
+    // dimension of x's children (level mod D).  LEAF_OK: x may be a leaf
+    // (else its left child is known to exist).
     struct Below2 {
         unsigned long long k_c0, k_c1, k_g00, k_g01, k_g10, k_g11;
         float sdc0, sdc1;
     };
-    template <bool STAGE>
+    template <bool STAGE, bool LEAF_OK>
     __device__ __forceinline__ static Below2 load_below2(int x, int dim1, const float4 *__restrict__ nodes,
                                                          const int32_t *__restrict__ ids, const float4 *s_nodes,
                                                          int staged, int N, const float (&q)[NC])
@@ -345,14 +346,15 @@ struct Walker {
         const int last = N - 1;
         const int lc = 2 * x + 1, rc = lc + 1;
         const int g0 = 2 * lc + 1;
-        const NodeVal<LAYOUT> c0 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
+        const int lcx = LEAF_OK ? min(lc, last) : lc;
+        const NodeVal<LAYOUT> c0 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lcx);
         const NodeVal<LAYOUT> c1 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(rc, last));
         const NodeVal<LAYOUT> g00 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0, last));
         const NodeVal<LAYOUT> g01 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 1, last));
         const NodeVal<LAYOUT> g10 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 2, last));
         const NodeVal<LAYOUT> g11 = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, min(g0 + 3, last));
         Below2 b;
-        b.k_c0 = node_key(c0, lc, ids, q);
+        b.k_c0 = node_key(c0, lcx, ids, q);
         b.k_c1 = node_key(c1, min(rc, last), ids, q);
         b.k_g00 = node_key(g00, min(g0, last), ids, q);
         b.k_g01 = node_key(g01, min(g0 + 1, last), ids, q);
@@ -365,27 +367,83 @@ struct Walker {
     }
     // the machine's order over that subtree, x already processed, sd: x's
     // split offset
-    template <class List>
+    template <bool LEAF_OK, class List>
     __device__ __forceinline__ static void walk_below2(int x, float sd, const Below2 &b, int N, List &list,
                                                        int &visits)
     {
         const int lc = 2 * x + 1, rc = lc + 1;
-        const bool rc_ok = rc < N;
+        const bool lc_ok = !LEAF_OK || lc < N, rc_ok = rc < N;
         const float sd2 = __fmul_rn(sd, sd);
         if constexpr (ORDERED) {
             const bool right_first = sd > 0.f;
-            if (!right_first || rc_ok)
+            if (right_first ? rc_ok : lc_ok)
                 eager_leaf_parent(right_first ? rc : lc, right_first ? b.k_c1 : b.k_c0, right_first ? b.sdc1 : b.sdc0,
                                   right_first ? b.k_g10 : b.k_g00, right_first ? b.k_g11 : b.k_g01, N, list, visits);
-            if ((right_first || rc_ok) && sd2 <= list.cull())
+            if ((right_first ? lc_ok : rc_ok) && sd2 <= list.cull())
                 eager_leaf_parent(right_first ? lc : rc, right_first ? b.k_c0 : b.k_c1, right_first ? b.sdc0 : b.sdc1,
                                   right_first ? b.k_g00 : b.k_g10, right_first ? b.k_g01 : b.k_g11, N, list, visits);
         } else {
-            if (sd <= 0.f || sd2 <= list.cull())
+            if (lc_ok && (sd <= 0.f || sd2 <= list.cull()))
                 eager_leaf_parent(lc, b.k_c0, b.sdc0, b.k_g00, b.k_g01, N, list, visits);
             if (rc_ok && (sd > 0.f || sd2 <= list.cull()))
                 eager_leaf_parent(rc, b.k_c1, b.sdc1, b.k_g10, b.k_g11, N, list, visits);
         }
+    }
+
+
+    // The subtree below a processed node x of depth at most L >= 2, in the
+    // machine's order: for L = 2 the six-node block above; otherwise each
+    // child in turn (close child first, or left first unordered; a child only
+    // when it exists and is in range), its key offered and the subtree below
+    // it walked the same way.  A child's own node is loaded together with the
+    // first block below it.  dimc: the split dimension of x's children.
+    // MIN: a lower bound on the depth of x's subtree (x is a leaf only when
+    // MIN = 0); a child's subtree is at most two levels shallower than its
+    // parent's lower bound (the right one may be a level shallower than the
+    // left, which is one shallower than the parent).
+    template <int L, bool STAGE, int MIN, class List>
+    __device__ __forceinline__ static void walk_below(int x, float sd, int dimc, int D,
+                                                      const float4 *__restrict__ nodes,
+                                                      const int32_t *__restrict__ ids, const float4 *s_nodes,
+                                                      int staged, int N, const float (&q)[NC], List &list,
+                                                      int &visits)
+    {
+        if constexpr (L <= 2) {
+            walk_below2<MIN < 1>(x, sd, load_below2<STAGE, (MIN < 1)>(x, dimc, nodes, ids, s_nodes, staged, N, q), N,
+                                 list, visits);
+        } else {
+            const int lc = 2 * x + 1;
+            const int dimg = dimc + 1 == D ? 0 : dimc + 1;
+            const bool first_right = ORDERED && sd > 0.f;
+            const int fc = lc + (int)first_right, sc = lc + 1 - (int)first_right;
+            const float sd2 = __fmul_rn(sd, sd);
+            if (fc < N && (ORDERED || sd <= 0.f || sd2 <= list.cull())) {
+                const NodeVal<LAYOUT> nf = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, fc);
+                ++visits;
+                offer(list, node_key(nf, fc, ids, q));
+                const int df = split_dim_of<LAYOUT>(nf, dimc);
+                walk_below<L - 1, STAGE, (MIN >= 2 ? MIN - 2 : 0)>(fc, __fsub_rn(select_dim<NC>(q, df), select_dim<NC>(nf.c, df)), dimg, D,
+                                         nodes, ids, s_nodes, staged, N, q, list, visits);
+            }
+            if (sc < N && ((!ORDERED && sd > 0.f) || sd2 <= list.cull())) {
+                const NodeVal<LAYOUT> ns = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, sc);
+                ++visits;
+                offer(list, node_key(ns, sc, ids, q));
+                const int ds = split_dim_of<LAYOUT>(ns, dimc);
+                walk_below<L - 1, STAGE, (MIN >= 2 ? MIN - 2 : 0)>(sc, __fsub_rn(select_dim<NC>(q, ds), select_dim<NC>(ns.c, ds)), dimg, D,
+                                         nodes, ids, s_nodes, staged, N, q, list, visits);
+            }
+        }
+    }
+
+    // whether the subtree below node c is exactly L levels deep: its leftmost
+    // descendant L levels down, (c + 1) 2^L - 1, exists and the one a level
+    // further down does not
+    template <int L>
+    __device__ __forceinline__ static bool depth_is(int c, int N)
+    {
+        const uint64_t c1 = (uint64_t)c + 1ull;
+        return (c1 << L) - 1ull < (uint64_t)N && (c1 << (L + 1)) - 1ull >= (uint64_t)N;
     }
 
     // One or more steps; returns true when the traversal has finished.  With
@@ -418,42 +476,21 @@ struct Walker {
         int next;
         const int rc = lc + 1;
         const int dim1 = dim + 1 == D ? 0 : dim + 1;
-        if (INLINE >= 3 && from_parent && lc < N && 2 * lc + 1 < N && 2 * (2 * lc + 1) + 1 < N &&
-            2ull * (2ull * (2ull * (uint64_t)lc + 1ull) + 1ull) + 1ull >= (uint64_t)N) {
-            // the subtree below is three levels deep: both children (each with
-            // the depth-1 or depth-2 subtree below it) in the machine's order,
-            // each child's seven nodes loaded at once when the machine enters
-            // that child
-            const int dim2 = dim1 + 1 == D ? 0 : dim1 + 1;
-            const bool first_right = ORDERED && sd > 0.f;
-            const int fc = lc + (int)first_right, sc = lc + 1 - (int)first_right;
-            {
-                const NodeVal<LAYOUT> nf = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, fc);
-                const Below2 bf = load_below2<STAGE>(fc, dim2, nodes, ids, s_nodes, staged, N, q);
-                const bool in = ORDERED || sd <= 0.f || sd2 <= list.cull();
-                if (in) {
-                    ++visits;
-                    offer(list, node_key(nf, fc, ids, q));
-                    const int df = split_dim_of<LAYOUT>(nf, dim1);
-                    walk_below2(fc, __fsub_rn(select_dim<NC>(q, df), select_dim<NC>(nf.c, df)), bf, N, list, visits);
-                }
-            }
-            const bool in2 = (ORDERED ? false : sd > 0.f) || sd2 <= list.cull();
-            if (in2) {
-                const NodeVal<LAYOUT> ns = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, sc);
-                const Below2 bs = load_below2<STAGE>(sc, dim2, nodes, ids, s_nodes, staged, N, q);
-                ++visits;
-                offer(list, node_key(ns, sc, ids, q));
-                const int ds = split_dim_of<LAYOUT>(ns, dim1);
-                walk_below2(sc, __fsub_rn(select_dim<NC>(q, ds), select_dim<NC>(ns.c, ds)), bs, N, list, visits);
-            }
+        if (INLINE >= 4 && from_parent && depth_is<4>(curr, N)) {
+            // the subtree below is four levels deep: its two depth-3 halves,
+            // each as two depth-2 blocks of seven loads issued together
+            walk_below<4, STAGE, 4>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
-        } else if (INLINE >= 2 && from_parent && lc < N && 2 * lc + 1 < N &&
-                   2u * (2u * (uint32_t)lc + 1u) + 1u >= (uint32_t)N) {
+        } else if (INLINE >= 3 && from_parent && depth_is<3>(curr, N)) {
+            // three levels deep: both children (each with the depth-1 or
+            // depth-2 subtree below it) in the machine's order, each child's
+            // seven nodes loaded at once when the machine enters that child
+            walk_below<3, STAGE, 3>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
+            next = parent;
+        } else if (INLINE >= 2 && from_parent && depth_is<2>(curr, N)) {
             // the children have only leaves below them: the whole depth-2
             // subtree in the machine's order, its six loads issued first
-            walk_below2(curr, sd, load_below2<STAGE>(curr, dim1, nodes, ids, s_nodes, staged, N, q), N, list,
-                        visits);
+            walk_below<2, STAGE, 2>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
         } else if (INLINE >= 1 && from_parent && lc < N && 2 * lc + 1 >= N) {
             // both children are leaves (the right one may be missing): both
@@ -502,11 +539,8 @@ struct Walker {
             return false;
         // stop before a heavy step (entering a node whose bottom subtree is
         // processed whole), so that it starts the next call
-        const int lcn = 2 * curr + 1;
-        if (curr > prev && lcn < N &&
-            ((INLINE >= 3 && 2ull * (2ull * (2ull * (uint64_t)lcn + 1ull) + 1ull) + 1ull >= (uint64_t)N) ||
-             (INLINE == 2 && 2u * (2u * (uint32_t)lcn + 1u) + 1u >= (uint32_t)N) ||
-             (INLINE == 1 && 2 * lcn + 1 >= N)))
+        if (curr > prev && 2 * curr + 1 < N &&
+            ((((uint64_t)curr + 1ull) << (INLINE + 1)) - 1ull >= (uint64_t)N))
             return false;
       }
     }

@@ -171,8 +171,8 @@ int kdt_set_inline_depth(kdt_tree *t, int depth)
 {
     if (!t)
         return set_error(KDT_EINVAL, "tree is NULL");
-    if (depth < -1 || depth > 3)
-        return set_error(KDT_EINVAL, "depth must be -1, 0, 1, 2 or 3 (got %d)", depth);
+    if (depth < -1 || depth > 4)
+        return set_error(KDT_EINVAL, "depth must be in [-1, 4] (got %d)", depth);
     t->inline_depth = depth;
     return KDT_OK;
 }
@@ -256,7 +256,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     };
     const bool simple_ok = !(flags & KDT_UNORDERED) && k <= 16 && t->layout != 2;
     consider(best, 0.f);
-    for (int d : {3, 1, 0}) {
+    for (int d : {3, 4, 1, 0}) {
         Tuned c = best;
         c.inline_depth = d;
         if (rc == KDT_OK && (d > 0 || simple_ok))
@@ -358,7 +358,7 @@ int kdt_tuning_load(const char *path)
         const char *d = strstr(ge, "\"inline_depth\": ");
         const char *r = strstr(ge, "\"light_run\": ");
         if ((c && (sscanf(c + 15, "%d", &cs) != 1 || cs < 1 || cs > 256)) ||
-            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 3)) ||
+            (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 4)) ||
             (r && (sscanf(r + 13, "%d", &lr) != 1 || lr < 1 || lr > 64))) {
             bad = true;
             break;

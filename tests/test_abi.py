@@ -68,7 +68,7 @@ def test_tuning_file_round_trip_without_gpu(lib, tmp_path):
     assert rows["cpu-test-b"]["claim_steps"] == 128 and rows["cpu-test-b"]["inline_depth"] == 0
     assert rows["cpu-test-b"]["light_run"] == 8 and rows["cpu-test-a"]["light_run"] == 1
     for bad in ('"stage_levels": 99}', '"stage_levels": 0, "claim_steps": 0}', '"stage_levels": 0, "light_run": 0}',
-                '"stage_levels": 0, "claim_steps": 64, "inline_depth": 3}'):
+                '"stage_levels": 0, "claim_steps": 64, "inline_depth": 5}'):
         src.write_text('[\n  {"gpu": "x", "D": 3, "k_bucket": 3, "log2n": 18, ' + bad + '\n]\n')
         assert lib.kdt_tuning_load(str(src).encode()) == -7
     assert lib.kdt_tuning_load(str(tmp_path / "missing.json").encode()) == -7

@@ -49,7 +49,7 @@ def test_claim_steps_and_inline_depth_identical(kdt, k):
     dq = torch.from_numpy(qs).cuda()
     ref = kdt.kdt_knn(tree, dq, k, flags=kdt.KDT_MORTON)
     ref_v = kdt.kdt_knn_visits(tree, dq, k)
-    for depth, lr in ((0, 1), (1, 4), (2, 1), (2, 8), (1, 64), (3, 1), (3, 4)):
+    for depth, lr in ((0, 1), (1, 4), (2, 1), (2, 8), (1, 64), (3, 1), (3, 4), (4, 1)):
         for cs in (1, 7, 16, 64, 256):
             kdt.kdt_set_inline_depth(tree, depth)
             kdt.kdt_set_claim_steps(tree, cs)
@@ -59,7 +59,7 @@ def test_claim_steps_and_inline_depth_identical(kdt, k):
                 r = kdt.kdt_knn(tree, dq, k, flags=flags)
                 assert torch.equal(r[0], ref[0]) and torch.equal(r[1], ref[1]), (depth, cs, flags)
             assert torch.equal(kdt.kdt_knn_visits(tree, dq, k), ref_v)
-    for bad in ((kdt.kdt_set_inline_depth, 4), (kdt.kdt_set_claim_steps, 0), (kdt.kdt_set_claim_steps, 257),
+    for bad in ((kdt.kdt_set_inline_depth, 5), (kdt.kdt_set_claim_steps, 0), (kdt.kdt_set_claim_steps, 257),
                 (kdt.kdt_set_light_run, 0), (kdt.kdt_set_light_run, 65)):
         with pytest.raises(kdt.KdtError):
             bad[0](tree, bad[1])
@@ -77,7 +77,7 @@ def test_autotune_and_tuning_file(kdt, tmp_path):
     lv, ms = kdt.kdt_autotune(tree, dq, 8, kdt.KDT_MORTON)
     assert lv in (0, 4, 6, 8) and ms > 0
     tlv, cs, depth, lr = kdt.kdt_tuned_params(tree, 8)
-    assert tlv == lv and cs in (16, 32, 64, 128) and depth in (0, 1, 2, 3) and lr in (1, 4, 8)
+    assert tlv == lv and cs in (16, 32, 64, 128) and depth in (0, 1, 2, 3, 4) and lr in (1, 4, 8)
     path = os.path.join(tmp_path, "tuning.json")
     kdt.kdt_tuning_save(path)
     rows = json.load(open(path))
@@ -101,11 +101,13 @@ def test_autotune_and_tuning_file(kdt, tmp_path):
 
 
 @pytest.mark.parametrize("N,D,widest", [(1 << 16, 3, False), (50001, 3, False), (9, 3, False), (23, 2, False),
+                                        (47, 3, False), (24, 3, True), (1 << 17, 3, False), (98303, 2, False),
                                         (100003, 4, False), (40000, 8, False), (70001, 3, True), (131071, 1, False)])
-def test_inline_depth_three_identical(kdt, N, D, widest):
-    """The depth-3 step (a node and both depth-2 subtrees below it in one step)
-    on complete and ragged last levels, every node layout and a stored split
-    dimension: the same results and processed nodes as depth 2, both orders."""
+def test_deep_inline_depths_identical(kdt, N, D, widest):
+    """The depth-3 and depth-4 steps (a node and the whole subtree below it, as
+    depth-2 blocks, in one step) on complete and ragged last levels, every node
+    layout and a stored split dimension: the same results and processed nodes
+    as depth 2, both orders."""
     g = np.random.default_rng(N + D)
     pts = g.random((N, D), dtype=np.float32)
     qs = g.random((6000, D), dtype=np.float32) * 1.2 - 0.1
@@ -116,9 +118,11 @@ def test_inline_depth_three_identical(kdt, N, D, widest):
             kdt.kdt_set_inline_depth(tree, 2)
             want = kdt.kdt_knn(tree, dq, k, flags=flags)
             want_v = kdt.kdt_knn_visits(tree, dq, k, flags=flags)
-            kdt.kdt_set_inline_depth(tree, 3)
-            got = kdt.kdt_knn(tree, dq, k, flags=flags)
-            got_v = kdt.kdt_knn_visits(tree, dq, k, flags=flags)
-            assert torch.equal(got[0], want[0]) and torch.equal(got[1].view(torch.int32), want[1].view(torch.int32))
-            assert torch.equal(got_v, want_v), (k, flags)
+            for depth in (3, 4):
+                kdt.kdt_set_inline_depth(tree, depth)
+                got = kdt.kdt_knn(tree, dq, k, flags=flags)
+                got_v = kdt.kdt_knn_visits(tree, dq, k, flags=flags)
+                assert torch.equal(got[0], want[0]) and torch.equal(got[1].view(torch.int32),
+                                                                    want[1].view(torch.int32)), (depth, k, flags)
+                assert torch.equal(got_v, want_v), (depth, k, flags)
     kdt.kdt_status(tree)
