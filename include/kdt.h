@@ -58,12 +58,13 @@ extern "C" {
                               and re-run the queries that find fewer than k points with
                               the caller's radius (not in the paper; results unchanged) */
 #define KDT_NO_STAGE   0x8 /* do not stage the top tree levels in shared memory */
-#define KDT_COST_ORDER 0x20 /* with KDT_MORTON, single trees with D <= 3: run the queries in four
-                              cost classes, most expensive first (judged by how far the greedy
+#define KDT_COST_ORDER 0x20 /* with KDT_MORTON, single trees with D <= 3: run the queries in cost
+                              classes, most expensive first (judged by how far the greedy
                               descent ends from its leaf point, relative to the mean point
-                              spacing), Morton order within a class.  Pays when a few queries
-                              cost far more than the rest (queries outside the data); costs one
-                              descent per query */
+                              spacing: one class per power of two of that squared distance
+                              beyond 64 spacings squared, three below), Morton order within a
+                              class.  Pays when a few queries cost far more than the rest
+                              (queries outside the data); costs one descent per query */
 /* Traversal ablations (ordered kNN / fcp, k <= 16, D <= 4; at most one; not
  * with KDT_UNORDERED or KDT_LEARNED).  Same results as without them; they
  * measure the choices around Sec. 3's stack-free traversal, for which the

@@ -86,10 +86,14 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
 
 // 30-bit Morton code of the first min(D,3) coordinates quantised to 10 bits
 // inside the bounding box of the query's tree.  With `nodes` (a single tree
-// of D <= 3), the two bits above the code hold a cost class, most expensive
-// first: a query whose greedy descent ends far from its leaf point, relative
-// to the tree's mean point spacing, lies outside the data and processes many
-// nodes; starting those first keeps them out of the end of the launch.
+// of D <= 3), the key is a 5-bit cost class above a 27-bit Morton code (9 bits
+// per coordinate), most expensive class first: a query whose greedy descent
+// ends far from its leaf point, relative to the tree's mean point spacing,
+// lies outside the data and processes many nodes, more the farther it ends.
+// With r = d2(leaf) / spacing^2, queries with r > 64 are classed by
+// floor(log2 r) (larger first), the others in three classes (r > 8, r > 1,
+// the rest).  Starting the longest queries first keeps them out of the end of
+// the launch, where too few lanes are left to hide their latency.
 __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, const float *__restrict__ bbox, int T,
                               const int64_t *__restrict__ q_off, const float4 *__restrict__ nodes, int64_t N,
                               bool stored, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
@@ -116,19 +120,26 @@ __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, co
         }
         const float *bb = bbox + 6 * t;
         uint32_t code = 0;
+        const float cells = nodes ? 512.f : 1024.f;
         for (int j = 0; j < 3 && j < D; ++j) {
             float ext = bb[3 + j] - bb[j];
             float x = ext > 0.f ? (qs[i * D + j] - bb[j]) / ext : 0.f;
             x = fminf(fmaxf(x, 0.f), 1.f);
-            uint32_t c = (uint32_t)fminf(x * 1024.f, 1023.f);
+            uint32_t c = (uint32_t)fminf(x * cells, cells - 1.f);
             code |= spread3(c) << (2 - j);
         }
         if (nodes) {
             float q[3];
             load_query<0>(qs, i, D, q);
             const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q, stored) / spacing2;
-            const uint32_t cls = r > 64.f ? 0u : (r > 8.f ? 1u : (r > 1.f ? 2u : 3u));  // NaN: 3
-            code |= cls << 30;
+            uint32_t cls;
+            if (r > 64.f) {  // floor(log2 r) >= 6: classes 28 (r < 128) down to 0
+                const int e = ilogbf(r);
+                cls = (uint32_t)(28 - min(e - 6, 28));
+            } else {
+                cls = r > 8.f ? 29u : (r > 1.f ? 30u : 31u);  // NaN: 31
+            }
+            code |= cls << 27;
         }
         keys[i] = code;
         vals[i] = (uint32_t)i;
