@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch parameters instead of running its tuner first "
                          "(profiling runs whose first traversal launch must be a full one)")
+    ap.add_argument("--launch", default=None,
+                    help="inline_depth,light_run,claim_steps set on the tree instead of running the tuner "
+                         "(profiling runs that must capture the tuned kernel as the first traversal launch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--config", default="gmm_large",
                     choices=["gmm_large", "uniform_small", "dims", "surface_learned", "batched", "ablation", "range",
@@ -291,7 +294,12 @@ def main():
     stream = torch.cuda.current_stream()
     # the library's launch tuner (inline depth, claim steps, staging depth),
     # measured on 2^20 of the queries before anything is timed
-    if not args.no_tune:
+    if args.launch:
+        depth, light, claim = (int(x) for x in args.launch.split(","))
+        kdt.kdt_set_inline_depth(tree, depth)
+        kdt.kdt_set_light_run(tree, light)
+        kdt.kdt_set_claim_steps(tree, claim)
+    elif not args.no_tune:
         kdt.kdt_autotune(tree, dq, K_NN, flags)
     tuned = dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"), kdt.kdt_tuned_params(tree, K_NN)))
 
@@ -441,7 +449,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(args.log2n), **{"launch_autotuned" if not args.no_tune else "launch": tuned}),
+            "config": dict(workload_config(args.log2n),
+                           **{"launch_autotuned" if not (args.no_tune or args.launch) else "launch": tuned}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk.summary(), "bit_exact_sample": exact,
             "breakdown": {"build_ms": build_ms, "query_ms": query_ms, "query_qps": n / (query_ms / 1000.0)},
