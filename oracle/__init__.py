@@ -29,7 +29,7 @@ _lib = None
 
 # gcc flags: every float operation evaluated as written (no contraction into
 # fused multiply-add, which GCC does by default on aarch64), no fast-math.
-CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread"]
 
 
 def ensure_built(force: bool = False) -> str:
@@ -69,6 +69,8 @@ def _load():
         lib.orc_knn_reduce.restype = None
         lib.orc_build_widest.argtypes = [P, i64, i32, P, P]
         lib.orc_build_widest.restype = i32
+        lib.orc_build_par.argtypes = [P, i64, i32, P, P, i32]
+        lib.orc_build_par.restype = i32
         lib.orc_knn_stackfree_batch_dims.argtypes = [P, P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
         lib.orc_knn_stackfree_batch_dims.restype = i32
         lib.orc_knn_brute.argtypes = [P, i64, i32, P, i64, i32, f32, P, P]
@@ -109,24 +111,31 @@ def left_size(n: int) -> int:
     return int(_load().orc_left_size(int(n)))
 
 
-def build(points) -> np.ndarray:
-    """Level-order tree as node -> input index (int32[N])."""
+def build(points, threads: int = 1) -> np.ndarray:
+    """Level-order tree as node -> input index (int32[N]); threads > 1 builds
+    the subtrees of the top levels in parallel (the same tree)."""
     pts = _f32(points)
     N, D = pts.shape
     out = np.empty(N, dtype=np.int32)
-    if _load().orc_build(_ptr(pts), N, D, _ptr(out)) != 0:
+    lib = _load()
+    rc = (lib.orc_build_par(_ptr(pts), N, D, _ptr(out), None, int(threads)) if threads > 1
+          else lib.orc_build(_ptr(pts), N, D, _ptr(out)))
+    if rc != 0:
         raise ValueError("oracle build failed (bad arguments or non-finite point)")
     return out
 
 
-def build_widest(points):
+def build_widest(points, threads: int = 1):
     """Level-order tree with a stored split dimension per node (widest extent
     of the node's points): (node -> input index int32[N], dims uint8[N])."""
     pts = _f32(points)
     N, D = pts.shape
     out = np.empty(N, dtype=np.int32)
     dims = np.empty(N, dtype=np.uint8)
-    if _load().orc_build_widest(_ptr(pts), N, D, _ptr(out), _ptr(dims)) != 0:
+    lib = _load()
+    rc = (lib.orc_build_par(_ptr(pts), N, D, _ptr(out), _ptr(dims), int(threads)) if threads > 1
+          else lib.orc_build_widest(_ptr(pts), N, D, _ptr(out), _ptr(dims)))
+    if rc != 0:
         raise ValueError("oracle build failed (bad arguments or non-finite point)")
     return out, dims
 
@@ -145,6 +154,59 @@ def knn_tree_dims(points, node_pid, node_dim, queries, k, max_radius=float("inf"
     rc = _load().orc_knn_stackfree_batch_dims(_ptr(pts), _ptr(node_pid), _ptr(node_dim), N, D, _ptr(qs), Q, k,
                                               float(max_radius), int(ordered), _ptr(ids), _ptr(d2), _ptr(nv))
     if rc != 0:
+        raise RuntimeError("oracle traversal exceeded its step cap")
+    return ids, d2, nv
+
+
+def knn_tree_threaded(points, node_pid, queries, k, max_radius=float("inf"), ordered=True, node_dim=None,
+                      threads: int = 0):
+    """The stack-free traversal of many queries (level mod D, or stored split
+    dimensions with node_dim) split over host threads by query (each C call
+    releases the GIL): (ids, d2, first visits per query)."""
+    pts, qs = _f32(points), _f32(queries)
+    node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
+    dims = None if node_dim is None else np.ascontiguousarray(node_dim, dtype=np.uint8)
+    N, D = pts.shape
+    Q = qs.shape[0]
+    threads = max(1, min(threads or (os.cpu_count() or 1), max(Q, 1)))
+    ids = np.empty((Q, k), dtype=np.int32)
+    d2 = np.empty((Q, k), dtype=np.float32)
+    nv = np.empty(Q, dtype=np.int32)
+    lib = _load()
+    # interleaved chunks: expensive queries tend to sit together
+    chunk = 64
+    starts = list(range(0, Q, chunk))
+    nxt = [0]
+    lock = threading.Lock()
+    failed = []
+
+    def work():
+        while True:
+            with lock:
+                if nxt[0] >= len(starts):
+                    return
+                a = starts[nxt[0]]
+                nxt[0] += 1
+            b = min(a + chunk, Q)
+            sub = np.ascontiguousarray(qs[a:b])
+            oi = np.empty((b - a, k), dtype=np.int32)
+            od = np.empty((b - a, k), dtype=np.float32)
+            ov = np.empty(b - a, dtype=np.int32)
+            rc = lib.orc_knn_stackfree_batch_dims(_ptr(pts), _ptr(node_pid), None if dims is None else _ptr(dims), N,
+                                                  D, _ptr(sub), b - a, k, float(max_radius), int(ordered), _ptr(oi),
+                                                  _ptr(od), _ptr(ov))
+            if rc != 0:
+                failed.append(a)
+            ids[a:b] = oi
+            d2[a:b] = od
+            nv[a:b] = ov
+
+    ts = [threading.Thread(target=work) for _ in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if failed:
         raise RuntimeError("oracle traversal exceeded its step cap")
     return ids, d2, nv
 

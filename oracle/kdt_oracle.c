@@ -19,6 +19,8 @@
  *                       builder produces), round-robin split dimension
  *   orc_build_widest    the same with a stored per-node split dimension (the
  *                       other splitDimOf variant Sec. 3 names): widest extent
+ *   orc_build_par       either builder with the two subtrees of the top few
+ *                       nodes built in separate threads (the same recursion)
  *   orc_knn_brute       plain definition of the fcp / kNN result (exact method,
  *                       Sec. 3 "shrinking max radius"), FP32 distances
  *   orc_knn_brute_f64   the same selection with distances in FP64
@@ -49,6 +51,7 @@
  */
 #define _GNU_SOURCE 1 /* qsort_r */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -156,7 +159,58 @@ static int orc_build_rec(const float *pts, int64_t N, int D, int32_t *S,
     return orc_build_rec(pts, N, D, S + L + 1, n - L - 1, 2 * node + 2, node_pid, node_dim);
 }
 
-static int orc_build_any(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim)
+/* The same recursion, with the left subtree of each node in the top `spawn`
+ * levels built by a new thread while the calling thread builds the right one.
+ * The subtrees write disjoint parts of S and of the output arrays. */
+typedef struct {
+    const float *pts;
+    int64_t N;
+    int D;
+    int32_t *S;
+    int64_t n;
+    int64_t node;
+    int32_t *node_pid;
+    uint8_t *node_dim;
+    int spawn;
+    int rc;
+} orc_build_task;
+
+static void *orc_build_task_run(void *arg)
+{
+    orc_build_task *t = (orc_build_task *)arg;
+    if (t->spawn <= 0 || t->n < 4096) {
+        t->rc = orc_build_rec(t->pts, t->N, t->D, t->S, t->n, t->node, t->node_pid, t->node_dim);
+        return NULL;
+    }
+    t->rc = 0;
+    if (t->n == 0)
+        return NULL;
+    if (t->node >= t->N) {
+        t->rc = -1;
+        return NULL;
+    }
+    int dim = t->node_dim ? orc_widest_dim(t->pts, t->D, t->S, t->n) : orc_level(t->node) % t->D;
+    if (t->node_dim)
+        t->node_dim[t->node] = (uint8_t)dim;
+    orc_sort_ctx ctx = {t->pts, t->D, dim};
+    qsort_r(t->S, (size_t)t->n, sizeof(int32_t), orc_cmp_coord_idx, &ctx);
+    int64_t L = orc_left_size(t->n);
+    t->node_pid[t->node] = t->S[L];
+    orc_build_task left = {t->pts, t->N, t->D, t->S, L, 2 * t->node + 1, t->node_pid, t->node_dim, t->spawn - 1, 0};
+    orc_build_task right = {t->pts, t->N, t->D, t->S + L + 1, t->n - L - 1, 2 * t->node + 2, t->node_pid,
+                            t->node_dim, t->spawn - 1, 0};
+    pthread_t th;
+    int spawned = pthread_create(&th, NULL, orc_build_task_run, &left) == 0;
+    if (!spawned)
+        orc_build_task_run(&left);
+    orc_build_task_run(&right);
+    if (spawned)
+        pthread_join(th, NULL);
+    t->rc = (left.rc || right.rc) ? -1 : 0;
+    return NULL;
+}
+
+static int orc_build_any(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim, int threads)
 {
     if (N < 1 || D < 1 || D > 8)
         return -1;
@@ -168,7 +222,17 @@ static int orc_build_any(const float *pts, int64_t N, int D, int32_t *node_pid, 
         return -1;
     for (int64_t i = 0; i < N; ++i)
         S[i] = (int32_t)i;
-    int rc = orc_build_rec(pts, N, D, S, N, 0, node_pid, node_dim);
+    int rc;
+    if (threads > 1) {
+        int spawn = 0;
+        while ((1 << spawn) < threads && spawn < 12)
+            ++spawn;
+        orc_build_task root = {pts, N, D, S, N, 0, node_pid, node_dim, spawn, 0};
+        orc_build_task_run(&root);
+        rc = root.rc;
+    } else {
+        rc = orc_build_rec(pts, N, D, S, N, 0, node_pid, node_dim);
+    }
     free(S);
     return rc;
 }
@@ -178,7 +242,7 @@ static int orc_build_any(const float *pts, int64_t N, int D, int32_t *node_pid, 
  * non-finite coordinate. */
 int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
 {
-    return orc_build_any(pts, N, D, node_pid, NULL);
+    return orc_build_any(pts, N, D, node_pid, NULL, 1);
 }
 
 /* The same builder with the split dimension of every node stored in the node
@@ -187,7 +251,14 @@ int orc_build(const float *pts, int64_t N, int D, int32_t *node_pid)
  * node_dim[t] receives it. */
 int orc_build_widest(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim)
 {
-    return orc_build_any(pts, N, D, node_pid, node_dim);
+    return orc_build_any(pts, N, D, node_pid, node_dim, 1);
+}
+
+/* orc_build (node_dim NULL) or orc_build_widest with up to about `threads`
+ * threads building subtrees in parallel: the same tree. */
+int orc_build_par(const float *pts, int64_t N, int D, int32_t *node_pid, uint8_t *node_dim, int threads)
+{
+    return orc_build_any(pts, N, D, node_pid, node_dim, threads);
 }
 
 /* ------------------------------------------------------------------------ */

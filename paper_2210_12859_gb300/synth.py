@@ -66,6 +66,13 @@ def gmm_queries(mix: Mixture, n: int, frac_uniform: float, seed: int) -> np.ndar
     return q.astype(np.float32)
 
 
+def gmm_query_is_uniform(n: int, frac_uniform: float, seed: int) -> np.ndarray:
+    """Which of the ``gmm_queries(mix, n, frac_uniform, seed)`` queries were drawn
+    uniformly (the generator's first draw); those land between the clusters
+    (the mixture covers a small part of the cube)."""
+    return rng(seed).random(n) < frac_uniform
+
+
 @dataclass
 class Shapes:
     kind: np.ndarray      # [S] 0 = sphere, 1 = torus

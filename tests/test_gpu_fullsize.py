@@ -1,0 +1,163 @@
+"""Parity at the full size of the benchmark workload, in the launch
+configuration the benchmark times.
+
+gmm_large: N = Q = 2^24 3-D points from the 64-component mixture, queries 90 %
+from the mixture and 10 % uniform in the cube.  The oracle builds its own tree
+(the recursive median builder, threads over the top subtrees) and walks its
+own stack-free machine; nothing it computes comes from the GPU.  Compared:
+
+* the whole tree (node -> input index, coordinates, stored split dimensions)
+  after the first build and after a rebuild;
+* ids and squared-distance bits of a seeded, stratified sample of 2^16
+  queries: 8192 of the uniformly drawn queries, which land between the
+  clusters and carry almost all of the work (each processes thousands to
+  millions of nodes), and 57344 of the mixture queries, after one GPU launch
+  over all 2^24 queries with the tuned launch parameters; at max_radius = inf
+  and 0.005, for k = 8 (the benchmark's k) and, on an 8192-query part of the
+  sample, k = 1 and k = 64;
+* the processed-node count of every sampled query (the roofline's V_q) against
+  the oracle machine's count, for both radii and for the stored-split tree;
+* the learned-radius form's results on the same sample (its processed nodes
+  depend on the network's proposals, which the oracle does not compute).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_12859_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LOG2N = 24
+N = 1 << LOG2N
+SEED = synth.BASE_SEED + 2
+FLAGS_NAMES = ("MORTON", "COST_ORDER")
+N_UNIFORM, N_SAMPLE = 8192, 1 << 16
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def kdt():
+    from paper_2210_12859_gb300 import build
+
+    build.build_library()
+    from paper_2210_12859_gb300 import kdt as k
+
+    return k
+
+
+@pytest.fixture(scope="module")
+def work(kdt):
+    pts, qs = synth.gmm_large(N, N, seed=SEED)
+    uni = synth.gmm_query_is_uniform(N, 0.1, SEED + 2)
+    g = np.random.default_rng(221012859)
+    iu = g.choice(np.nonzero(uni)[0], N_UNIFORM, replace=False)
+    im = g.choice(np.nonzero(~uni)[0], N_SAMPLE - N_UNIFORM, replace=False)
+    idx = np.sort(np.concatenate([iu, im]))
+    tree_o = oracle.build(pts, threads=THREADS)
+    dp = torch.from_numpy(pts).cuda()
+    dq = torch.from_numpy(qs).cuda()
+    flags = 0
+    for n in FLAGS_NAMES:
+        flags |= getattr(kdt, "KDT_" + n)
+    tree = kdt.kdt_build(dp)
+    yield {"pts": pts, "qs": qs, "idx": idx, "uni": uni, "tree_o": tree_o, "dp": dp, "dq": dq, "flags": flags,
+           "tree": tree, "oracle": {}}
+    tree.free()
+
+
+def oracle_knn(w, k, r, sub=None):
+    key = (k, r, sub)
+    if key not in w["oracle"]:
+        idx = w["idx"] if sub is None else w["idx"][sub]
+        w["oracle"][key] = oracle.knn_tree_threaded(w["pts"], w["tree_o"], w["qs"][idx], k, max_radius=r,
+                                                    threads=THREADS)
+    return w["oracle"][key]
+
+
+def check_tree(kdt, tree, pts, want_pid, want_dims=None):
+    coords, ids = kdt.kdt_tree_export(tree)
+    assert np.array_equal(ids.cpu().numpy(), want_pid)
+    assert np.array_equal(coords.cpu().numpy().view(np.uint32), pts[want_pid].view(np.uint32))
+    if want_dims is not None:
+        assert np.array_equal(kdt.kdt_tree_split_dims(tree).cpu().numpy(), want_dims)
+
+
+def test_fullsize_tree_equals_oracle(kdt, work):
+    w = work
+    check_tree(kdt, w["tree"], w["pts"], w["tree_o"])
+    kdt.kdt_rebuild(w["tree"], w["dp"], opts=kdt.KDT_BUILD_ASYNC)
+    torch.cuda.synchronize()
+    kdt.kdt_status(w["tree"])
+    check_tree(kdt, w["tree"], w["pts"], w["tree_o"])
+
+
+@pytest.mark.parametrize("r", [math.inf, 0.005])
+def test_fullsize_knn_sample_bit_exact(kdt, work, r):
+    w = work
+    k = 8
+    kdt.kdt_autotune(w["tree"], w["dq"], k, w["flags"])
+    gi, gd = kdt.kdt_knn(w["tree"], w["dq"], k, r, w["flags"])
+    gv = kdt.kdt_knn_visits(w["tree"], w["dq"], k, r, w["flags"])
+    torch.cuda.synchronize()
+    kdt.kdt_status(w["tree"])
+    wi, wd, wv = oracle_knn(w, k, r)
+    idx = w["idx"]
+    assert np.array_equal(gi.cpu().numpy()[idx], wi)
+    assert np.array_equal(gd.cpu().numpy()[idx].view(np.uint32), wd.view(np.uint32))
+    assert np.array_equal(gv.cpu().numpy()[idx], wv)
+    if r == math.inf:
+        # the sample holds thousands of the long between-cluster queries
+        assert int((wv > 1000).sum()) >= 4096
+        assert int(w["uni"][idx].sum()) == N_UNIFORM
+
+
+@pytest.mark.parametrize("k", [1, 64])
+def test_fullsize_fcp_and_large_k(kdt, work, k):
+    w = work
+    sub = slice(0, N_SAMPLE, 8)  # 8192 queries of the sample, about 1024 of them between the clusters
+    kdt.kdt_autotune(w["tree"], w["dq"], k, w["flags"])
+    gi, gd = kdt.kdt_knn(w["tree"], w["dq"], k, math.inf, w["flags"])
+    torch.cuda.synchronize()
+    kdt.kdt_status(w["tree"])
+    wi, wd, _ = oracle_knn(w, k, math.inf, sub)
+    rows = w["idx"][sub]
+    assert np.array_equal(gi.cpu().numpy()[rows], wi)
+    assert np.array_equal(gd.cpu().numpy()[rows].view(np.uint32), wd.view(np.uint32))
+
+
+def test_fullsize_stored_split_dims(kdt, work):
+    w = work
+    pid, dims = oracle.build_widest(w["pts"], threads=THREADS)
+    tree = kdt.kdt_build(w["dp"], opts=kdt.KDT_BUILD_WIDEST)
+    try:
+        check_tree(kdt, tree, w["pts"], pid, dims)
+        gi, gd = kdt.kdt_knn(tree, w["dq"], 8, math.inf, w["flags"])
+        gv = kdt.kdt_knn_visits(tree, w["dq"], 8, math.inf, w["flags"])
+        torch.cuda.synchronize()
+        kdt.kdt_status(tree)
+        idx = w["idx"]
+        wi, wd, wv = oracle.knn_tree_threaded(w["pts"], pid, w["qs"][idx], 8, node_dim=dims, threads=THREADS)
+        assert np.array_equal(gi.cpu().numpy()[idx], wi)
+        assert np.array_equal(gd.cpu().numpy()[idx].view(np.uint32), wd.view(np.uint32))
+        assert np.array_equal(gv.cpu().numpy()[idx], wv)
+    finally:
+        tree.free()
+
+
+def test_fullsize_learned_radius(kdt, work):
+    w = work
+    mix = synth.gmm_mixture(64, 3, 0.01, SEED)
+    train_q = torch.from_numpy(synth.gmm_queries(mix, 1 << 20, 0.1, synth.BASE_SEED + 77)).cuda()
+    kdt.kdt_radius_model_train(w["tree"], train_q, 8, epochs=20, seed=1)
+    gi, gd = kdt.kdt_knn(w["tree"], w["dq"], 8, math.inf, w["flags"] | kdt.KDT_LEARNED)
+    torch.cuda.synchronize()
+    kdt.kdt_status(w["tree"])
+    wi, wd, _ = oracle_knn(w, 8, math.inf)
+    idx = w["idx"]
+    assert np.array_equal(gi.cpu().numpy()[idx], wi)
+    assert np.array_equal(gd.cpu().numpy()[idx].view(np.uint32), wd.view(np.uint32))

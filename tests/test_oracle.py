@@ -168,6 +168,45 @@ def test_threaded_brute_equals_single_call(threads):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
 
+@pytest.mark.parametrize("threads", [2, 5, 16])
+def test_parallel_builders_equal_serial(threads):
+    """The threaded driver of the recursive builders (subtrees of the top
+    levels in their own threads) gives the serial builders' trees: both split
+    rules, ties on every dimension, ragged and complete sizes, sizes below the
+    size at which subtrees stop spawning threads."""
+    g = np.random.default_rng(threads)
+    for N, D in ((1 << 15, 3), (50001, 3), (30000, 2), (9000, 5), (1000, 3)):
+        pts = g.random((N, D)).astype(np.float32)
+        pts[::5, 0] = 0.25
+        pts[::7, D - 1] = np.float32(-0.0)
+        pts[::11] = pts[3]
+        assert np.array_equal(oracle.build(pts, threads=threads), oracle.build(pts))
+        if D <= 3:
+            a, b = oracle.build_widest(pts, threads=threads), oracle.build_widest(pts)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_traversal_equals_single_call(threads):
+    """The threaded traversal (chunks of queries claimed by host threads) gives
+    the single call's ids, distance bits and processed-node counts, for both
+    split rules."""
+    g = np.random.default_rng(43)
+    pts = g.random((3000, 3)).astype(np.float32)
+    qs = (g.random((777, 3)) * 1.4 - 0.2).astype(np.float32)
+    pid = oracle.build(pts)
+    wpid, wdims = oracle.build_widest(pts)
+    for k, r in ((1, math.inf), (8, math.inf), (5, 0.05)):
+        a = oracle.knn_tree(pts, pid, qs, k, r)
+        b = oracle.knn_tree_threaded(pts, pid, qs, k, r, threads=threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+        assert np.array_equal(a[2], b[2])
+        c = oracle.knn_tree_dims(pts, wpid, wdims, qs, k, r)
+        d = oracle.knn_tree_threaded(pts, wpid, qs, k, r, node_dim=wdims, threads=threads)
+        assert np.array_equal(c[0], d[0]) and np.array_equal(c[1].view(np.uint32), d[1].view(np.uint32))
+        assert np.array_equal(c[2], d[2])
+
+
 def test_zero_radius_returns_exact_duplicates_only():
     g = np.random.default_rng(7)
     pts = g.integers(0, 3, size=(60, 2)).astype(np.float32)

@@ -64,6 +64,20 @@ def test_gmm_queries_uniform_share():
     assert np.array_equal(q, synth.gmm_queries(mix, 50000, 0.1, seed=6))
 
 
+def test_gmm_query_is_uniform_marks_the_uniform_draws():
+    """The mask of uniformly drawn queries: those lie in the cube and (but for
+    the ~1e-3 that land near a centre) farther than 6 sigma from every centre,
+    the others within it."""
+    mix = synth.gmm_mixture(8, 3, 0.005, seed=5)
+    q = synth.gmm_queries(mix, 50000, 0.1, seed=6)
+    uni = synth.gmm_query_is_uniform(50000, 0.1, seed=6)
+    d = np.linalg.norm(q[:, None, :].astype(np.float64) - mix.centres[None], axis=2).min(axis=1)
+    assert np.all(d[~uni] < 6 * 0.005)
+    assert np.mean(d[uni] > 6 * 0.005) > 0.99
+    assert np.all(q[uni] >= 0.0) and np.all(q[uni] <= 1.0)
+    assert abs(uni.mean() - 0.1) < 0.005
+
+
 def test_gmm_queries_without_uniform_share():
     mix = synth.gmm_mixture(8, 3, 0.005, seed=5)
     q = synth.gmm_queries(mix, 20000, 0.0, seed=6)
