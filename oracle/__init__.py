@@ -90,8 +90,8 @@ def _load():
         lib.orc_round_bf16.restype = f32
         lib.orc_mlp_forward.argtypes = [P, i32, P, i64, P]
         lib.orc_mlp_forward.restype = None
-        lib.orc_mlp_forward_bf16act.argtypes = [P, i32, P, i64, P]
-        lib.orc_mlp_forward_bf16act.restype = None
+        lib.orc_mlp_forward_bound.argtypes = [P, i32, P, i64, P, P]
+        lib.orc_mlp_forward_bound.restype = None
         lib.orc_mlp_loss_grad.argtypes = [P, i32, P, P, i64, P]
         lib.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
@@ -444,14 +444,16 @@ def mlp_forward(params, H: int, x) -> np.ndarray:
     return y
 
 
-def mlp_forward_bf16act(params, H: int, x) -> np.ndarray:
-    """Forward of the tensor-core inference path: FP32 fused layer 1, hidden
-    activations rounded to bfloat16, the rest exact (FP64)."""
-    p = np.ascontiguousarray(params, dtype=np.float32)
-    xs = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+def mlp_forward_bound(params, H: int, x):
+    """FP64 forward of the model and, per sample, a bound on the error of an
+    evaluation with BF16 hidden activations and FP32 arithmetic (any order,
+    rounding or truncating): (y float64[n], bound float64[n])."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty(xs.shape[0], dtype=np.float64)
-    _load().orc_mlp_forward_bf16act(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y))
-    return y
+    bound = np.empty(xs.shape[0], dtype=np.float64)
+    _load().orc_mlp_forward_bound(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y), _ptr(bound))
+    return y, bound
 
 
 def mlp_loss_grad(params, H: int, x, label):

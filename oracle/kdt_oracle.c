@@ -40,7 +40,8 @@
  *                       radius proposal; not in the paper)
  *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
  *                       paper; parity target for the GPU training kernels),
- *                       and the forward with BF16 hidden activations (parity
+ *                       and the forward with a per-sample bound on the error
+ *                       of a BF16-in / FP32-accumulate evaluation (parity
  *                       target for the tensor-core inference kernel)
  *
  * Parity status: every function above is pinned by tests under tests/ against
@@ -774,40 +775,75 @@ double orc_mlp_loss_grad(const double *params, int H, const double *x,
     return loss / (double)n;
 }
 
-/* Forward pass of the device inference kernel: layer 1 in FP32 with a fused
- * multiply-add chain in input order starting from the bias, ReLU, the hidden
- * activations rounded to bfloat16 (the tensor-core operand type); layer 2 and
- * the output layer evaluated exactly (FP64) from those values.  params are
- * float32 values (weights already rounded to bfloat16 by the caller). */
-void orc_mlp_forward_bf16act(const float *params, int H, const float *x, int64_t n, double *y)
+/* The model's forward (as orc_mlp_forward, FP64) together with, per sample, a
+ * bound on how far from it an evaluation in the precision the radius model is
+ * specified in can land: the hidden activations rounded to bfloat16 as the
+ * operands of the 64 x 64 contraction (BF16 in), everything else in FP32
+ * (FP32 accumulation), in any order, each FP32 operation with a relative error
+ * of at most 2^-23 (round to nearest gives 2^-24; the bound also admits
+ * truncating accumulation).  params hold bfloat16-valued weights, x values
+ * exact in FP32.  With g(m) = m e / (1 - m e), e = 2^-23, for m operations and
+ * b = 2^-8 the unit roundoff of bfloat16 (8 significant bits):
+ *   layer 1: |z1' - z1| <= g(10) S1, S1 = |b1| + sum |W1 x|; the activation
+ *            relu(z1') rounded to bfloat16 is within
+ *            e1 = b (h1 + g(10) S1) + g(10) S1 of h1 (relu is 1-Lipschitz);
+ *   layer 2: e2 = sum_i |W2_ji| e1_i + g(2H + 2) (|b2_j| + sum_i |W2_ji| (h1_i + e1_i));
+ *   output:  e3 = sum_j |w3_j| e2_j + g(2H + 2) (|b3| + sum_j |w3_j| (h2_j + e2_j)). */
+static double orc_gamma(int m)
 {
-    const float *W1 = params;
-    const float *b1 = W1 + (int64_t)H * 4;
-    const float *W2 = b1 + H;
-    const float *b2 = W2 + (int64_t)H * H;
-    const float *w3 = b2 + H;
-    const float *b3 = w3 + H;
+    const double e = 1.0 / 8388608.0;
+    return m * e / (1.0 - m * e);
+}
+
+void orc_mlp_forward_bound(const double *params, int H, const double *x, int64_t n, double *y, double *bound)
+{
+    const double *W1 = params;
+    const double *b1 = W1 + (int64_t)H * 4;
+    const double *W2 = b1 + H;
+    const double *b2 = W2 + (int64_t)H * H;
+    const double *w3 = b2 + H;
+    const double *b3 = w3 + H;
+    const double ub = 1.0 / 256.0;
+    const double g1 = orc_gamma(10), g2 = orc_gamma(2 * H + 2);
     double *h1 = (double *)malloc((size_t)H * sizeof(double));
+    double *e1 = (double *)malloc((size_t)H * sizeof(double));
+    double *h2 = (double *)malloc((size_t)H * sizeof(double));
+    double *e2 = (double *)malloc((size_t)H * sizeof(double));
     for (int64_t s = 0; s < n; ++s) {
-        const float *xs = x + s * 4;
+        const double *xs = x + s * 4;
         for (int i = 0; i < H; ++i) {
-            float a = b1[i];
-            for (int j = 0; j < 4; ++j)
-                a = fmaf(W1[i * 4 + j], xs[j], a);
-            a = a > 0.0f ? a : 0.0f;
-            h1[i] = (double)orc_round_bf16(a);
+            double z = b1[i], S = fabs(b1[i]);
+            for (int j = 0; j < 4; ++j) {
+                z += W1[i * 4 + j] * xs[j];
+                S += fabs(W1[i * 4 + j] * xs[j]);
+            }
+            h1[i] = z > 0.0 ? z : 0.0;
+            e1[i] = ub * (h1[i] + g1 * S) + g1 * S;
         }
-        double o = (double)b3[0];
-        for (int i = 0; i < H; ++i) {
-            double acc = 0.0;
-            for (int j = 0; j < H; ++j)
-                acc += (double)W2[(int64_t)i * H + j] * h1[j];
-            acc += (double)b2[i];
-            o += (double)w3[i] * (acc > 0.0 ? acc : 0.0);
+        for (int j = 0; j < H; ++j) {
+            double z = b2[j], A = fabs(b2[j]), prop = 0.0;
+            for (int i = 0; i < H; ++i) {
+                double w = W2[(int64_t)j * H + i];
+                z += w * h1[i];
+                A += fabs(w) * (h1[i] + e1[i]);
+                prop += fabs(w) * e1[i];
+            }
+            h2[j] = z > 0.0 ? z : 0.0;
+            e2[j] = prop + g2 * A;
+        }
+        double o = b3[0], A = fabs(b3[0]), prop = 0.0;
+        for (int j = 0; j < H; ++j) {
+            o += w3[j] * h2[j];
+            A += fabs(w3[j]) * (h2[j] + e2[j]);
+            prop += fabs(w3[j]) * e2[j];
         }
         y[s] = o;
+        bound[s] = prop + g2 * A;
     }
     free(h1);
+    free(e1);
+    free(h2);
+    free(e2);
 }
 
 /* ------------------------------------------------------------------------ */

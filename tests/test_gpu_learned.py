@@ -83,20 +83,21 @@ def test_descent_features_match_oracle(kdt, surface):
 
 def test_mlp_forward_matches_oracle(kdt):
     """The inference forward (hidden layer on the tensor cores, BF16 operands,
-    FP32 accumulation) against the oracle's forward with the same BF16
-    rounding of the hidden activations; 5000 samples = 40 tiles of 128 with a
-    ragged last tile."""
+    FP32 accumulation) against the oracle's FP64 model with the same
+    bfloat16-valued weights, within the oracle's per-sample bound for any
+    BF16-in / FP32-accumulate evaluation (the bfloat16 rounding of the 64
+    hidden activations, unit roundoff 2^-8, carried through both layers, plus
+    an FP32 allowance of 2^-23 per operation); 5000 samples = 40 tiles of 128
+    with a ragged last tile."""
     p = random_params(1)
     g = np.random.default_rng(2)
     x = g.standard_normal((5000, 4)).astype(np.float32)
-    y = kdt.kdt_mlp_forward(p, cu(x)).cpu().numpy()
-    want = oracle.mlp_forward_bf16act(rounded(p).astype(np.float32), H, x)
-    # two 64-term sums accumulated in FP32 (exact BF16 products) against FP64:
-    # at most 64u each relative to the sum of magnitudes, 2 * 64u = 7.6e-6
-    assert np.allclose(y, want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
-    # and close to the exact model (BF16 activations change it only slightly)
-    exact = oracle.mlp_forward(rounded(p), H, x.astype(np.float64))
-    assert np.allclose(y, exact, rtol=2e-2, atol=2e-2 * np.abs(exact).max())
+    y = kdt.kdt_mlp_forward(p, cu(x)).cpu().numpy().astype(np.float64)
+    want, bound = oracle.mlp_forward_bound(rounded(p), H, x.astype(np.float64))
+    err = np.abs(y - want)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # the tensor-core result is not the FP64 model's: the rounding shows
+    assert err.max() > 0
 
 
 def test_mlp_gradients_match_oracle(kdt):

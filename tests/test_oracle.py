@@ -491,55 +491,124 @@ def test_mlp_gradient_matches_finite_differences():
         assert abs(fd - grad[i]) <= 1e-5 * max(1.0, abs(fd)), i
 
 
-def test_mlp_bf16_activation_forward_equals_exact_when_nothing_rounds():
-    """With small-integer weights, biases and inputs every hidden activation is
-    an integer below 256 (exact in bfloat16) and the FP32 layer is exact, so
-    the device-path forward must equal the plain FP64 forward."""
+def _bf16(v):
+    """Round float32 values to the nearest bfloat16 (ties to even) through torch."""
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _bf16_params(H, seed, scale=0.5):
+    g = np.random.default_rng(seed)
+    p = (g.standard_normal(oracle.mlp_param_count(H)) * scale).astype(np.float32)
+    return _bf16(p).astype(np.float64)
+
+
+def _simulate_bf16_in(p, H, x, order):
+    """An FP32 evaluation with the hidden activations rounded to bfloat16:
+    layer 1 unfused (products rounded) or through FP64 then rounded once
+    (a fused chain's accuracy), sums left to right or reversed."""
+    f = np.float32
+    W1 = p[: 4 * H].reshape(H, 4).astype(f)
+    b1 = p[4 * H: 5 * H].astype(f)
+    W2 = p[5 * H: 5 * H + H * H].reshape(H, H).astype(f)
+    b2 = p[5 * H + H * H: 6 * H + H * H].astype(f)
+    w3 = p[6 * H + H * H: 7 * H + H * H].astype(f)
+    b3 = f(p[-1])
+    xs = x.astype(f)
+    if order == "fused":
+        z1 = (b1.astype(np.float64) + xs.astype(np.float64) @ W1.T.astype(np.float64)).astype(f)
+    else:
+        z1 = np.repeat(b1[None, :], xs.shape[0], 0)
+        for j in range(4):
+            z1 = (z1 + (W1[:, j][None, :] * xs[:, j:j + 1]).astype(f)).astype(f)
+    h1 = _bf16(np.maximum(z1, f(0)))
+    idx = range(H) if order != "reversed" else range(H - 1, -1, -1)
+    acc = np.zeros((xs.shape[0], H), dtype=f)
+    for i in idx:
+        acc = (acc + (h1[:, i:i + 1] * W2[:, i][None, :]).astype(f)).astype(f)
+    h2 = np.maximum((acc + b2[None, :]).astype(f), f(0))
+    y = np.full(xs.shape[0], b3, dtype=f)
+    for j in idx:
+        y = (y + (w3[j] * h2[:, j]).astype(f)).astype(f)
+    return y.astype(np.float64)
+
+
+def test_mlp_forward_bound_value_is_the_fp64_forward():
+    H = 16
+    p = _bf16_params(H, 15)
+    x = np.random.default_rng(16).standard_normal((200, 4)).astype(np.float32).astype(np.float64)
+    y, bound = oracle.mlp_forward_bound(p, H, x)
+    assert np.array_equal(y.view(np.uint64), oracle.mlp_forward(p, H, x).view(np.uint64))
+    assert np.all(bound > 0)
+
+
+@pytest.mark.parametrize("order", ["unfused", "fused", "reversed"])
+def test_mlp_forward_bound_covers_bf16_in_fp32_evaluations(order):
+    """Simulated BF16-in / FP32 evaluations in three orders stay within the
+    per-sample bound, on the model's width and on a narrow one."""
+    for H, seed in ((64, 17), (8, 18)):
+        p = _bf16_params(H, seed)
+        x = np.random.default_rng(seed + 100).standard_normal((3000, 4)).astype(np.float32).astype(np.float64)
+        y, bound = oracle.mlp_forward_bound(p, H, x)
+        sim = _simulate_bf16_in(p, H, x, order)
+        assert np.all(np.abs(sim - y) <= bound), float(np.max(np.abs(sim - y) / bound))
+        # and the rounding does show: the bound is not vacuous for these models
+        assert np.max(np.abs(sim - y)) > 0
+
+
+def test_mlp_forward_bound_is_tight_for_one_rounded_activation():
+    """A hidden activation of 1 + 2^-8 lies halfway between the bfloat16
+    neighbours 1 and 1 + 2^-7 and rounds to 1 (ties to even): the model's
+    output 1 + 2^-8 becomes 1, an error of 2^-8.  The bound must cover it, and
+    by little (the FP32 terms add only about 2^-20)."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0            # W1[0][0]
+    p[4] = 2.0 ** -8      # b1
+    p[5] = 1.0            # W2
+    p[7] = 1.0            # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    y, bound = oracle.mlp_forward_bound(p, H, x)
+    assert y[0] == 1.0 + 2.0 ** -8
+    assert _simulate_bf16_in(p, H, x, "unfused")[0] == 1.0
+    assert 2.0 ** -8 <= bound[0] <= 1.01 * 2.0 ** -8
+
+
+def test_mlp_forward_bound_covers_cancellation_in_layer1():
+    """Layer 1 with cancelling terms: (1 + 2^-7)(1 + 2^-20) is 1 + 2^-7 + 2^-20
+    + 2^-27 exactly and 1 + 2^-7 + 2^-20 in FP32, so with the second term
+    -(1 + 2^-7 + 2^-20) an FP32 evaluation gets 0 where the model has 2^-27.
+    Only the bound's FP32 allowance of layer 1 covers that (the activation is
+    far below the bfloat16 level)."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0 + 2.0 ** -7     # W1[0][0]
+    p[1] = -1.0                # W1[0][1]
+    p[5] = 1.0                 # W2
+    p[7] = 1.0                 # w3
+    x = np.array([[1.0 + 2.0 ** -20, 1.0 + 2.0 ** -7 + 2.0 ** -20, 0, 0]])
+    y, bound = oracle.mlp_forward_bound(p, H, x)
+    assert y[0] == 2.0 ** -27
+    assert _simulate_bf16_in(p, H, x, "unfused")[0] == 0.0
+    assert bound[0] >= 2.0 ** -27
+
+
+def test_mlp_forward_bound_value_exact_for_integer_model():
+    """Small-integer weights, biases and inputs: every value is exact in
+    bfloat16 and FP32, so a BF16-in / FP32 evaluation gives the FP64 forward's
+    value exactly (a dropped bias or a transposed matrix would show here)."""
     H = 16
     g = np.random.default_rng(14)
     p = np.zeros(oracle.mlp_param_count(H))
-    p[: 4 * H] = g.integers(-2, 3, 4 * H)          # W1
-    p[4 * H: 5 * H] = g.integers(-3, 4, H)         # b1
-    p[5 * H:] = g.standard_normal(len(p) - 5 * H)  # W2, b2, w3, b3 (bf16-exact below)
-    p[5 * H:] = [oracle.round_bf16(float(v)) for v in p[5 * H:]]
+    p[: 4 * H] = g.integers(-2, 3, 4 * H)
+    p[4 * H: 5 * H] = g.integers(-3, 4, H)
+    p[5 * H: 5 * H + H * H] = g.integers(-1, 2, H * H)
+    p[5 * H + H * H:] = g.integers(-2, 3, len(p) - 5 * H - H * H)
     x = g.integers(-4, 5, size=(50, 4)).astype(np.float64)
-    a = oracle.mlp_forward(p, H, x)
-    b = oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))
-    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
-
-
-def test_mlp_bf16_activation_forward_rounds_hidden_layer():
-    """A hidden activation of 1 + 2^-10 is not a bfloat16 value: the device-path
-    forward sees 1 (ties to even), the exact forward sees 1 + 2^-10."""
-    H = 1
-    p = np.zeros(oracle.mlp_param_count(H))
-    p[0] = 1.0                  # W1[0][0]
-    p[4] = 2.0 ** -10           # b1
-    p[5] = 1.0                  # W2
-    p[7] = 1.0                  # w3
-    x = np.array([[1.0, 0, 0, 0]])
-    assert oracle.mlp_forward(p, H, x)[0] == 1.0 + 2.0 ** -10
-    assert oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0] == 1.0
-
-
-def test_mlp_bf16_activation_layer1_rounds_once_per_term():
-    """Layer 1 of the device-path forward is a fused multiply-add chain: each
-    term w*x + a is rounded to FP32 once.  With w = 1 + 2^-13, x = 1 + 2^-11 -
-    2^-13 + 2^-19 and bias -1 the exact w*x - 1 is M + d, M = 2^-11 + 2^-19 and
-    d = 2^-24 - 2^-26 + 2^-32 (exact in FP32 at that magnitude).  Rounded once
-    it stays above M, the midpoint of the bfloat16 neighbours 2^-11 and
-    2^-11 + 2^-18, and rounds up; rounding the product first (its d is below
-    half an FP32 ulp at 1) lands exactly on M, which ties to even: 2^-11."""
-    H = 1
-    p = np.zeros(oracle.mlp_param_count(H))
-    p[0] = 1.0 + 2.0 ** -13                   # W1[0][0]
-    p[4] = -1.0                               # b1
-    p[5] = 1.0                                # W2
-    p[7] = 1.0                                # w3
-    x = np.array([[1.0 + 2.0 ** -11 - 2.0 ** -13 + 2.0 ** -19, 0, 0, 0]])
-    assert np.float32(p[0]) == p[0] and np.float32(x[0, 0]) == x[0, 0]
-    y = oracle.mlp_forward_bf16act(p.astype(np.float32), H, x.astype(np.float32))[0]
-    assert y == 2.0 ** -11 + 2.0 ** -18
+    y, bound = oracle.mlp_forward_bound(p, H, x)
+    assert np.array_equal(_simulate_bf16_in(p, H, x, "unfused"), y)
+    assert np.all(bound >= 0)
 
 
 # ---------------------------------------------------------------- stored split dimension

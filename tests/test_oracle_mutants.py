@@ -160,10 +160,6 @@ MUTANTS = {
     "grad_w1_input_index": [(
         "gW1[i * 4 + j] += g1[i] * xs[j];",
         "gW1[i * 4 + j] += g1[i] * xs[3 - j];")],
-    # BF16-activation forward: the second layer's bias dropped
-    "bf16act_bias_dropped": [(
-        "            acc += (double)b2[i];\n",
-        "")],
     # range machine: the ball test exclusive
     "range_ball_exclusive": [(
         "hit = v <= r2;",
@@ -220,10 +216,6 @@ MUTANTS = {
     "grad_b1_from_layer2": [(
         "gb1[i] += g1[i];",
         "gb1[i] += g2[i];")],
-    # BF16-activation forward: layer 1 rounded per operation instead of fused
-    "bf16act_layer1_unfused": [(
-        "a = fmaf(W1[i * 4 + j], xs[j], a);",
-        "a = W1[i * 4 + j] * xs[j] + a;")],
     # ball definition: exclusive radius
     "radius_brute_exclusive": [(
         "            if (v <= r2) {",
@@ -277,10 +269,22 @@ MUTANTS = {
     "grad_w2_preactivation": [(
         "gW2[(int64_t)i * H + j] += g2[i] * h1[j];",
         "gW2[(int64_t)i * H + j] += g2[i] * z1[j];")],
-    # BF16-activation forward: the hidden activations not rounded
-    "bf16act_not_rounded": [(
-        "h1[i] = (double)orc_round_bf16(a);",
-        "h1[i] = (double)a;")],
+    # forward bound: the bfloat16 unit roundoff taken as 2^-9
+    "bound_bf16_roundoff_halved": [(
+        "const double ub = 1.0 / 256.0;",
+        "const double ub = 1.0 / 512.0;")],
+    # forward bound: layer 1's error not carried through the hidden contraction
+    "bound_no_propagation_layer2": [(
+        "                prop += fabs(w) * e1[i];\n",
+        "")],
+    # forward bound: the output layer's error from the hidden layer dropped
+    "bound_no_propagation_output": [(
+        "            prop += fabs(w3[j]) * e2[j];\n",
+        "")],
+    # forward bound: the FP32 allowance of layer 1 dropped
+    "bound_layer1_fp32_dropped": [(
+        "            e1[i] = ub * (h1[i] + g1 * S) + g1 * S;",
+        "            e1[i] = ub * h1[i];")],
     # payload reductions: the payload row stride dropped
     "reduce_payload_stride": [(
         "s = s + payload[(int64_t)hits[i] * C + c];",
