@@ -347,6 +347,20 @@ def main():
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
+    def timed_loop(fn):
+        """ms per call over the contract's step count, after its warm-up."""
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
     build_ms = timeit(lambda: kdt.kdt_rebuild(tree, dp, opts=kdt.KDT_BUILD_ASYNC), 3)
     query_ms = timeit(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags, out_i, out_d), 2)
     visits = kdt.kdt_knn_visits(tree, dq, K_NN, math.inf, flags)
@@ -380,11 +394,17 @@ def main():
     bytes_per_launch = n * (4 * 3 + 8 * K_NN) + v_sum * 16.0
     achieved = bytes_per_launch / (kern_ms / 1000.0) / 1e9
     traffic = profiled_traffic()
+    # the same algorithmic bytes against L2: the read bandwidth of a 32 MiB
+    # buffer that stays in L2, measured by the library's own probe kernel
+    l2_gbs = kdt.kdt_l2_read_bandwidth(32 << 20, 200)
+    l2_note = "L2 read bandwidth measured by the library's probe (32 MiB buffer, 16-byte L1-bypassing loads)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "peak_source": peak_src,
                 "kernel": "knn_kernel<layout0,K=8,ordered> (stack-free traversal)",
                 "kernel_ms": kern_ms, "bytes_per_query": bytes_per_launch / n,
-                "visits_per_query": v_mean}
+                "visits_per_query": v_mean,
+                "l2": {"achieved": achieved, "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+                       "peak_source": l2_note}}
 
     # ---- learned radius form (same queries, same results)
     learned = None
@@ -392,21 +412,40 @@ def main():
         mix = synth.gmm_mixture(64, 3, 0.01, synth.BASE_SEED + 2)
         train_q = torch.from_numpy(synth.gmm_queries(mix, 1 << 20, 0.1, synth.BASE_SEED + 77)).to(dev)
         t0 = time.perf_counter()
-        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=20, seed=1)
+        # the gate (all queries, the far ones, none) is timed on the training
+        # queries with the bench's query flags and the fastest kept
+        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=20, seed=1, query_flags=flags)
         train_s = time.perf_counter() - t0
+        gate = kdt.kdt_radius_model_gate(tree)
         li = torch.empty_like(out_i)
         ld = torch.empty_like(out_d)
         kdt.kdt_knn(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED, li, ld)
-        learned_ms = timeit(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED, li, ld), 2)
+        # both query forms over the contract's step count, after its warm-up
+        plain_loop_ms = timed_loop(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags, out_i, out_d))
+        learned_ms = timed_loop(lambda: kdt.kdt_knn(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED, li, ld))
         fb, ratio = kdt.kdt_learned_stats(tree)
+        gated = kdt.kdt_learned_gated(tree)
         same = bool(torch.equal(li, out_i) and torch.equal(ld.view(torch.int32), out_d.view(torch.int32)))
         lv = kdt.kdt_knn_visits(tree, dq, K_NN, math.inf, flags | kdt.KDT_LEARNED)
+        lv_sum = float(lv.double().sum().item())
+        # algorithmic bytes: as the plain query, with the processed nodes of
+        # the bounded and re-run passes, plus 16 B of features per gated query
+        l_bytes = n * (4 * 3 + 8 * K_NN) + lv_sum * 16.0 + 16.0 * gated
+        l_ach = l_bytes / (learned_ms / 1000.0) / 1e9
         learned = {"query_qps": n / (learned_ms / 1000.0), "query_ms": learned_ms,
-                   "plain_query_qps": n / (query_ms / 1000.0), "speedup_vs_plain": query_ms / learned_ms,
-                   "fallback_rate": fb / n, "radius_ratio": ratio, "identical_to_plain": same,
-                   "visits_per_query": float(lv.double().mean().item()), "train_s": train_s,
+                   "plain_query_qps": n / (plain_loop_ms / 1000.0), "plain_query_ms": plain_loop_ms,
+                   "speedup_vs_plain": plain_loop_ms / learned_ms,
+                   "timing": f"{args.steps} calls of each form after {args.warmup} warm-up calls, CUDA events",
+                   "gate": {kdt.KDT_GATE_ALL: "all", kdt.KDT_GATE_FAR: "far", kdt.KDT_GATE_NONE: "none"}[gate],
+                   "gated_queries": gated, "fallback_rate": fb / n, "radius_ratio": ratio,
+                   "identical_to_plain": same, "visits_per_query": lv_sum / n, "train_s": train_s,
                    "train_loss": loss, "train_queries": 1 << 20, "train_epochs": 20,
-                   "train_weighting": "plain-traversal work (resampled)"}
+                   "train_weighting": "plain-traversal work (resampled)",
+                   "roofline": {"bound": "hbm", "achieved": l_ach, "peak": hbm, "unit": "GB/s", "frac": l_ach / hbm,
+                                "bytes_per_query": l_bytes / n, "peak_source": peak_src,
+                                "l2": {"peak": l2_gbs, "frac": l_ach / l2_gbs, "peak_source": l2_note},
+                                "time": "whole learned call (Morton pass, features and network for the gated "
+                                        "queries, bounded traversal)"}}
 
     # ---- the same queries on a tree with a stored per-node split dimension
     # (widest extent; the paper's other splitDimOf variant), same results

@@ -43,6 +43,40 @@ def _emit(**kw):
     print(json.dumps(kw), flush=True)
 
 
+def _peaks(kdt):
+    """(measured HBM GB/s or the fallback, its source, L2 read GB/s from the library's probe)."""
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+        hbm, src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        hbm, src = 6800.0, "fallback"
+    return hbm, src, kdt.kdt_l2_read_bandwidth(32 << 20, 200)
+
+
+def _roofline(bytes_, ms, hbm, src, l2, note):
+    ach = bytes_ / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
+            "l2": {"peak": l2, "frac": ach / l2,
+                   "peak_source": "L2 read bandwidth measured by the library's probe (32 MiB, L1-bypassing loads)"},
+            "bytes": bytes_, "time": note}
+
+
+def _loop(torch, fn, steps, warmup):
+    """ms per call over `steps` calls after `warmup` untimed ones (CUDA events)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(steps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
 def run_config(args):
     import torch
 
@@ -100,28 +134,50 @@ def run_config(args):
         qs = synth.surface_sample(sh, n, synth.BASE_SEED + 43)
         dp, dq, dt = cu(pts), cu(qs), cu(train)
         tree = kdt.kdt_build(dp)
-        for k, margin in ((8, 0.0), (32, 0.0), (8, 1.25), (32, 1.25)):
-            # margin 0: calibrated by the library; 1.25: the fixed margin of the configuration
+        hbm, src, l2 = _peaks(kdt)
+        F = kdt.KDT_MORTON
+        gate_names = {kdt.KDT_GATE_ALL: "all", kdt.KDT_GATE_FAR: "far", kdt.KDT_GATE_NONE: "none"}
+        for k, margin in ((8, 1.25), (32, 1.25), (8, 0.0), (32, 0.0)):
+            # 1.25: the fixed margin of the configuration; 0: calibrated by the library
+            kdt.kdt_autotune(tree, dq, k, F)
             t0 = time.perf_counter()
-            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1, margin=margin)
+            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1, margin=margin, query_flags=F)
             train_s = time.perf_counter() - t0
             used_margin = kdt.kdt_radius_model_get(tree)[2]
             out_i = torch.empty((n, k), dtype=torch.int32, device="cuda")
             out_d = torch.empty((n, k), dtype=torch.float32, device="cuda")
             li = torch.empty_like(out_i)
             ld = torch.empty_like(out_d)
-            plain_ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, kdt.KDT_MORTON, out_i, out_d), 2)
-            learned_ms = timeit(lambda: kdt.kdt_knn(tree, dq, k, math.inf, kdt.KDT_MORTON | kdt.KDT_LEARNED, li, ld), 2)
+            steps, warm = max(args.steps, 5), max(args.warmup, 3)
+            plain_ms = _loop(torch, lambda: kdt.kdt_knn(tree, dq, k, math.inf, F, out_i, out_d), steps, warm)
+            learned_ms = _loop(torch, lambda: kdt.kdt_knn(tree, dq, k, math.inf, F | kdt.KDT_LEARNED, li, ld),
+                               steps, warm)
             fb, ratio = kdt.kdt_learned_stats(tree)
-            pv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON).double().mean().item()
-            lv = kdt.kdt_knn_visits(tree, dq, k, flags=kdt.KDT_MORTON | kdt.KDT_LEARNED).double().mean().item()
+            gated = kdt.kdt_learned_gated(tree)
+            pv = kdt.kdt_knn_visits(tree, dq, k, flags=F).double().sum().item()
+            lv = kdt.kdt_knn_visits(tree, dq, k, flags=F | kdt.KDT_LEARNED).double().sum().item()
             same = bool(torch.equal(li, out_i) and torch.equal(ld.view(torch.int32), out_d.view(torch.int32)))
+            # forced gates, for context (the library keeps the fastest on the training queries)
+            forced = {}
+            kept = kdt.kdt_radius_model_gate(tree)
+            for g in (kdt.KDT_GATE_ALL, kdt.KDT_GATE_FAR):
+                if g == kept:
+                    continue
+                kdt.kdt_radius_model_set_gate(tree, g)
+                forced[gate_names[g]] = plain_ms / _loop(
+                    torch, lambda: kdt.kdt_knn(tree, dq, k, math.inf, F | kdt.KDT_LEARNED, li, ld), steps, warm)
+            kdt.kdt_radius_model_set_gate(tree, kept)
             _emit(config="surface_learned N=Q=2^24 (256 spheres/tori)",
                   form=f"kNN k={k} plain vs learned ({'margin 1.25 as configured' if margin else 'calibrated margin'})",
-                  margin=used_margin,
+                  margin=used_margin, gate=gate_names[kept], gated_queries=gated,
                   plain_qps=n / (plain_ms / 1e3), learned_qps=n / (learned_ms / 1e3),
-                  speedup=plain_ms / learned_ms, fallback_rate=fb / n, radius_ratio=ratio,
-                  plain_visits=pv, learned_visits=lv, identical=same, train_s=train_s, train_loss=loss,
+                  speedup=plain_ms / learned_ms, speedup_with_other_gates=forced,
+                  timing=f"{steps} calls of each form after {warm} warm-up calls",
+                  fallback_rate=fb / n, radius_ratio=ratio,
+                  plain_visits=pv / n, learned_visits=lv / n, identical=same, train_s=train_s, train_loss=loss,
+                  roofline_plain=_roofline(n * (12 + 8 * k) + 16.0 * pv, plain_ms, hbm, src, l2, "plain query call"),
+                  roofline_learned=_roofline(n * (12 + 8 * k) + 16.0 * lv + 16.0 * gated, learned_ms, hbm, src, l2,
+                                             "learned query call (features and network included)"),
                   bit_exact_sample=_exact(oracle, pts, qs, out_i.cpu().numpy(), out_d.cpu().numpy(), k))
         return
 
@@ -291,6 +347,8 @@ def run_config(args):
             res[name] = (ms, out_i.clone(), out_d.clone())
         same = all(torch.equal(res[a][1], res["one launch per tree"][1]) and
                    torch.equal(res[a][2], res["one launch per tree"][2]) for a in res)
+        visits = kdt.kdt_knn_batched_visits(forest, dq, c.qoffsets, 8).double().sum().item()
+        hbm, src, l2 = _peaks(kdt)
         # sampled oracle check on a few clouds
         gi = out_i.cpu().numpy()
         gd = out_d.cpu().numpy()
@@ -304,5 +362,7 @@ def run_config(args):
             _emit(config=f"batched: 4096 clouds, {int(c.offsets[-1])} points, {Q} queries, kNN k=8", form=name,
                   query_qps=Q / (ms / 1e3), query_ms=ms, forest_build_s=build_s, identical_forms=same,
                   launch_autotuned={"threads": th, "claim_steps": cs, "inline_depth": il, "light_run": lr},
+                  visits_per_query=visits / Q,
+                  roofline=_roofline(Q * (12 + 8 * 8) + 16.0 * visits, ms, hbm, src, l2, "whole batched call"),
                   bit_exact_sample=ok)
         return

@@ -259,6 +259,20 @@ int kdt_knn_static(const kdt_tree *tree, const float *d_queries, int64_t Q, int 
 
 /* ---- learned radius proposal (not in the paper) ------------------------- */
 
+/* Which queries of a KDT_LEARNED call take the proposed radius (no paper
+ * counterpart; results are the same for every choice).  A proposal saves
+ * work only where the plain traversal wastes it: queries far from the data
+ * process many nodes, and a tight initial radius removes some of them, while
+ * queries inside the data find their neighbours at once and only pay for the
+ * features and the network. */
+#define KDT_GATE_AUTO 0 /* training option: choose among the forms below from the training queries (see
+                           kdt_train_opts.gate) */
+#define KDT_GATE_ALL  1 /* every query */
+#define KDT_GATE_FAR  2 /* queries whose greedy descent ends more than 8 mean point spacings from its leaf point
+                           (the far cost classes of KDT_COST_ORDER, which the call then uses); the others run the
+                           plain traversal */
+#define KDT_GATE_NONE 3 /* no query: the call runs the plain traversal */
+
 typedef struct kdt_train_opts {
     int epochs;           /* passes over the training queries (default 6 if <= 0) */
     int batch;            /* minibatch size (default 1024 if <= 0; rounded down to a multiple of 64) */
@@ -273,6 +287,15 @@ typedef struct kdt_train_opts {
                              the mean), by resampling the training set with those
                              probabilities; the margin's fallback target is then a share of
                              that work.  1: every query weighs the same */
+    int gate;             /* KDT_GATE_* (default KDT_GATE_AUTO: on up to 2^20 of the training
+                             queries, with query_flags, the processed nodes of the plain traversal
+                             and of the learned forms (all queries gated, the far ones) are counted,
+                             and the network pass's cost per gated query is measured in
+                             processed-node equivalents (its time per query over the plain
+                             traversal's time per processed node); the form that saves the most
+                             nodes net of that cost is kept, KDT_GATE_NONE when none saves any) */
+    int query_flags;      /* flags of the queries the automatic gate is judged with (default
+                             KDT_MORTON | KDT_COST_ORDER) */
 } kdt_train_opts;
 
 /* Width of the two hidden layers of the radius model. */
@@ -299,7 +322,13 @@ int kdt_radius_model_train(kdt_tree *tree, const float *d_train_queries, int64_t
 int kdt_radius_model_get(const kdt_tree *tree, float *h_params, float *h_norm, float *margin);
 int kdt_radius_model_set(kdt_tree *tree, const float *h_params, const float *h_norm, float margin);
 
-/* Save / load the model as a small versioned binary file. */
+/* The gate of the tree's radius model (KDT_GATE_ALL / FAR / NONE), and a way
+ * to set it after training or loading. */
+int kdt_radius_model_gate(const kdt_tree *tree, int *gate);
+int kdt_radius_model_set_gate(kdt_tree *tree, int gate);
+
+/* Save / load the model as a small versioned binary file (the gate included;
+ * files of the first version load with KDT_GATE_ALL). */
 int kdt_radius_model_save(const kdt_tree *tree, const char *path);
 int kdt_radius_model_load(kdt_tree *tree, const char *path);
 
@@ -323,9 +352,14 @@ int kdt_mlp_loss_grad(const float *h_params, const float *d_x, const float *d_la
 
 /* Learned-path statistics of the last KDT_LEARNED query on this tree:
  * number of queries re-run with the caller's radius, and the mean of
- * (proposed radius / true k-th neighbour radius) over queries that did not
- * fall back.  Synchronises `stream`. */
+ * (proposed radius / true k-th neighbour radius) over the gated queries that
+ * did not fall back.  Synchronises `stream`. */
 int kdt_learned_stats(const kdt_tree *tree, int64_t *fallbacks, double *radius_ratio, void *stream);
+
+/* Number of queries of the last KDT_LEARNED call on this tree that took the
+ * proposed radius (all of them, the far ones or none, by the model's gate).
+ * Synchronises `stream`. */
+int kdt_learned_gated(const kdt_tree *tree, int64_t *gated, void *stream);
 
 /* ---- batched: many independent trees ------------------------------------ */
 
@@ -357,6 +391,14 @@ int kdt_forest_export(const kdt_forest *forest, float *d_coords, int32_t *d_ids,
  * Shared-memory staging does not apply to forests: the lanes of a warp walk
  * different trees.  The next kdt_knn_batched re-captures its graph. */
 int kdt_forest_set_launch(kdt_forest *forest, int threads, int claim_steps, int inline_depth, int light_run);
+
+/* Processed nodes (first visits) of every query of a kdt_knn_batched call
+ * (same arguments; KDT_UNORDERED respected, the other flags do not change
+ * the counts): d_visits int32 [total queries], 0 for queries of an empty
+ * cloud.  Counts the traversal of Sec. 3.2 as kdt_knn_visits does for one
+ * tree (the roofline's V_q of the batched form); one launch per tree. */
+int kdt_knn_batched_visits(kdt_forest *forest, const float *d_queries, const int64_t *h_query_offsets, int k,
+                           float max_radius, int flags, int32_t *d_visits, void *stream);
 
 /* Time the batched query (kdt_knn_batched with these arguments, graph
  * included; it writes d_ids / d_d2 like that call) for inline depths {2, 1},
@@ -452,6 +494,15 @@ int kdt_profile_enable(kdt_tree *tree, int enable);
 /* Synchronise, then return the accumulated milliseconds and launch count of the
  * traversal kernels since profiling was enabled, and reset them. */
 int kdt_profile_read(kdt_tree *tree, double *ms, int64_t *launches);
+
+/* L2 read bandwidth of the current GPU in GB/s, measured by the library's own
+ * kernel (no paper counterpart): a device buffer of `bytes` (1 MiB to 1 GiB;
+ * small enough to stay in L2 for the figure to mean L2) is read once, then
+ * `reps` times with 16-byte loads that bypass L1, by 8 blocks of 256 threads
+ * per SM; *gbs = bytes x reps over the fastest of three timed launches.  The
+ * buffer is allocated and freed on `stream`.  Synchronous.  This is the
+ * denominator of the L2 fractions the benchmark reports. */
+int kdt_l2_read_bandwidth(int64_t bytes, int reps, double *gbs, void *stream);
 
 #ifdef __cplusplus
 }

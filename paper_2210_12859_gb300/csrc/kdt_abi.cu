@@ -96,7 +96,8 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
 // the launch, where too few lanes are left to hide their latency.
 __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, const float *__restrict__ bbox, int T,
                               const int64_t *__restrict__ q_off, const float4 *__restrict__ nodes, int64_t N,
-                              bool stored, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals)
+                              bool stored, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                              unsigned long long *__restrict__ n_far)
 {
     float spacing2 = 0.f;
     if (nodes) {
@@ -105,44 +106,58 @@ __global__ void morton_kernel(const float *__restrict__ qs, int64_t Q, int D, co
             vol *= fmaxf(bbox[3 + j] - bbox[j], 1e-30f);
         spacing2 = powf(vol / (float)N, 2.f / (float)D);
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q; i += (int64_t)gridDim.x * blockDim.x) {
-        int t = 0;
-        if (T > 1) {
-            int lo = 0, hi = T - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (q_off[mid] <= i)
-                    lo = mid;
-                else
-                    hi = mid - 1;
+    // every thread of the grid runs the same number of iterations, so the
+    // warp vote that counts far queries sees full warps
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t iters = (Q + stride - 1) / stride;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        bool far = false;
+        if (i < Q) {
+            int t = 0;
+            if (T > 1) {
+                int lo = 0, hi = T - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (q_off[mid] <= i)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                t = lo;
             }
-            t = lo;
-        }
-        const float *bb = bbox + 6 * t;
-        uint32_t code = 0;
-        const float cells = nodes ? 512.f : 1024.f;
-        for (int j = 0; j < 3 && j < D; ++j) {
-            float ext = bb[3 + j] - bb[j];
-            float x = ext > 0.f ? (qs[i * D + j] - bb[j]) / ext : 0.f;
-            x = fminf(fmaxf(x, 0.f), 1.f);
-            uint32_t c = (uint32_t)fminf(x * cells, cells - 1.f);
-            code |= spread3(c) << (2 - j);
-        }
-        if (nodes) {
-            float q[3];
-            load_query<0>(qs, i, D, q);
-            const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q, stored) / spacing2;
-            uint32_t cls;
-            if (r > 64.f) {  // floor(log2 r) >= 6: classes 28 (r < 128) down to 0
-                const int e = ilogbf(r);
-                cls = (uint32_t)(28 - min(e - 6, 28));
-            } else {
-                cls = r > 8.f ? 29u : (r > 1.f ? 30u : 31u);  // NaN: 31
+            const float *bb = bbox + 6 * t;
+            uint32_t code = 0;
+            const float cells = nodes ? 512.f : 1024.f;
+            for (int j = 0; j < 3 && j < D; ++j) {
+                float ext = bb[3 + j] - bb[j];
+                float x = ext > 0.f ? (qs[i * D + j] - bb[j]) / ext : 0.f;
+                x = fminf(fmaxf(x, 0.f), 1.f);
+                uint32_t c = (uint32_t)fminf(x * cells, cells - 1.f);
+                code |= spread3(c) << (2 - j);
             }
-            code |= cls << 27;
+            if (nodes) {
+                float q[3];
+                load_query<0>(qs, i, D, q);
+                const float r = descent_leaf_d2(nodes, nullptr, 0, (int)N, D, q, stored) / spacing2;
+                uint32_t cls;
+                if (r > 64.f) {  // floor(log2 r) >= 6: classes 28 (r < 128) down to 0
+                    const int e = ilogbf(r);
+                    cls = (uint32_t)(28 - min(e - 6, 28));
+                    far = true;
+                } else {
+                    cls = r > 8.f ? 29u : (r > 1.f ? 30u : 31u);  // NaN: 31
+                }
+                code |= cls << 27;
+            }
+            keys[i] = code;
+            vals[i] = (uint32_t)i;
         }
-        keys[i] = code;
-        vals[i] = (uint32_t)i;
+        if (n_far) {
+            const unsigned m = __ballot_sync(0xffffffffu, far);
+            if ((threadIdx.x & 31) == 0 && m)
+                atomicAdd(n_far, (unsigned long long)__popc(m));
+        }
     }
 }
 
@@ -177,7 +192,8 @@ size_t morton_scratch_bytes(int64_t Q)
 // permutation of the queries along the Morton curve (stable: equal codes keep
 // their index order); perm receives traversal order -> query index
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s)
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s,
+                 unsigned long long *n_far)
 {
     Carve c{(char *)scratch};
     uint32_t *keys = c.take<uint32_t>(Q);
@@ -186,8 +202,10 @@ int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, c
     uint32_t *tv = c.take<uint32_t>(Q);
     uint32_t *rs = c.take<uint32_t>(radix_scratch_elems(Q));
     const bool cost = nodes && D <= 3 && T == 1;
+    if (n_far)
+        KDT_CUDA(cudaMemsetAsync(n_far, 0, sizeof(unsigned long long), s));
     KDT_LAUNCH morton_kernel<<<grid_1d(Q), 256, 0, s>>>(d_q, Q, D, bbox, T, d_qoff, cost ? nodes : nullptr, N, stored,
-                                                        keys, perm);
+                                                        keys, perm, cost ? n_far : nullptr);
     KDT_TRY(radix_sort_pairs(keys, perm, tk, tv, Q, cost ? 32 : 30, rs, s));
     if (T > 1) {
         KDT_LAUNCH tree_of_query_kernel<<<grid_1d(Q), 256, 0, s>>>(perm, Q, d_qoff, T, keys);
@@ -772,6 +790,60 @@ static int forest_enqueue(kdt_forest *f, ForestGraph *g, const float *d_q, int64
     a.inline_depth = f->inline_depth == 1 ? 1 : 2;
     a.light_run = f->light_run > 0 ? f->light_run : 1;
     return launch_query(layout_of(f->f.D), a, !(flags & KDT_UNORDERED), 0, true, s);
+}
+
+int kdt_knn_batched_visits(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int k, float max_radius,
+                           int flags, int32_t *d_visits, void *stream)
+{
+    if (!f || !h_qoff)
+        return set_error(KDT_EINVAL, "NULL forest or offsets");
+    const int T = f->f.T;
+    if (k < 1 || k > 64 || bad_radius(max_radius))
+        return set_error(KDT_EINVAL, "bad k or max_radius");
+    if (flags & (KDT_LEARNED | KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK))
+        return set_error(KDT_EINVAL, "forest visit counts are for the plain traversal");
+    if (h_qoff[0] != 0)
+        return set_error(KDT_EINVAL, "query offsets must start at 0");
+    for (int i = 0; i < T; ++i)
+        if (h_qoff[i + 1] < h_qoff[i])
+            return set_error(KDT_EINVAL, "query offsets must be non-decreasing");
+    if (h_qoff[T] == 0)
+        return KDT_OK;
+    if (!d_q || !d_visits)
+        return set_error(KDT_EINVAL, "NULL query or visits pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    KDT_TRY(sc.alloc(256));
+    const int layout = layout_of(f->f.D);
+    const int NF = float4_per_node(f->f.D);
+    // one counting launch per tree: the counts do not depend on how the
+    // queries are scheduled
+    for (int i = 0; i < T; ++i) {
+        const int64_t nq = h_qoff[i + 1] - h_qoff[i];
+        const int64_t nb = f->h_offsets[i];
+        const int64_t n = f->h_offsets[i + 1] - nb;
+        if (nq == 0)
+            continue;
+        if (n == 0) {
+            KDT_CUDA(cudaMemsetAsync(d_visits + h_qoff[i], 0, nq * 4, s));
+            continue;
+        }
+        QueryArgs a;
+        a.nodes = f->nodes + nb * NF;
+        a.ids = f->ids ? f->ids + nb : nullptr;
+        a.N = (int)n;
+        a.D = f->f.D;
+        a.queries = d_q + h_qoff[i] * f->f.D;
+        a.Q = nq;
+        a.k = k;
+        a.r2 = max_radius * max_radius;
+        a.visits = d_visits + h_qoff[i];
+        a.err = f->err;
+        a.counter = (unsigned long long *)sc.p;
+        a.claim_steps = default_claim_steps_k(k);
+        KDT_TRY(launch_query(layout, a, !(flags & KDT_UNORDERED), MODE_VISITS, false, s));
+    }
+    return KDT_OK;
 }
 
 int kdt_knn_batched(kdt_forest *f, const float *d_q, const int64_t *h_qoff, int k, float max_radius, int flags,

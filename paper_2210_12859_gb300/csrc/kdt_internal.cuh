@@ -161,9 +161,12 @@ int exclusive_scan_u64(unsigned long long *data, int64_t n, unsigned long long *
 
 int num_sms();
 
-// permutation of queries along the Morton curve (traversal order -> query index)
+// permutation of queries along the Morton curve (traversal order -> query index);
+// with cost classes (nodes given), n_far (device, may be NULL) receives the
+// number of queries in the far classes, which come first in the permutation
 int morton_order(const float *d_q, int64_t Q, int D, const float *bbox, int T, const int64_t *d_qoff, int tbits,
-                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s);
+                 const float4 *nodes, int64_t N, bool stored, void *scratch, uint32_t **perm_out, cudaStream_t s,
+                 unsigned long long *n_far = nullptr);
 size_t morton_scratch_bytes(int64_t Q);
 
 // ---------------------------------------------------------------- scratch
@@ -257,6 +260,8 @@ struct Model {
     float norm[8] = {0, 0, 0, 0, 1, 1, 1, 1};
     float margin = 1.25f;
     int k_trained = 0;
+    int gate = KDT_GATE_ALL;       // which queries get the proposal
+    float gate_cost = 0.f;         // network pass per query in processed-node equivalents (automatic gate)
 };
 
 struct ForestDesc {
@@ -283,6 +288,7 @@ struct kdt_tree {
     // learned-path statistics of the last learned query
     int64_t *stats = nullptr;      // device [2]: fallback count, sum of radius ratios (double bits)
     int64_t last_learned_q = 0;
+    int last_learned_gate = KDT_GATE_ALL;
     // top tree levels staged in shared memory by the traversal kernels
     // (-1: the tuned or default depth for this tree's shape)
     int stage_levels = -1;

@@ -418,6 +418,17 @@ int check_learned_tree(const kdt_tree *t)
     return KDT_OK;
 }
 
+// queries of the last learned call that took the proposal (counted: the far
+// queries the Morton pass counted, for KDT_GATE_FAR)
+int64_t learned_gated(const kdt_tree *t, int64_t counted)
+{
+    switch (t->last_learned_gate) {
+    case KDT_GATE_FAR: return counted;
+    case KDT_GATE_NONE: return 0;
+    default: return t->last_learned_q;
+    }
+}
+
 }  // namespace
 
 void fill_inf(float *p, int64_t n, cudaStream_t s)
@@ -443,6 +454,18 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     if (!t->model.trained)
         return set_error(KDT_ENOMODEL, "the tree has no trained radius model");
     KDT_TRY(ensure_stats(t));
+    const int gate = t->model.gate;
+    t->last_learned_q = Q;
+    t->last_learned_gate = gate;
+    // stats slots: [0] fallback count, [1] ratio sum (double bits), [2] gated queries
+    KDT_CUDA(cudaMemsetAsync(t->stats, 0, 3 * sizeof(int64_t), s));
+    if (gate == KDT_GATE_NONE)  // the proposal pays on none of these queries: the plain traversal
+        return run_query(t, d_q, Q, k, r2, flags & ~KDT_LEARNED, d_ids ? MODE_RESULTS : MODE_VISITS, d_ids, d_d2,
+                         d_visits, s);
+    // far queries only: their cost classes come first in the traversal order,
+    // and the Morton pass counts them
+    if (gate == KDT_GATE_FAR)
+        flags |= KDT_MORTON | KDT_COST_ORDER;
     const bool morton = flags & KDT_MORTON;
     size_t off_w = 0, off_r2 = 1 << 15;
     size_t off_m = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
@@ -452,15 +475,16 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     char *B = (char *)sc.p;
     float *wts = (float *)(B + off_w);                                  // P floats
     unsigned long long *counter = (unsigned long long *)(B + 20480);    // 3 x u64 after the weights
+    unsigned long long *n_far = gate == KDT_GATE_FAR ? (unsigned long long *)(B + 20736) : nullptr;
     float *r2q = (float *)(B + off_r2);
     uint32_t *perm = nullptr;
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
-                             t->N, t->layout == 3, B + off_m, &perm, s));
+                             t->N, t->layout == 3, B + off_m, &perm, s, n_far));
     KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
-    KDT_TRY(tc_radius(t, wts, d_q, Q, perm, r2, r2q, s));
-    // stats slots: [0] fallback count, [1] ratio sum (double bits)
-    KDT_CUDA(cudaMemsetAsync(t->stats, 0, 2 * sizeof(int64_t), s));
+    KDT_TRY(tc_radius(t, wts, d_q, Q, perm, r2, r2q, s, n_far));
+    if (n_far)
+        KDT_CUDA(cudaMemcpyAsync(t->stats + 2, n_far, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
 
     QueryArgs a;
     a.nodes = t->nodes;
@@ -483,11 +507,112 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.step_cap = t->debug_step_cap;
     a.inline_depth = inline_depth_for(t, k) >= 2 ? inline_depth_for(t, k) : 1;  // depth 0 is plain-query only
     a.r2q = r2q;
+    a.n_gate = n_far;
     a.fb_count = (unsigned long long *)t->stats;
     a.ratio_sum = (double *)(t->stats + 1);
     const bool ordered = !(flags & KDT_UNORDERED);
     KDT_TRY(launch_query(t->layout, a, ordered, MODE_BOUNDED, false, s));
-    t->last_learned_q = Q;
+    return KDT_OK;
+}
+
+// The automatic gate, from the training queries: the processed nodes the
+// plain traversal needs and those the learned forms need (all queries gated,
+// or the far ones), counted exactly, and the cost of the network pass (the
+// descent for the features, the MLP) per gated query in processed-node
+// equivalents: its time per query over the plain traversal's time per
+// processed node.  A form's score is the nodes it saves minus that cost times
+// the queries it gates; the best positive score wins, else no query is gated.
+// (Timing the whole forms on the training set does not transfer: at 2^20
+// queries the traversal's launch tail weighs differently than at full size.)
+int choose_gate(kdt_tree *t, const float *d_q, int64_t n, int k, int qflags, cudaStream_t s)
+{
+    qflags &= ~(KDT_LEARNED | KDT_PLAIN_STEP | KDT_CLOSE_FIRST | KDT_STACK);
+    Dev buf(s);
+    const size_t vis_b = ((size_t)n * 4 + 255) & ~(size_t)255;
+    const size_t out_b = ((size_t)n * k * 4 + 255) & ~(size_t)255;
+    KDT_CUDA(cudaMallocAsync(&buf.p, vis_b + 2 * out_b + 3 * vis_b + (1 << 15), s));
+    char *B = (char *)buf.p;
+    int32_t *vis = (int32_t *)B;
+    int32_t *ids = (int32_t *)(B + vis_b);
+    float *d2 = (float *)(B + vis_b + out_b);
+    float *r2q = (float *)(B + vis_b + 2 * out_b);
+    float *wts = (float *)(B + 4 * vis_b + 2 * out_b);
+    std::vector<int32_t> hv(n);
+    int rc = KDT_OK;
+    auto total = [&](double *out) {
+        if (rc != KDT_OK)
+            return;
+        if (cudaMemcpyAsync(hv.data(), vis, (size_t)n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = set_error(KDT_ECUDA, "visit count copy failed");
+            return;
+        }
+        double sum = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            sum += hv[i];
+        *out = sum;
+    };
+    double v_plain = 0, v_all = 0, v_far = 0;
+    rc = run_query(t, d_q, n, k, INFINITY, qflags, MODE_VISITS, nullptr, nullptr, vis, s);
+    total(&v_plain);
+    t->model.gate = KDT_GATE_ALL;
+    if (rc == KDT_OK)
+        rc = run_learned_query(t, d_q, n, k, INFINITY, qflags, nullptr, nullptr, vis, s);
+    total(&v_all);
+    t->model.gate = KDT_GATE_FAR;
+    if (rc == KDT_OK)
+        rc = run_learned_query(t, d_q, n, k, INFINITY, qflags, nullptr, nullptr, vis, s);
+    total(&v_far);
+    int64_t stats[3] = {0, 0, 0};
+    if (rc == KDT_OK && (cudaMemcpyAsync(stats, t->stats, sizeof(stats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess))
+        rc = set_error(KDT_ECUDA, "stats copy failed");
+    const double n_far = (double)stats[2];
+    // times: the plain query, and the network pass over all n queries
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == KDT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = set_error(KDT_ECUDA, "event create");
+    if (rc == KDT_OK)
+        KDT_LAUNCH round_params_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->model.d_params, wts);
+    auto best_of = [&](bool net, float *best) {
+        *best = 3.4e38f;
+        for (int rep = 0; rep < 4 && rc == KDT_OK; ++rep) {
+            float ms = 0.f;
+            if (cudaEventRecord(e0, s) != cudaSuccess)
+                rc = set_error(KDT_ECUDA, "event record");
+            if (rc == KDT_OK)
+                rc = net ? tc_radius(t, wts, d_q, n, nullptr, INFINITY, r2q, s)
+                         : run_query(t, d_q, n, k, INFINITY, qflags, MODE_RESULTS, ids, d2, nullptr, s);
+            if (rc == KDT_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = set_error(KDT_ECUDA, "event timing failed");
+            if (rep > 0 && ms < *best)
+                *best = ms;
+        }
+    };
+    float t_plain = 0.f, t_net = 0.f;
+    best_of(false, &t_plain);
+    best_of(true, &t_net);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (rc != KDT_OK)
+        return rc;
+    // network pass per query, in processed-node equivalents of the plain traversal
+    const double c = (t_net / (double)n) / (t_plain / std::max(v_plain, 1.0));
+    const double score_all = (v_plain - v_all) - c * (double)n;
+    const double score_far = (v_plain - v_far) - c * n_far;
+    int best = KDT_GATE_NONE;
+    double best_score = 0.0;
+    if (score_all > best_score) {
+        best = KDT_GATE_ALL;
+        best_score = score_all;
+    }
+    if (score_far > best_score)
+        best = KDT_GATE_FAR;
+    t->model.gate = best;
+    t->model.gate_cost = (float)c;
     return KDT_OK;
 }
 
@@ -581,7 +706,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     if (Qt > ((int64_t)1 << 26))
         return set_error(KDT_EINVAL, "at most 2^26 training queries");
     cudaStream_t s = (cudaStream_t)stream;
-    kdt_train_opts o{6, 1024, 2e-3f, 1, 0.f, 0.02f, 0};
+    kdt_train_opts o{6, 1024, 2e-3f, 1, 0.f, 0.02f, 0, KDT_GATE_AUTO, 0};
     if (opts) {
         if (opts->epochs > 0)
             o.epochs = opts->epochs;
@@ -595,7 +720,11 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         if (opts->fallback_target > 0)
             o.fallback_target = std::min(opts->fallback_target, 0.5f);
         o.uniform_weights = opts->uniform_weights;
+        o.gate = opts->gate;
+        o.query_flags = opts->query_flags;
     }
+    if (o.gate < KDT_GATE_AUTO || o.gate > KDT_GATE_NONE)
+        return set_error(KDT_EINVAL, "gate must be one of KDT_GATE_* (got %d)", o.gate);
     o.batch = std::max(TS, (o.batch / TS) * TS);
     KDT_TRY(ensure_params(t));
 
@@ -737,6 +866,12 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
     t->model.margin = margin;
     t->model.k_trained = k;
     t->model.trained = true;
+    if (o.gate != KDT_GATE_AUTO) {
+        t->model.gate = o.gate;
+    } else {
+        const int qf = o.query_flags ? o.query_flags : (KDT_MORTON | KDT_COST_ORDER);
+        KDT_TRY(choose_gate(t, d_q, std::min<int64_t>(Qt, (int64_t)1 << 20), k, qf, s));
+    }
     if (final_loss)
         *final_loss = last;
     return KDT_OK;
@@ -785,9 +920,10 @@ int kdt_radius_model_save(const kdt_tree *t, const char *path)
     FILE *f = fopen(path, "wb");
     if (!f)
         return set_error(KDT_EIO, "cannot open %s for writing", path);
-    int32_t hdr[4] = {1, H, P, t->model.k_trained};
+    int32_t hdr[4] = {2, H, P, t->model.k_trained};
+    const int32_t gate = t->model.gate;
     bool ok = fwrite(MODEL_MAGIC, 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 && fwrite(norm, 4, 8, f) == 8 &&
-              fwrite(&margin, 4, 1, f) == 1 && fwrite(p.data(), 4, P, f) == (size_t)P;
+              fwrite(&margin, 4, 1, f) == 1 && fwrite(p.data(), 4, P, f) == (size_t)P && fwrite(&gate, 4, 1, f) == 1;
     ok = (fclose(f) == 0) && ok;
     return ok ? KDT_OK : set_error(KDT_EIO, "write to %s failed", path);
 }
@@ -804,14 +940,53 @@ int kdt_radius_model_load(kdt_tree *t, const char *path)
     int32_t hdr[4];
     float norm[8], margin;
     std::vector<float> p(P);
+    // version 1: no gate (every query takes the proposal); version 2: the gate follows the parameters
+    int32_t gate = KDT_GATE_ALL;
     bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, MODEL_MAGIC, 8) == 0 && fread(hdr, 4, 4, f) == 4 &&
-              hdr[0] == 1 && hdr[1] == H && hdr[2] == P && fread(norm, 4, 8, f) == 8 && fread(&margin, 4, 1, f) == 1 &&
-              fread(p.data(), 4, P, f) == (size_t)P;
+              (hdr[0] == 1 || hdr[0] == 2) && hdr[1] == H && hdr[2] == P && fread(norm, 4, 8, f) == 8 &&
+              fread(&margin, 4, 1, f) == 1 && fread(p.data(), 4, P, f) == (size_t)P &&
+              (hdr[0] == 1 || (fread(&gate, 4, 1, f) == 1 && gate >= KDT_GATE_ALL && gate <= KDT_GATE_NONE));
     fclose(f);
     if (!ok)
-        return set_error(KDT_EIO, "%s is not a radius model file of this version", path);
+        return set_error(KDT_EIO, "%s is not a radius model file of a known version", path);
     KDT_TRY(kdt_radius_model_set(t, p.data(), norm, margin));
     t->model.k_trained = hdr[3];
+    t->model.gate = gate;
+    return KDT_OK;
+}
+
+int kdt_radius_model_gate(const kdt_tree *t, int *gate)
+{
+    if (!t || !gate)
+        return set_error(KDT_EINVAL, "tree or out pointer is NULL");
+    if (!t->model.trained)
+        return set_error(KDT_ENOMODEL, "the tree has no radius model");
+    *gate = t->model.gate;
+    return KDT_OK;
+}
+
+int kdt_radius_model_set_gate(kdt_tree *t, int gate)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (!t->model.trained)
+        return set_error(KDT_ENOMODEL, "the tree has no radius model");
+    if (gate < KDT_GATE_ALL || gate > KDT_GATE_NONE)
+        return set_error(KDT_EINVAL, "gate must be KDT_GATE_ALL, KDT_GATE_FAR or KDT_GATE_NONE (got %d)", gate);
+    t->model.gate = gate;
+    return KDT_OK;
+}
+
+int kdt_learned_gated(const kdt_tree *t, int64_t *gated, void *stream)
+{
+    if (!t || !gated)
+        return set_error(KDT_EINVAL, "tree or out pointer is NULL");
+    if (!t->stats)
+        return set_error(KDT_ENOMODEL, "no learned query has run on this tree");
+    int64_t h[3];
+    KDT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    KDT_CUDA(cudaMemcpy(h, t->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    *gated = learned_gated(t, h[2]);
     return KDT_OK;
 }
 
@@ -821,12 +996,13 @@ int kdt_learned_stats(const kdt_tree *t, int64_t *fallbacks, double *radius_rati
         return set_error(KDT_EINVAL, "tree is NULL");
     if (!t->stats)
         return set_error(KDT_ENOMODEL, "no learned query has run on this tree");
-    int64_t h[2];
+    int64_t h[3];
     KDT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     KDT_CUDA(cudaMemcpy(h, t->stats, sizeof(h), cudaMemcpyDeviceToHost));
     double ratio_sum;
     memcpy(&ratio_sum, &h[1], 8);
-    const int64_t exact = t->last_learned_q - h[0];
+    const int64_t gated = learned_gated(t, h[2]);
+    const int64_t exact = gated - h[0];
     if (fallbacks)
         *fallbacks = h[0];
     if (radius_ratio)

@@ -14,9 +14,10 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
               float *d_d2, int32_t *d_visits, cudaStream_t s);
 void free_model(kdt_tree *t);
 // tensor-core inference (kdt_mlp_tc.cu): per-query cull radius of the learned
-// pass, and the model output for given normalised features
+// pass (for the first *n_lim queries of perm when n_lim is given), and the
+// model output for given normalised features
 int tc_radius(const kdt_tree *t, const float *wts, const float *d_q, int64_t Q, const uint32_t *perm, float r2_user,
-              float *r2q, cudaStream_t s);
+              float *r2q, cudaStream_t s, const unsigned long long *n_lim = nullptr);
 int tc_forward(const float *wts, const float *d_x, int64_t n, float *d_y, int *d_err, cudaStream_t s);
 void fill_inf(float *p, int64_t n, cudaStream_t s);
 }  // namespace kdt

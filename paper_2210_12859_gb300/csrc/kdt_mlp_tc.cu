@@ -111,6 +111,7 @@ struct TcArgs {
     float mu[4], sd[4];
     float margin, r2_user;
     float *r2q;
+    const unsigned long long *n_lim;  // radius mode: only the first *n_lim entries of perm (NULL: all n)
     // forward mode
     const float *x;            // normalised features [n][4]
     float *y;
@@ -162,10 +163,13 @@ __global__ void __launch_bounds__(TILE_M) mlp_tc_kernel(const TcArgs a)
     const float b3 = w3[H];
 
     uint32_t phase = 0;
-    const int64_t tiles = (a.n + TILE_M - 1) / TILE_M;
+    int64_t n = a.n;
+    if (MODE == 0 && a.n_lim)
+        n = min(n, (int64_t)*a.n_lim);
+    const int64_t tiles = (n + TILE_M - 1) / TILE_M;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t i = tile * TILE_M + tid;
-        const bool valid = i < a.n;
+        const bool valid = i < n;
         int64_t qi = 0;
         float x[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid) {
@@ -287,9 +291,10 @@ int launch_tc(int mode, const TcArgs &a, cudaStream_t s)
 }  // namespace
 
 int tc_radius(const kdt_tree *t, const float *wts, const float *d_q, int64_t Q, const uint32_t *perm, float r2_user,
-              float *r2q, cudaStream_t s)
+              float *r2q, cudaStream_t s, const unsigned long long *n_lim)
 {
     TcArgs a{};
+    a.n_lim = n_lim;
     a.wts = wts;
     a.n = Q;
     a.nodes = t->nodes;

@@ -38,6 +38,7 @@ struct QueryArgs {
     const int64_t *q_off = nullptr;    // [T+1]
     // learned radius proposal
     const float *r2q = nullptr;        // per-query cull radius of the bounded pass (mode 2)
+    const unsigned long long *n_gate = nullptr;  // mode 2: only slots below *n_gate take r2q (NULL: all)
     unsigned long long *fb_count = nullptr;
     double *ratio_sum = nullptr;       // sum of proposed / true k-th radius (mode 2, exact queries)
 };

@@ -13,13 +13,13 @@ namespace kdt {
 // neighbour in its warp is still traversing, until the work runs out.
 // Register-list kernels with k <= 8 are built for at least 6 resident blocks
 // per SM (at most 85 registers a thread; without the bound the depth-2 kernel
-// once took 82 registers and 5 blocks fit); the learned radius's bounded
-// kernel for 7.  With the bottom subtrees handled as scalar keys the depth-2
-// kernel needs 64 registers (8 blocks) and the bounded one 72, both without
-// spills, so the bounds now only guard against regressions.
+// once took 82 registers and 5 blocks fit), the learned radius's bounded
+// kernel included, so that it runs with the plain kernel's occupancy.  With
+// the bottom subtrees handled as scalar keys the depth-2 kernel needs 64
+// registers (8 blocks) and the depth-3 one 79, both without spills, so the
+// bounds only guard against regressions.
 template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE, bool RUNS = false>
-__global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
-                                  K <= 8 ? (MODE == MODE_BOUNDED ? 7 : 6) : 1)
+__global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS, K <= 8 ? 6 : 1)
     knn_kernel(const QueryArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
@@ -32,6 +32,10 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         __syncthreads();
     }
     const int64_t Qn = a.Q;
+    // learned radius: the traversal-order slots below n_gate take the
+    // proposal, the others the caller's radius
+    const int64_t ngate = (MODE == MODE_BOUNDED && a.n_gate) ? (int64_t)*a.n_gate : INT64_MAX;
+    bool gated = false;
     double ratio = 0.0;
     int64_t qi = -1;
     bool exhausted = false;
@@ -50,7 +54,8 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         if (need) {
             if (slot < Qn) {
                 qi = a.perm ? (int64_t)a.perm[slot] : slot;
-                r2 = MODE == MODE_BOUNDED ? a.r2q[qi] : a.r2;
+                gated = MODE == MODE_BOUNDED && slot < ngate;
+                r2 = gated ? a.r2q[qi] : a.r2;
                 load_query<LAYOUT>(a.queries, qi, a.D, q);
                 list.init(a.k, r2);
                 w.start();
@@ -87,6 +92,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
         const bool fallback = MODE == MODE_BOUNDED && !(full || r2 == a.r2);
         if (fallback) {
             atomicAdd(a.fb_count, 1ull);
+            gated = false;
             r2 = a.r2;
             list.init(a.k, r2);
             w.start();
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS,
             list.store(a.k, a.out_ids + qi * a.k, a.out_d2 + qi * a.k);
         if (MODE == MODE_VISITS || (MODE == MODE_BOUNDED && a.visits))
             a.visits[qi] = overflow ? -1 : visits;
-        if (MODE == MODE_BOUNDED && full && list.cull() > 0.f && r2 < __int_as_float(0x7f800000))
+        if (MODE == MODE_BOUNDED && gated && full && list.cull() > 0.f && r2 < __int_as_float(0x7f800000))
             ratio += sqrt((double)r2 / (double)list.cull());
         qi = -1;
     }
@@ -205,6 +211,16 @@ inline int launch_mode(const QueryArgs &a, bool ordered, int mode, int threads, 
         return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, STAGE, INLINE>, threads, smem, a, s);
     case MODE_BOUNDED:
         if constexpr (LAYOUT == 0 || LAYOUT == 3) {
+            // light runs as for the plain traversal (the same tuned value)
+            if constexpr (!STAGE) {
+                if (a.light_run > 1) {
+                    if (ordered)
+                        return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, false, INLINE, true>, threads,
+                                             smem, a, s);
+                    return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, false, INLINE, true>, threads,
+                                         smem, a, s);
+                }
+            }
             if (ordered)
                 return launch_kernel(knn_kernel<LAYOUT, K, true, MODE_BOUNDED, STAGE, INLINE>, threads, smem, a, s);
             return launch_kernel(knn_kernel<LAYOUT, K, false, MODE_BOUNDED, STAGE, INLINE>, threads, smem, a, s);

@@ -47,6 +47,7 @@ KDT_BUILD_ASYNC = 0x1
 KDT_REDUCE_SUM, KDT_REDUCE_MEAN, KDT_REDUCE_DENSITY = 0, 1, 2
 KDT_PAYLOAD_MAX_C = 8
 KDT_BUILD_WIDEST = 0x2
+KDT_GATE_AUTO, KDT_GATE_ALL, KDT_GATE_FAR, KDT_GATE_NONE = 0, 1, 2, 3
 
 MLP_HIDDEN = 64
 MLP_PARAMS = 64 * 4 + 64 + 64 * 64 + 64 + 64 + 1
@@ -68,7 +69,7 @@ _D = ctypes.c_double
 class TrainOpts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("margin", ctypes.c_float), ("fallback_target", ctypes.c_float),
-                ("uniform_weights", ctypes.c_int)]
+                ("uniform_weights", ctypes.c_int), ("gate", ctypes.c_int), ("query_flags", ctypes.c_int)]
 
 
 def _sig(name, args, res=_I):
@@ -108,6 +109,7 @@ _sig("kdt_knn_batched", [_P, _P, _P, _I, _F, _I, _P, _P, _P])
 _sig("kdt_forest_export", [_P, _P, _P, _P])
 _sig("kdt_forest_free", [_P], None)
 _sig("kdt_forest_set_launch", [_P, _I, _I, _I, _I])
+_sig("kdt_knn_batched_visits", [_P, _P, _P, _I, _F, _I, _P, _P])
 _sig("kdt_forest_autotune", [_P, _P, _P, _I, _F, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_profile_enable", [_P, _I])
@@ -122,6 +124,7 @@ _sig("kdt_autotune", [_P, _P, _I64, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_
 _sig("kdt_tuning_save", [ctypes.c_char_p])
 _sig("kdt_tuning_load", [ctypes.c_char_p])
 _sig("kdt_profile_read", [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)])
+_sig("kdt_l2_read_bandwidth", [_I64, _I, ctypes.POINTER(_D), _P])
 
 _OPTIONAL = {}
 
@@ -142,6 +145,9 @@ _optional("kdt_descent_features", [_P, _P, _I64, _P, _P])
 _optional("kdt_mlp_forward", [_P, _P, _I64, _P, _P])
 _optional("kdt_mlp_loss_grad", [_P, _P, _P, _I64, ctypes.POINTER(_F), _P, _P])
 _optional("kdt_learned_stats", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), _P])
+_optional("kdt_learned_gated", [_P, ctypes.POINTER(_I64), _P])
+_optional("kdt_radius_model_gate", [_P, ctypes.POINTER(_I)])
+_optional("kdt_radius_model_set_gate", [_P, _I])
 
 
 def _check(rc: int):
@@ -552,6 +558,18 @@ def kdt_knn_batched(forest: Forest, queries: torch.Tensor, qoffsets, k: int, max
     return out_ids, out_d2
 
 
+def kdt_knn_batched_visits(forest: Forest, queries: torch.Tensor, qoffsets, k: int, max_radius: float = math.inf,
+                           flags: int = 0, stream=None) -> torch.Tensor:
+    """Processed nodes of every query of the batched kNN (int32 [total queries])."""
+    qoff = np.ascontiguousarray(qoffsets, dtype=np.int64)
+    Q = int(qoff[-1])
+    v = torch.empty(Q, dtype=torch.int32, device=queries.device)
+    _check(_lib.kdt_knn_batched_visits(forest.handle, _dev(queries, torch.float32, "queries", (Q, forest.D)),
+                                       ctypes.c_void_p(qoff.ctypes.data), k, float(max_radius), flags,
+                                       _dev(v, torch.int32, "visits", (Q,)), _stream(stream)))
+    return v
+
+
 def kdt_forest_set_launch(forest: Forest, threads: int = 0, claim_steps: int = 0, inline_depth: int = 0,
                           light_run: int = 0) -> None:
     _check(_lib.kdt_forest_set_launch(forest.handle, threads, claim_steps, inline_depth, light_run))
@@ -597,8 +615,10 @@ def _need(name):
 
 def kdt_radius_model_train(tree: Tree, train_queries: torch.Tensor, k: int, epochs: int = 0, batch: int = 0,
                            lr: float = 0.0, seed: int = 0, margin: float = 0.0, fallback_target: float = 0.0,
-                           uniform_weights: bool = False, stream=None) -> float:
-    opts = TrainOpts(epochs, batch, lr, seed, margin, fallback_target, int(uniform_weights))
+                           uniform_weights: bool = False, gate: int = KDT_GATE_AUTO, query_flags: int = 0,
+                           stream=None) -> float:
+    opts = TrainOpts(epochs, batch, lr, seed, margin, fallback_target, int(uniform_weights), int(gate),
+                     int(query_flags))
     loss = _F()
     Qt = train_queries.shape[0]
     _check(_need("kdt_radius_model_train")(tree.handle, _dev(train_queries, torch.float32, "train_queries",
@@ -664,3 +684,27 @@ def kdt_learned_stats(tree: Tree, stream=None):
     ratio = _D()
     _check(_need("kdt_learned_stats")(tree.handle, ctypes.byref(fb), ctypes.byref(ratio), _stream(stream)))
     return fb.value, ratio.value
+
+
+def kdt_learned_gated(tree: Tree, stream=None) -> int:
+    """Queries of the last learned call that took the proposed radius."""
+    n = _I64()
+    _check(_need("kdt_learned_gated")(tree.handle, ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def kdt_radius_model_gate(tree: Tree) -> int:
+    g = _I()
+    _check(_need("kdt_radius_model_gate")(tree.handle, ctypes.byref(g)))
+    return g.value
+
+
+def kdt_radius_model_set_gate(tree: Tree, gate: int) -> None:
+    _check(_need("kdt_radius_model_set_gate")(tree.handle, int(gate)))
+
+
+def kdt_l2_read_bandwidth(nbytes: int = 32 << 20, reps: int = 200, stream=None) -> float:
+    """L2 read bandwidth of the current GPU in GB/s (the library's own probe kernel)."""
+    v = _D()
+    _check(_lib.kdt_l2_read_bandwidth(int(nbytes), int(reps), ctypes.byref(v), _stream(stream)))
+    return v.value

@@ -87,6 +87,23 @@ def test_forest_knn_equals_oracle(kdt, forest, flags_name, k, r):
             assert np.array_equal(bits(gd[qoff[i]:qoff[i + 1]]), bits(wd)), i
 
 
+@pytest.mark.parametrize("k,r,unordered", [(8, math.inf, False), (3, 0.05, True), (20, math.inf, False)])
+def test_forest_visits_equal_oracle(kdt, forest, k, r, unordered):
+    """Processed nodes of every forest query equal the oracle machine's on
+    that cloud's own tree (0 for queries of an empty cloud)."""
+    pts, qs, P, Q, off, qoff, f = forest
+    flags = kdt.KDT_UNORDERED if unordered else 0
+    v = kdt.kdt_knn_batched_visits(f, cu(Q), qoff, k, r, flags).cpu().numpy()
+    for i, (p, q) in enumerate(zip(pts, qs)):
+        if len(q) == 0:
+            continue
+        if len(p) == 0:
+            assert (v[qoff[i]:qoff[i + 1]] == 0).all()
+            continue
+        _, _, wv = oracle.knn_tree(p, oracle.build(p), q, k, r, ordered=not unordered)
+        assert np.array_equal(v[qoff[i]:qoff[i + 1]], wv), i
+
+
 def test_forest_graph_recaptures_on_new_arguments(kdt, forest):
     pts, qs, P, Q, off, qoff, f = forest
     dq = cu(Q)

@@ -119,7 +119,8 @@ def test_mlp_gradients_match_oracle(kdt):
 def trained(kdt, surface):
     pts, qs, tree = surface
     train = cu(qs[: 1 << 15])
-    loss = kdt.kdt_radius_model_train(tree, train, 8, epochs=10, batch=1024, seed=7)
+    # every query takes the proposal: these tests look at the proposal itself
+    loss = kdt.kdt_radius_model_train(tree, train, 8, epochs=10, batch=1024, seed=7, gate=kdt.KDT_GATE_ALL)
     return loss
 
 
@@ -223,6 +224,12 @@ def test_model_save_load_roundtrip(kdt, surface, trained, tmp_path):
     kdt.kdt_radius_model_load(other, path)
     p2, n2, m2 = kdt.kdt_radius_model_get(other)
     assert np.array_equal(p1, p2) and np.array_equal(n1, n2) and m1 == m2
+    assert kdt.kdt_radius_model_gate(other) == kdt.kdt_radius_model_gate(tree)
+    kdt.kdt_radius_model_set_gate(other, kdt.KDT_GATE_FAR)
+    kdt.kdt_radius_model_save(other, path)
+    third = kdt.kdt_build(cu(pts))
+    kdt.kdt_radius_model_load(third, path)
+    assert kdt.kdt_radius_model_gate(third) == kdt.KDT_GATE_FAR
     q = cu(qs[1 << 15: (1 << 15) + 5000])
     a = kdt.kdt_knn(tree, q, 8, flags=kdt.KDT_LEARNED)
     b = kdt.kdt_knn(other, q, 8, flags=kdt.KDT_LEARNED)
@@ -243,3 +250,71 @@ def test_learned_rejects_untrained_and_high_dim(kdt):
     with pytest.raises(kdt.KdtError) as e:
         kdt.kdt_knn(t3, cu(pts[:10, :3].copy()), 8, flags=kdt.KDT_LEARNED)
     assert e.value.code == kdt.KDT_ENOMODEL
+
+
+@pytest.fixture(scope="module")
+def clustered(kdt):
+    """Clustered points with 10 % of the queries between the clusters, and a
+    model trained on them (every query gated)."""
+    mix = synth.gmm_mixture(64, 3, 0.01, 21)
+    pts = synth.gmm_sample(mix, 1 << 18, 22)
+    train = synth.gmm_queries(mix, 1 << 15, 0.1, 23)
+    qs = synth.gmm_queries(mix, 30001, 0.1, 24)
+    tree = kdt.kdt_build(cu(pts))
+    kdt.kdt_radius_model_train(tree, cu(train), 8, epochs=8, batch=1024, seed=9, gate=kdt.KDT_GATE_ALL)
+    return pts, qs, tree
+
+
+@pytest.mark.parametrize("flags_name", ["MORTON", "MORTON|COST_ORDER", "ORDERED", "UNORDERED"])
+def test_every_gate_equals_plain(kdt, clustered, flags_name):
+    """All queries, the far ones only, or none take the proposal: the same
+    results and, with no query gated, the plain method's processed nodes.  The
+    far gate takes the queries whose greedy descent ends far outside the data,
+    about the 10 % drawn between the clusters."""
+    pts, qs, tree = clustered
+    flags = 0
+    for n in flags_name.split("|"):
+        flags |= getattr(kdt, "KDT_" + n)
+    q = cu(qs)
+    Q = qs.shape[0]
+    pi, pd = kdt.kdt_knn(tree, q, 8, flags=flags)
+    pv = kdt.kdt_knn_visits(tree, q, 8, flags=flags)
+    for gate in (kdt.KDT_GATE_ALL, kdt.KDT_GATE_FAR, kdt.KDT_GATE_NONE):
+        kdt.kdt_radius_model_set_gate(tree, gate)
+        assert kdt.kdt_radius_model_gate(tree) == gate
+        li, ld = kdt.kdt_knn(tree, q, 8, flags=flags | kdt.KDT_LEARNED)
+        assert torch.equal(pi, li) and torch.equal(pd.view(torch.int32), ld.view(torch.int32)), gate
+        gated = kdt.kdt_learned_gated(tree)
+        fb, ratio = kdt.kdt_learned_stats(tree)
+        assert 0 <= fb <= gated
+        if gate == kdt.KDT_GATE_ALL:
+            assert gated == Q
+        elif gate == kdt.KDT_GATE_FAR:
+            assert 0.05 * Q < gated < 0.15 * Q, gated
+            assert ratio >= 1.0
+        else:
+            assert gated == 0 and fb == 0
+            assert torch.equal(kdt.kdt_knn_visits(tree, q, 8, flags=flags | kdt.KDT_LEARNED), pv)
+    kdt.kdt_radius_model_set_gate(tree, kdt.KDT_GATE_ALL)
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_radius_model_set_gate(tree, 7)
+    kdt.kdt_status(tree)
+
+
+def test_automatic_gate(kdt, clustered):
+    """Training with the default gate times the plain and the gated forms on
+    the training queries and keeps one of them; the results stay the plain
+    method's."""
+    pts, qs, _ = clustered
+    mix = synth.gmm_mixture(64, 3, 0.01, 21)
+    tree = kdt.kdt_build(cu(pts))
+    kdt.kdt_radius_model_train(tree, cu(synth.gmm_queries(mix, 1 << 15, 0.1, 25)), 8, epochs=4, batch=1024, seed=2)
+    assert kdt.kdt_radius_model_gate(tree) in (kdt.KDT_GATE_ALL, kdt.KDT_GATE_FAR, kdt.KDT_GATE_NONE)
+    q = cu(qs)
+    flags = kdt.KDT_MORTON | kdt.KDT_COST_ORDER
+    pi, pd = kdt.kdt_knn(tree, q, 8, flags=flags)
+    li, ld = kdt.kdt_knn(tree, q, 8, flags=flags | kdt.KDT_LEARNED)
+    assert torch.equal(pi, li) and torch.equal(pd.view(torch.int32), ld.view(torch.int32))
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_radius_model_train(tree, cu(qs[:2048]), 8, epochs=1, gate=9)
+    kdt.kdt_status(tree)
