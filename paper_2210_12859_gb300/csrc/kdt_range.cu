@@ -10,7 +10,10 @@
 //   ACT_COUNT   count the hits;
 //   ACT_FILL    write the hits to the query's slice [offsets[q], offsets[q+1])
 //               in traversal order (count and fill walk the same nodes in the
-//               same order, so no atomics are needed);
+//               same order, so no atomics are needed); hits from the first
+//               16-byte boundary of the slice on are collected four at a time
+//               in registers and written as 16-byte stores, the slice's
+//               unaligned head and its last partial group one word at a time;
 //   ACT_REDUCE  sum a per-point payload over the hits in traversal order (the
 //               point types with payload, e.g. photon power, that Sec. 3 names;
 //               the fixed-radius photon-map density estimate on top).
@@ -50,6 +53,7 @@ struct RangeArgs {
     int mode;              // KDT_REDUCE_*
     float *out;            // [Q][C] (ACT_REDUCE)
     bool count_visits;     // ACT_COUNT: count processed nodes instead of hits
+    bool vec_fill;         // ACT_FILL: outputs 16-byte aligned, groups of four hits stored at once
     int *err;
     unsigned long long *counter;
 };
@@ -92,6 +96,10 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
     int curr = 0, prev = -1, dim = 0;
     uint32_t steps = 0;
     int64_t count = 0, base = 0, limit = 0, visits = 0;
+    // fill: the last `ns` hits (ns < 4) not yet written, newest in the last slot
+    int32_t sid0 = 0, sid1 = 0, sid2 = 0, sid3 = 0;
+    float sd20 = 0.f, sd21 = 0.f, sd22 = 0.f, sd23 = 0.f;
+    int ns = 0;
     const uint32_t cap = 3u * (uint32_t)a.N + 3u;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
@@ -111,6 +119,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                 if (ACT == ACT_FILL) {
                     base = a.offsets[qi];
                     limit = a.offsets[qi + 1] - base;
+                    ns = 0;
                 }
                 if (ACT == ACT_REDUCE) {
 #pragma unroll
@@ -150,9 +159,24 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
                 }
                 if (hit) {
                     if (ACT == ACT_FILL && count < limit) {
-                        a.out_ids[base + count] = (int32_t)node_id<LAYOUT>(nd, a.ids, curr);
-                        if (KIND == 0 && a.out_d2)
-                            a.out_d2[base + count] = d2;
+                        const int32_t id = (int32_t)node_id<LAYOUT>(nd, a.ids, curr);
+                        const int64_t pos = base + count;
+                        if (!a.vec_fill || (ns == 0 && (pos & 3) != 0)) {
+                            // before the slice's first 16-byte boundary (or unaligned outputs)
+                            a.out_ids[pos] = id;
+                            if (KIND == 0 && a.out_d2)
+                                a.out_d2[pos] = d2;
+                        } else {
+                            sid0 = sid1; sid1 = sid2; sid2 = sid3; sid3 = id;
+                            sd20 = sd21; sd21 = sd22; sd22 = sd23; sd23 = d2;
+                            if (++ns == 4) {  // positions pos - 3 .. pos, pos - 3 on a 16-byte boundary
+                                *reinterpret_cast<int4 *>(a.out_ids + pos - 3) = make_int4(sid0, sid1, sid2, sid3);
+                                if (KIND == 0 && a.out_d2)
+                                    *reinterpret_cast<float4 *>(a.out_d2 + pos - 3) =
+                                        make_float4(sd20, sd21, sd22, sd23);
+                                ns = 0;
+                            }
+                        }
                     }
                     if (ACT == ACT_REDUCE) {
                         const float *p = a.payload + (int64_t)curr * a.C;
@@ -202,6 +226,24 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
         if (!done)
             continue;
         if (ACT == ACT_FILL) {
+            // the last partial group: the newest ns hits end at position base + min(count, limit) - 1
+            const int64_t end = base + (count < limit ? count : limit);
+            if (ns >= 3) {
+                a.out_ids[end - 3] = sid1;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 3] = sd21;
+            }
+            if (ns >= 2) {
+                a.out_ids[end - 2] = sid2;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 2] = sd22;
+            }
+            if (ns >= 1) {
+                a.out_ids[end - 1] = sid3;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 1] = sd23;
+            }
+            ns = 0;
             if (count != limit)
                 atomicOr(a.err, ERR_RANGE);
         } else {
@@ -352,6 +394,12 @@ RangeArgs blank_args()
     return a;
 }
 
+// 16-byte stores of the fill pass only into 16-byte aligned outputs
+bool fill_vectorizable(const int32_t *ids, const float *d2)
+{
+    return ((uintptr_t)ids & 15u) == 0 && ((uintptr_t)d2 & 15u) == 0;
+}
+
 }  // namespace
 }  // namespace kdt
 
@@ -395,6 +443,7 @@ int kdt_radius_fill(const kdt_tree *t, const float *d_q, int64_t Q, float radius
     a.offsets = d_offsets;
     a.out_ids = d_ids;
     a.out_d2 = d_d2;
+    a.vec_fill = fill_vectorizable(d_ids, d_d2);
     return run_range(t, 0, ACT_FILL, flags, a, (cudaStream_t)stream);
 }
 
@@ -431,6 +480,7 @@ int kdt_box_fill(const kdt_tree *t, const float *d_lo, const float *d_hi, int64_
     a.Q = Q;
     a.offsets = d_offsets;
     a.out_ids = d_ids;
+    a.vec_fill = fill_vectorizable(d_ids, nullptr);
     return run_range(t, 1, ACT_FILL, flags, a, (cudaStream_t)stream);
 }
 

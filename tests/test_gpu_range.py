@@ -193,6 +193,56 @@ def test_fill_is_deterministic_and_matches_knn(kdt):
         assert np.all(kid[q, m:] == -1)
 
 
+@pytest.mark.parametrize("kind", ["ball", "box"])
+def test_fill_vector_and_word_paths_agree(kdt, kind):
+    """The fill pass writes 16-byte groups into aligned outputs and single
+    words otherwise (here: outputs one word past a 16-byte boundary).  Both
+    give the oracle machine's hits in traversal order, over slices of every
+    start alignment and length (0 to dozens of hits)."""
+    import ctypes
+
+    mix = synth.gmm_mixture(16, 3, 0.02, 8)
+    pts = synth.gmm_sample(mix, 40000, 9)
+    qs = np.concatenate([synth.gmm_sample(mix, 3000, 10), synth.uniform(200, 3, seed=11)])
+    tree = kdt.kdt_build(cu(pts))
+    dq = cu(qs)
+    r = 0.005
+    lo, hi = (dq - r).contiguous(), (dq + r).contiguous()
+    counts = kdt.kdt_radius_count(tree, dq, r) if kind == "ball" else kdt.kdt_box_count(tree, lo, hi)
+    off, total = kdt.kdt_offsets(counts)
+    assert total > 0
+    res = []
+    for shift in (0, 1):
+        ids = torch.full((total + 8,), -5, dtype=torch.int32, device="cuda")
+        d2 = torch.full((total + 8,), -5.0, dtype=torch.float32, device="cuda")
+        pi, pd = ids.data_ptr() + 4 * shift, d2.data_ptr() + 4 * shift
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        if kind == "ball":
+            rc = kdt._lib.kdt_radius_fill(tree.handle, ctypes.c_void_p(dq.data_ptr()), len(qs), ctypes.c_float(r), 0,
+                                          ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(pi), ctypes.c_void_p(pd),
+                                          stream)
+        else:
+            rc = kdt._lib.kdt_box_fill(tree.handle, ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                                       len(qs), 0, ctypes.c_void_p(off.data_ptr()), ctypes.c_void_p(pi), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        kdt.kdt_status(tree)
+        ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
+        # nothing outside the written range was touched
+        assert (ids[:shift] == -5).all() and (ids[shift + total:] == -5).all()
+        res.append((ids[shift:shift + total], d2[shift:shift + total]))
+    assert np.array_equal(res[0][0], res[1][0])
+    if kind == "ball":
+        assert np.array_equal(bits(res[0][1]), bits(res[1][1]))
+    node_pid = oracle.build(pts)
+    if kind == "ball":
+        _, woff, wids, wd2 = oracle.range_tree(pts, node_pid, qs, radius=r)
+        assert np.array_equal(bits(res[0][1]), bits(wd2))
+    else:
+        _, woff, wids = oracle.range_tree(pts, node_pid, qs - np.float32(r), qs + np.float32(r))[:3]
+    assert np.array_equal(off.cpu().numpy(), woff) and np.array_equal(res[0][0], wids)
+
+
 def test_full_size_sampled(kdt):
     """2^22 clustered points, 2^18 queries: counts and sampled hit sets equal brute force."""
     mix = synth.gmm_mixture(64, 3, 0.01, 11)
