@@ -306,7 +306,9 @@ def run_config(args):
             _emit(config="gmm_large N=Q=2^24", form=f"{'fcp' if k == 1 else f'kNN k={k}'}, r={r}",
                   query_qps=n / (ms / 1e3), query_ms=ms, visits_per_query=v,
                   launch_autotuned=dict(zip(("stage_levels", "claim_steps", "inline_depth", "light_run"),
-                                            kdt.kdt_tuned_params(tree, k))),
+                                            kdt.kdt_tuned_params(tree, k)),
+                                        large_k_list=["shared heap", "global heap", "group of 4",
+                                                      "group of 8"][kdt.kdt_large_k_list(tree, k)]),
                   bit_exact_sample=_exact(oracle, pts, qs, gi.cpu().numpy(), gd.cpu().numpy(), k, r, n=32))
             del gi, gd
         del tree, dp, dq

@@ -449,6 +449,28 @@ int kdt_set_inline_depth(kdt_tree *tree, int depth);
  * nodes are the same for every value. */
 int kdt_set_light_run(kdt_tree *tree, int steps);
 
+/* Where the k-best lists of queries with k > 16 live (no paper counterpart; a
+ * placement choice of the GPU kernel, results and processed nodes are the same
+ * for every choice).  KDT_LIST_SHARED: a per-thread binary max-heap in shared
+ * memory (k x 8 bytes per thread, which limits the resident blocks and takes
+ * the on-chip array that L1 shares).  KDT_LIST_GLOBAL: the same heap in a
+ * per-thread slice of a scratch buffer in device memory (about
+ * SMs x 1024 x k x 8 bytes per call, allocated with the call's scratch),
+ * cached in L1 / L2 beside the tree.  -1 restores the default. */
+#define KDT_LIST_SHARED 0
+#define KDT_LIST_GLOBAL 1
+/* KDT_LIST_GROUP4 / 8: a sorted list spread over a group of 4 (8) lanes that
+ * walk the query together, k / 4 (k / 8) keys in each lane's registers,
+ * insertion by warp shuffles (ordered and unordered kNN and visit counts;
+ * other calls use the shared-memory heap). */
+#define KDT_LIST_GROUP4 2
+#define KDT_LIST_GROUP8 3
+int kdt_set_large_k_list(kdt_tree *tree, int placement);
+/* The placement kdt_knn uses for this tree and k: set on the tree, else tuned
+ * for its shape (kdt_autotune measures the shared-memory and the global heap
+ * for k > 16), else KDT_LIST_SHARED. */
+int kdt_large_k_list(const kdt_tree *tree, int k, int *placement);
+
 /* The launch parameters kdt_knn uses for this tree and k: set on the tree,
  * else tuned for its shape (kdt_autotune / kdt_tuning_load), else defaults
  * (no staging, 32 claim steps for k = 1 and 64 otherwise, inline depth 2,

@@ -249,12 +249,19 @@ int run_query(const kdt_tree *t, const float *d_q, int64_t Q, int k, float r2, i
 {
     pool_setup_once();
     const bool morton = flags & KDT_MORTON;
-    size_t bytes = carve_size({64}) + (morton ? morton_scratch_bytes(Q) : 0);
+    const bool gheap = heap_in_global(t, k);
+    const size_t heap_bytes = gheap ? (size_t)heap_scratch_threads() * k * 8 : 0;
+    size_t bytes = carve_size({64, heap_bytes}) + (morton ? morton_scratch_bytes(Q) : 0);
     Scratch sc(s);
     KDT_TRY(sc.alloc(bytes));
     Carve c{(char *)sc.p};
     unsigned long long *counter = c.take<unsigned long long>(8);
     QueryArgs a;
+    if (gheap) {
+        a.heap = c.take<unsigned long long>(heap_bytes / 8);
+        a.heap_threads = heap_scratch_threads();
+    }
+    a.group = list_group_for(t, k);
     if (morton)
         KDT_TRY(morton_order(d_q, Q, t->D, t->bbox, 1, nullptr, 0, (flags & KDT_COST_ORDER) ? t->nodes : nullptr,
                              t->N, t->layout == 3, c.base + c.off, const_cast<uint32_t **>(&a.perm),

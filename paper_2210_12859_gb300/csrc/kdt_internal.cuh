@@ -300,6 +300,8 @@ struct kdt_tree {
     int inline_depth = -1;
     // steps a lane may take per call while they are light (-1: tuned or 1)
     int light_run = -1;
+    // where the k-best heaps of k > 16 live (KDT_LIST_*; -1: the default)
+    int large_k_list = -1;
     // test hook: traversal step bound (0: 3N + 3)
     uint32_t debug_step_cap = 0;
     // per-point payload in node order [N][payload_c] and node_of[input index]
@@ -338,6 +340,12 @@ int claim_steps_for(const kdt_tree *t, int k);
 int default_claim_steps_k(int k);
 int inline_depth_for(const kdt_tree *t, int k);
 int light_run_for(const kdt_tree *t, int k);
+// whether a query for k neighbours keeps its heap in global scratch
+bool heap_in_global(const kdt_tree *t, int k);
+// lanes per query of the shuffle-inserted group list (1: one lane per query)
+int list_group_for(const kdt_tree *t, int k);
+// per-thread heap scratch for the traversal kernels (threads x k keys)
+inline int64_t heap_scratch_threads() { return (int64_t)num_sms() * 1024; }
 // builder shared by kdt_build and kdt_build_batched: fills nodes / ids / bbox
 // widest: split dimension per node = widest extent of its points (T == 1,
 // D <= 3), stored in the node (layout 3); else level mod D

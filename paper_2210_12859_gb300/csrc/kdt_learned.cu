@@ -467,8 +467,10 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     if (gate == KDT_GATE_FAR)
         flags |= KDT_MORTON | KDT_COST_ORDER;
     const bool morton = flags & KDT_MORTON;
+    const size_t heap_bytes = heap_in_global(t, k) ? (size_t)heap_scratch_threads() * k * 8 : 0;
     size_t off_w = 0, off_r2 = 1 << 15;
-    size_t off_m = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
+    size_t off_h = off_r2 + (((size_t)Q * 4 + 255) & ~(size_t)255);
+    size_t off_m = off_h + heap_bytes;
     size_t bytes = off_m + (morton ? morton_scratch_bytes(Q) : 0);
     Dev sc(s);
     KDT_CUDA(cudaMallocAsync(&sc.p, bytes, s));
@@ -508,6 +510,10 @@ int run_learned_query(kdt_tree *t, const float *d_q, int64_t Q, int k, float r2,
     a.inline_depth = inline_depth_for(t, k) >= 2 ? inline_depth_for(t, k) : 1;  // depth 0 is plain-query only
     a.r2q = r2q;
     a.n_gate = n_far;
+    if (heap_bytes) {
+        a.heap = (unsigned long long *)(B + off_h);
+        a.heap_threads = heap_scratch_threads();
+    }
     a.fb_count = (unsigned long long *)t->stats;
     a.ratio_sum = (double *)(t->stats + 1);
     const bool ordered = !(flags & KDT_UNORDERED);

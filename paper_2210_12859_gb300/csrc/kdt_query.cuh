@@ -32,6 +32,12 @@ struct QueryArgs {
     int light_run = 1;                 // steps a lane may take per call while they are light
     uint32_t step_cap = 0;             // traversal step bound (0: 3N + 3; a test hook lowers it)
     unsigned long long *counter = nullptr;  // dynamic work counter, zeroed before launch
+    // k > 16: the per-thread heaps in global memory (k entries per thread, for
+    // at most heap_threads threads; the grid is clamped to that), else (NULL)
+    // in shared memory
+    unsigned long long *heap = nullptr;
+    int64_t heap_threads = 0;
+    int group = 1;                     // k > 16: lanes per query holding a shuffle-inserted list (1: one lane)
     // batched forests
     int T = 1;
     const int64_t *node_off = nullptr; // [T+1]

@@ -1,6 +1,7 @@
 // Query kernels, instantiated once per node layout by kdt_query_l{0,1,2}.cu.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "kdt_query.cuh"
@@ -18,13 +19,19 @@ namespace kdt {
 // the bottom subtrees handled as scalar keys the depth-2 kernel needs 64
 // registers (8 blocks) and the depth-3 one 79, both without spills, so the
 // bounds only guard against regressions.
-template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE, bool RUNS = false>
+//
+// G > 1 (k > 16): a group of G lanes walks one query together and holds its
+// k-best list spread over the group (GroupList, insertion by warp shuffles);
+// the group's first lane claims the query for the group.
+template <int LAYOUT, int K, bool ORDERED, int MODE, bool STAGE, int INLINE, bool RUNS = false, int G = 1>
 __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS, K <= 8 ? 6 : 1)
     knn_kernel(const QueryArgs a)
 {
     constexpr int NC = LayoutTraits<LAYOUT>::NC;
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
-    using List = typename std::conditional<(K <= MAX_REG_K), RegList<K <= MAX_REG_K ? K : 1>, SmemList>::type;
+    using List = typename std::conditional<
+        (G > 1), GroupList<(G > 1 ? K / G : 1), (G > 1 ? G : 2)>,
+        typename std::conditional<(K <= MAX_REG_K), RegList<K <= MAX_REG_K ? K : 1>, SmemList>::type>::type;
     extern __shared__ float4 s_dyn[];
     float4 *s_nodes = s_dyn;
     if (STAGE) {
@@ -43,14 +50,22 @@ __global__ void __launch_bounds__(K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS, K
     float r2 = 0.f;
     int visits = 0;
     List list;
-    if constexpr (K > MAX_REG_K) {
-        list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
-        list.stride = blockDim.x;
+    if constexpr (K > MAX_REG_K && G == 1) {
+        if (a.heap) {  // this thread's k entries, contiguous
+            list.s = a.heap + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * (size_t)a.k;
+            list.stride = 1;
+        } else {
+            list.s = reinterpret_cast<unsigned long long *>(s_nodes + (size_t)a.staged * NF) + threadIdx.x;
+            list.stride = blockDim.x;
+        }
     }
     Walker<LAYOUT, ORDERED, INLINE> w;
+    const int glane = (threadIdx.x & 31) % G;
     for (;;) {
         const bool need = qi < 0 && !exhausted;
-        const int64_t slot = claim_slot(need, a.counter);
+        int64_t slot = claim_slot(need && glane == 0, a.counter);
+        if constexpr (G > 1)
+            slot = __shfl_sync(0xffffffffu, slot, (threadIdx.x & 31) - glane);
         if (need) {
             if (slot < Qn) {
                 qi = a.perm ? (int64_t)a.perm[slot] : slot;
@@ -195,6 +210,8 @@ inline int launch_kernel(Kern fn, int threads, size_t smem, const QueryArgs &a, 
     if (smem > 48 * 1024)
         KDT_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = grid_for_kernel((const void *)fn, threads, smem);
+    if (a.heap && (int64_t)grid * threads > a.heap_threads)
+        grid = (int)std::max<int64_t>(1, a.heap_threads / threads);
     KDT_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
     KDT_LAUNCH fn<<<grid, threads, smem, s>>>(a);
     KDT_CUDA(cudaGetLastError());
@@ -250,7 +267,7 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
 {
     constexpr int NF = LayoutTraits<LAYOUT>::NF;
     const int threads = batched && a.threads > 0 ? a.threads : (K <= MAX_REG_K ? REG_THREADS : SMEM_THREADS);
-    size_t list_bytes = K <= MAX_REG_K ? 0 : (size_t)a.k * threads * 8;
+    size_t list_bytes = (K <= MAX_REG_K || (a.heap && !batched)) ? 0 : (size_t)a.k * threads * 8;
     if (batched) {
         if constexpr (LAYOUT == 3)
             return set_error(KDT_EINVAL, "forests store no per-node split dimensions");
@@ -267,6 +284,27 @@ inline int launch_k(const QueryArgs &a, bool ordered, int mode, bool batched, cu
                            : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2, true>, threads, list_bytes, a, s);
         return ordered ? launch_kernel(knn_forest_kernel<LAYOUT, K, true, 2>, threads, list_bytes, a, s)
                        : launch_kernel(knn_forest_kernel<LAYOUT, K, false, 2>, threads, list_bytes, a, s);
+    }
+    if constexpr (K > MAX_REG_K) {
+        // k-best lists spread over groups of lanes: plain results and visit counts
+        if (a.group > 1 && (mode == MODE_RESULTS || mode == MODE_VISITS)) {
+            const bool vis = mode == MODE_VISITS;
+            const int d = a.inline_depth == 3 ? 3 : 2;
+#define KDT_GROUP_LAUNCH(GG, DD)                                                                                  \
+    return ordered ? (vis ? launch_kernel(knn_kernel<LAYOUT, K, true, MODE_VISITS, false, DD, false, GG>, threads, 0, a, s)   \
+                          : launch_kernel(knn_kernel<LAYOUT, K, true, MODE_RESULTS, false, DD, false, GG>, threads, 0, a, s)) \
+                   : (vis ? launch_kernel(knn_kernel<LAYOUT, K, false, MODE_VISITS, false, DD, false, GG>, threads, 0, a, s)  \
+                          : launch_kernel(knn_kernel<LAYOUT, K, false, MODE_RESULTS, false, DD, false, GG>, threads, 0, a, s))
+            if (a.group == 8) {
+                if (d == 3)
+                    KDT_GROUP_LAUNCH(8, 3);
+                KDT_GROUP_LAUNCH(8, 2);
+            }
+            if (d == 3)
+                KDT_GROUP_LAUNCH(4, 3);
+            KDT_GROUP_LAUNCH(4, 2);
+#undef KDT_GROUP_LAUNCH
+        }
     }
     size_t smem = (size_t)a.staged * NF * 16 + list_bytes;
     // staging is paired with depth-2 inlining only (both serve long queries)

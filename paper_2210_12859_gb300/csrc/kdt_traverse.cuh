@@ -145,9 +145,10 @@ struct RegList {
     __device__ __forceinline__ bool full(int) const { return (uint32_t)L[K - 1] != EMPTY_ID; }
 };
 
-// Shared-memory k-best set for 16 < k <= 64: a binary max-heap of packed
-// (d2, id) keys per thread (slot i of thread t at s[i * stride + t], so
-// consecutive threads hit consecutive banks).  The root is the worst key, i.e.
+// k-best set for 16 < k <= 64: a binary max-heap of packed (d2, id) keys per
+// thread, in shared memory (slot i of thread t at s[i * stride + t], so
+// consecutive threads hit consecutive banks) or in a per-thread slice of a
+// global scratch buffer (stride 1: the thread's k keys contiguous).  The root is the worst key, i.e.
 // the cull radius; an accepted key replaces the root and sifts down (log2 k
 // levels instead of k/2 shifts of a sorted list).  The k slots start at
 // (r2, EMPTY_ID) like the register list, which gives the same acceptance rule.
@@ -213,6 +214,68 @@ struct SmemList {
         }
     }
     // whether k points are held: the root is a real point
+    __device__ __forceinline__ bool full(int) const { return (uint32_t)w != EMPTY_ID; }
+};
+
+// k-best list spread over a group of G lanes that walk one query together
+// (every lane of the group runs the same steps on the same values).  The
+// list is sorted across the group: lane j of the group holds positions
+// [j M, (j + 1) M) in registers, sorted.  Inserting c shifts everything after
+// c's place by one position: lane j takes in max(c, last key of lane j - 1)
+// (c for lane 0; the blocks are contiguous, so that is the key leaving lane
+// j - 1), one warp shuffle, and runs the compare-swap chain of RegList on its
+// block, whose largest key leaves.  The group's last key, the worst (the cull
+// radius), is then broadcast from the group's last lane.  As in RegList, the
+// first G M - k positions hold key 0 and the k real ones start at
+// (r2, EMPTY_ID).  Shuffles use the group's lane mask: the group's lanes are
+// converged wherever the list is touched.
+template <int M, int G>
+struct GroupList {
+    unsigned long long L[M];
+    unsigned long long w;  // worst key of the group's list
+    int li;                // lane within the group
+    unsigned gmask;        // the group's lanes
+    __device__ __forceinline__ void init(int k, float r2)
+    {
+        const int lane = threadIdx.x & 31;
+        li = lane % G;
+        gmask = ((1u << G) - 1u) << (lane - li);
+        const unsigned long long s = pack_key(r2, EMPTY_ID);
+        const int pad = G * M - k;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            L[i] = li * M + i < pad ? 0ull : s;
+        w = s;
+    }
+    __device__ __forceinline__ float cull() const { return key_d2(w); }
+    __device__ __forceinline__ unsigned long long worst() const { return w; }
+    __device__ __forceinline__ void insert(unsigned long long c)
+    {
+        const unsigned long long left_last = __shfl_up_sync(gmask, L[M - 1], 1, G);
+        unsigned long long in = (li == 0 || c > left_last) ? c : left_last;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const unsigned long long a = L[i];
+            const bool sw = in < a;
+            L[i] = sw ? in : a;
+            in = sw ? a : in;
+        }
+        w = __shfl_sync(gmask, L[M - 1], G - 1, G);
+    }
+    __device__ __forceinline__ void store(int k, int32_t *ids, float *d2) const
+    {
+        const int pad = G * M - k;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int o = li * M + i - pad;
+            if (o >= 0) {
+                const uint32_t id = (uint32_t)L[i];
+                const bool empty = id == EMPTY_ID;
+                ids[o] = empty ? -1 : (int32_t)id;
+                d2[o] = empty ? __int_as_float(0x7f800000) : key_d2(L[i]);
+            }
+        }
+    }
     __device__ __forceinline__ bool full(int) const { return (uint32_t)w != EMPTY_ID; }
 };
 

@@ -13,7 +13,10 @@
 //     per step, where it applies: ordered, k <= 16, D <= 4, no staging);
 //   * light_run: steps a lane takes per call while they are light, so that
 //     the heavy steps (whole bottom subtrees) of a warp's lanes coincide
-//     (1 for long queries; 4 or 8 pay for short ones).
+//     (1 for long queries; 4 or 8 pay for short ones);
+//   * large_k_list (k > 16): the k-best heap in shared memory (pays for short
+//     queries) or in global scratch (full occupancy and L1; pays for long
+//     ones).
 // kdt_autotune measures them on the caller's queries and remembers the best
 // per shape (GPU, D, k bucket, floor(log2 N)), in memory and optionally in a
 // JSON file; without a tuning the defaults below apply.
@@ -35,6 +38,7 @@ namespace {
 constexpr int DEFAULT_STAGE_LEVELS = 0;
 constexpr int DEFAULT_INLINE_DEPTH = 2;
 constexpr int DEFAULT_LIGHT_RUN = 1;
+constexpr int DEFAULT_LARGE_K_LIST = KDT_LIST_SHARED;
 // measured on GB300: 64 steps per claim round is best for k >= 2 on every
 // workload tried, 32 for fcp
 int default_claim_steps(int k) { return k <= 1 ? 32 : 64; }
@@ -44,6 +48,7 @@ struct Tuned {
     int claim_steps;
     int inline_depth;
     int light_run;
+    int large_k_list;
 };
 
 using ShapeKey = std::tuple<std::string, int, int, int>;  // gpu, D, k bucket, log2 N
@@ -131,6 +136,24 @@ int light_run_for(const kdt_tree *t, int k)
     return tuned_for(t, k, &v) ? v.light_run : DEFAULT_LIGHT_RUN;
 }
 
+static int large_k_list_of(const kdt_tree *t, int k)
+{
+    if (t->large_k_list >= 0)
+        return t->large_k_list;
+    Tuned v;
+    return tuned_for(t, k, &v) ? v.large_k_list : DEFAULT_LARGE_K_LIST;
+}
+
+bool heap_in_global(const kdt_tree *t, int k) { return k > 16 && large_k_list_of(t, k) == KDT_LIST_GLOBAL; }
+
+int list_group_for(const kdt_tree *t, int k)
+{
+    if (k <= 16)
+        return 1;
+    const int p = large_k_list_of(t, k);
+    return p == KDT_LIST_GROUP8 ? 8 : (p == KDT_LIST_GROUP4 ? 4 : 1);
+}
+
 int inline_depth_for(const kdt_tree *t, int k)
 {
     if (t->inline_depth >= 0)
@@ -187,6 +210,24 @@ int kdt_set_light_run(kdt_tree *t, int steps)
     return KDT_OK;
 }
 
+int kdt_set_large_k_list(kdt_tree *t, int placement)
+{
+    if (!t)
+        return set_error(KDT_EINVAL, "tree is NULL");
+    if (placement < -1 || placement > KDT_LIST_GROUP8)
+        return set_error(KDT_EINVAL, "placement must be -1 or one of KDT_LIST_* (got %d)", placement);
+    t->large_k_list = placement;
+    return KDT_OK;
+}
+
+int kdt_large_k_list(const kdt_tree *t, int k, int *placement)
+{
+    if (!t || k < 1 || k > 64 || !placement)
+        return set_error(KDT_EINVAL, "bad tree, k or out pointer");
+    *placement = k > 16 ? large_k_list_of(t, k) : KDT_LIST_SHARED;
+    return KDT_OK;
+}
+
 int kdt_tuned_params(const kdt_tree *t, int k, int *stage_levels, int *claim_steps, int *inline_depth,
                      int *light_run)
 {
@@ -226,8 +267,9 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     KDT_CUDA(cudaEventCreate(&e0));
     KDT_CUDA(cudaEventCreate(&e1));
     const int saved_stage = t->stage_levels, saved_claim = t->claim_steps, saved_inline = t->inline_depth;
-    const int saved_light = t->light_run;
-    Tuned best{DEFAULT_STAGE_LEVELS, default_claim_steps(k), DEFAULT_INLINE_DEPTH, DEFAULT_LIGHT_RUN};
+    const int saved_light = t->light_run, saved_list = t->large_k_list;
+    Tuned best{DEFAULT_STAGE_LEVELS, default_claim_steps(k), DEFAULT_INLINE_DEPTH, DEFAULT_LIGHT_RUN,
+               DEFAULT_LARGE_K_LIST};
     float best_t = 3.4e38f;
     int rc = KDT_OK;
     auto measure = [&](const Tuned &c, float *out) {
@@ -235,6 +277,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
         t->claim_steps = c.claim_steps;
         t->inline_depth = c.inline_depth;
         t->light_run = c.light_run;
+        t->large_k_list = c.large_k_list;
         for (int rep = 0; rep < 3 && rc == KDT_OK; ++rep) {
             rc = run_query(t, d_q, n, k, INFINITY, flags & ~KDT_NO_STAGE, MODE_RESULTS, ids, d2, nullptr, s);
             if (rc == KDT_OK && rep == 0)
@@ -256,6 +299,11 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     };
     const bool simple_ok = !(flags & KDT_UNORDERED) && k <= 16 && t->layout != 2;
     consider(best, 0.f);
+    if (k > 16 && rc == KDT_OK) {
+        Tuned c = best;
+        c.large_k_list = KDT_LIST_GLOBAL;
+        consider(c, 0.02f);
+    }
     for (int d : {3, 4, 1, 0}) {
         Tuned c = best;
         c.inline_depth = d;
@@ -286,6 +334,7 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     t->claim_steps = saved_claim;
     t->inline_depth = saved_inline;
     t->light_run = saved_light;
+    t->large_k_list = saved_list;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(ids, s);
@@ -321,9 +370,9 @@ int kdt_tuning_save(const char *path)
         const Tuned &v = rows[i].second;
         ok = fprintf(f,
                      "  {\"gpu\": \"%s\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d, "
-                     "\"claim_steps\": %d, \"inline_depth\": %d, \"light_run\": %d}%s\n",
+                     "\"claim_steps\": %d, \"inline_depth\": %d, \"light_run\": %d, \"large_k_list\": %d}%s\n",
                      std::get<0>(key).c_str(), std::get<1>(key), std::get<2>(key), std::get<3>(key), v.stage_levels,
-                     v.claim_steps, v.inline_depth, v.light_run, i + 1 < rows.size() ? "," : "") > 0;
+                     v.claim_steps, v.inline_depth, v.light_run, v.large_k_list, i + 1 < rows.size() ? "," : "") > 0;
     }
     ok = ok && fprintf(f, "]\n") > 0;
     ok = (fclose(f) == 0) && ok;
@@ -348,7 +397,7 @@ int kdt_tuning_load(const char *path)
             continue;
         g += 8;
         const char *ge = strchr(g, '"');
-        int D, kb, l2, lv, cs = -1, inl = -1, lr = -1;
+        int D, kb, l2, lv, cs = -1, inl = -1, lr = -1, kl = -1;
         if (!ge || sscanf(ge, "\", \"D\": %d, \"k_bucket\": %d, \"log2n\": %d, \"stage_levels\": %d", &D, &kb, &l2,
                           &lv) != 4 || lv < 0 || lv > 16 || kb < 0 || kb > 5) {
             bad = true;
@@ -357,16 +406,18 @@ int kdt_tuning_load(const char *path)
         const char *c = strstr(ge, "\"claim_steps\": ");
         const char *d = strstr(ge, "\"inline_depth\": ");
         const char *r = strstr(ge, "\"light_run\": ");
+        const char *l = strstr(ge, "\"large_k_list\": ");
         if ((c && (sscanf(c + 15, "%d", &cs) != 1 || cs < 1 || cs > 256)) ||
             (d && (sscanf(d + 16, "%d", &inl) != 1 || inl < 0 || inl > 4)) ||
-            (r && (sscanf(r + 13, "%d", &lr) != 1 || lr < 1 || lr > 64))) {
+            (r && (sscanf(r + 13, "%d", &lr) != 1 || lr < 1 || lr > 64)) ||
+            (l && (sscanf(l + 16, "%d", &kl) != 1 || kl < 0 || kl > KDT_LIST_GROUP8))) {
             bad = true;
             break;
         }
         const int k_rep = kb == 0 ? 1 : (1 << kb);
         rows.emplace_back(ShapeKey(std::string(g, ge - g), D, kb, l2),
                           Tuned{lv, c ? cs : default_claim_steps(k_rep), d ? inl : DEFAULT_INLINE_DEPTH,
-                                r ? lr : DEFAULT_LIGHT_RUN});
+                                r ? lr : DEFAULT_LIGHT_RUN, l ? kl : DEFAULT_LARGE_K_LIST});
     }
     fclose(f);
     if (bad)

@@ -119,6 +119,8 @@ _sig("kdt_set_stage_levels", [_P, _I])
 _sig("kdt_set_claim_steps", [_P, _I])
 _sig("kdt_set_inline_depth", [_P, _I])
 _sig("kdt_set_light_run", [_P, _I])
+_sig("kdt_set_large_k_list", [_P, _I])
+_sig("kdt_large_k_list", [_P, _I, _P])
 _sig("kdt_tuned_params", [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)])
 _sig("kdt_autotune", [_P, _P, _I64, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _P])
 _sig("kdt_tuning_save", [ctypes.c_char_p])
@@ -482,6 +484,21 @@ def kdt_set_inline_depth(tree: Tree, depth: int) -> None:
 
 def kdt_set_light_run(tree: Tree, steps: int) -> None:
     _check(_lib.kdt_set_light_run(tree.handle, steps))
+
+
+KDT_LIST_SHARED, KDT_LIST_GLOBAL, KDT_LIST_GROUP4, KDT_LIST_GROUP8 = 0, 1, 2, 3
+
+
+def kdt_set_large_k_list(tree: Tree, placement: int) -> None:
+    """Where the k-best lists of k > 16 live: one of KDT_LIST_*, or -1 (the default)."""
+    _check(_lib.kdt_set_large_k_list(tree.handle, int(placement)))
+
+
+def kdt_large_k_list(tree: Tree, k: int) -> int:
+    """The k-best list placement (KDT_LIST_*) that kdt_knn uses for this tree and k."""
+    v = _I()
+    _check(_lib.kdt_large_k_list(tree.handle, int(k), ctypes.byref(v)))
+    return v.value
 
 
 def kdt_tuned_params(tree: Tree, k: int):

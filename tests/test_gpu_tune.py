@@ -126,3 +126,34 @@ def test_deep_inline_depths_identical(kdt, N, D, widest):
                                                                     want[1].view(torch.int32)), (depth, k, flags)
                 assert torch.equal(got_v, want_v), (depth, k, flags)
     kdt.kdt_status(tree)
+
+
+@pytest.mark.parametrize("N,D", [(1 << 16, 3), (50001, 3), (30000, 4), (70, 3)])
+def test_large_k_list_placements_identical(kdt, N, D):
+    """k > 16: the shared-memory heap, the same heap in global scratch, and the
+    lists spread over 4 or 8 lanes with shuffle insertion give the same ids,
+    distance bits and processed nodes, both orders, with and without a radius,
+    for k that fill the 4- and 8-lane blocks partly and fully."""
+    g = np.random.default_rng(N)
+    pts = g.random((N, D), dtype=np.float32)
+    qs = (g.random((5000, D)) * 1.2 - 0.1).astype(np.float32)
+    tree = kdt.kdt_build(torch.from_numpy(pts).cuda())
+    dq = torch.from_numpy(qs).cuda()
+    for k in (17, 32, 33, 64):
+        for flags, r in ((kdt.KDT_MORTON, float("inf")), (kdt.KDT_UNORDERED, float("inf")), (0, 0.08)):
+            kdt.kdt_set_large_k_list(tree, kdt.KDT_LIST_SHARED)
+            want = kdt.kdt_knn(tree, dq, k, r, flags=flags)
+            want_v = kdt.kdt_knn_visits(tree, dq, k, r, flags=flags)
+            for placement in (kdt.KDT_LIST_GLOBAL, kdt.KDT_LIST_GROUP4, kdt.KDT_LIST_GROUP8):
+                kdt.kdt_set_large_k_list(tree, placement)
+                for depth in (2, 3):
+                    kdt.kdt_set_inline_depth(tree, depth)
+                    got = kdt.kdt_knn(tree, dq, k, r, flags=flags)
+                    assert torch.equal(got[0], want[0]), (k, placement, depth)
+                    assert torch.equal(got[1].view(torch.int32), want[1].view(torch.int32)), (k, placement, depth)
+                    assert torch.equal(kdt.kdt_knn_visits(tree, dq, k, r, flags=flags), want_v), (k, placement)
+                kdt.kdt_set_inline_depth(tree, -1)
+    with pytest.raises(kdt.KdtError):
+        kdt.kdt_set_large_k_list(tree, 9)
+    kdt.kdt_set_large_k_list(tree, -1)
+    kdt.kdt_status(tree)
