@@ -467,8 +467,9 @@ int kdt_set_light_run(kdt_tree *tree, int steps);
 #define KDT_LIST_GROUP8 3
 int kdt_set_large_k_list(kdt_tree *tree, int placement);
 /* The placement kdt_knn uses for this tree and k: set on the tree, else tuned
- * for its shape (kdt_autotune measures the shared-memory and the global heap
- * for k > 16), else KDT_LIST_SHARED. */
+ * for its shape (for k > 16 kdt_autotune takes the global heap when its query
+ * sample processes at least 1024 nodes per query, the shared-memory heap
+ * otherwise), else KDT_LIST_SHARED. */
 int kdt_large_k_list(const kdt_tree *tree, int k, int *placement);
 
 /* The launch parameters kdt_knn uses for this tree and k: set on the tree,

@@ -16,7 +16,7 @@
 //     (1 for long queries; 4 or 8 pay for short ones);
 //   * large_k_list (k > 16): the k-best heap in shared memory (pays for short
 //     queries) or in global scratch (full occupancy and L1; pays for long
-//     ones).
+//     ones), chosen by the sample's processed nodes per query.
 // kdt_autotune measures them on the caller's queries and remembers the best
 // per shape (GPU, D, k bucket, floor(log2 N)), in memory and optionally in a
 // JSON file; without a tuning the defaults below apply.
@@ -300,9 +300,27 @@ int kdt_autotune(kdt_tree *t, const float *d_q, int64_t Q, int k, int flags, int
     const bool simple_ok = !(flags & KDT_UNORDERED) && k <= 16 && t->layout != 2;
     consider(best, 0.f);
     if (k > 16 && rc == KDT_OK) {
-        Tuned c = best;
-        c.large_k_list = KDT_LIST_GLOBAL;
-        consider(c, 0.02f);
+        // the heap placement follows the queries' length, not a timing: on a
+        // sample this size the launch's tail of a few long queries decides,
+        // where fewer, less contended warps win, while at full size the
+        // global heap's residency does (clustered 2^24, k = 32 / 64: 1.6x).
+        // Long queries amortise the heap's trips to memory, short ones do not
+        // (surface k = 32, ~190 nodes per query: the shared heap is 1.6x
+        // faster).  Threshold: 1024 processed nodes per query.
+        rc = run_query(t, d_q, n, k, INFINITY, flags & ~KDT_NO_STAGE, MODE_VISITS, nullptr, nullptr, ids, s);
+        std::vector<int32_t> hv(n);
+        if (rc == KDT_OK && (cudaMemcpyAsync(hv.data(), ids, (size_t)n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                             cudaStreamSynchronize(s) != cudaSuccess))
+            rc = set_error(KDT_ECUDA, "visit count copy failed");
+        double sum = 0.0;
+        for (int32_t v : hv)
+            sum += v;
+        if (rc == KDT_OK && sum >= 1024.0 * (double)n) {
+            best.large_k_list = KDT_LIST_GLOBAL;
+            float ms;
+            if (measure(best, &ms))  // the reference time of the later candidates
+                best_t = ms;
+        }
     }
     for (int d : {3, 4, 1, 0}) {
         Tuned c = best;
