@@ -346,7 +346,11 @@ int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d
 
 /* Mean squared error of the model on (d_x, d_label) and its gradient with
  * respect to the BF16-rounded parameters: h_grad float32 [KDT_MLP_PARAMS].
- * Synchronous. */
+ * The training path: the three 64 x 64 contractions of the step (hidden
+ * layer forward, back-propagation through it, its weight gradient) run on the
+ * tensor cores (tcgen05.mma) with BF16 operands (weights, hidden activations,
+ * back-propagated gradients) and FP32 accumulation; the rest in FP32, sums in
+ * a fixed order.  Synchronous. */
 int kdt_mlp_loss_grad(const float *h_params, const float *d_x, const float *d_label, int64_t n,
                       float *h_loss, float *h_grad, void *stream);
 

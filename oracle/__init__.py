@@ -92,6 +92,8 @@ def _load():
         lib.orc_mlp_forward.restype = None
         lib.orc_mlp_forward_bound.argtypes = [P, i32, P, i64, P, P]
         lib.orc_mlp_forward_bound.restype = None
+        lib.orc_mlp_loss_grad_bound.argtypes = [P, i32, P, P, i64, P, P]
+        lib.orc_mlp_loss_grad_bound.restype = ctypes.c_double
         lib.orc_mlp_loss_grad.argtypes = [P, i32, P, P, i64, P]
         lib.orc_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
@@ -454,6 +456,20 @@ def mlp_forward_bound(params, H: int, x):
     bound = np.empty(xs.shape[0], dtype=np.float64)
     _load().orc_mlp_forward_bound(_ptr(p), H, _ptr(xs), xs.shape[0], _ptr(y), _ptr(bound))
     return y, bound
+
+
+def mlp_loss_grad_bound(params, H: int, x, label):
+    """FP64 loss and gradient of the model and, per parameter, a bound on the
+    error of a BF16-in / FP32-accumulate evaluation: (loss, grad float64[P],
+    bound float64[P], loss bound)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    lab = np.ascontiguousarray(label, dtype=np.float64)
+    P = mlp_param_count(H)
+    grad = np.empty(P, dtype=np.float64)
+    bound = np.empty(P + 1, dtype=np.float64)
+    loss = _load().orc_mlp_loss_grad_bound(_ptr(p), H, _ptr(xs), _ptr(lab), xs.shape[0], _ptr(grad), _ptr(bound))
+    return loss, grad, bound[:P], bound[P]
 
 
 def mlp_loss_grad(params, H: int, x, label):

@@ -39,10 +39,11 @@
  *   orc_descent_leaf    greedy close-child descent (feature of the learned
  *                       radius proposal; not in the paper)
  *   orc_mlp_*           FP64 forward / backward of the radius MLP (not in the
- *                       paper; parity target for the GPU training kernels),
- *                       and the forward with a per-sample bound on the error
- *                       of a BF16-in / FP32-accumulate evaluation (parity
- *                       target for the tensor-core inference kernel)
+ *                       paper), and both with a bound on the error of a
+ *                       BF16-in / FP32-accumulate evaluation (per sample for
+ *                       the forward, per parameter for the gradient): parity
+ *                       targets for the tensor-core inference and training
+ *                       kernels
  *
  * Parity status: every function above is pinned by tests under tests/ against
  * values fixed by the paper (the six-point example of Figure 1), closed forms,
@@ -844,6 +845,144 @@ void orc_mlp_forward_bound(const double *params, int H, const double *x, int64_t
     free(e1);
     free(h2);
     free(e2);
+}
+
+/* The loss and gradient of orc_mlp_loss_grad (FP64) together with, per
+ * parameter, a bound on how far from it an evaluation in the training
+ * precision of the radius model can land: the forward as for
+ * orc_mlp_forward_bound (hidden activations rounded to bfloat16 where they
+ * enter the 64 x 64 contraction), and in the backward pass the gradient at the
+ * hidden layer's pre-activations rounded to bfloat16 where it enters the two
+ * contractions (G2 W2 and G2^T H1), everything else in FP32 in any order, each
+ * FP32 operation with a relative error of at most 2^-23.  A ReLU whose input
+ * lies within its error bound of 0 may switch either way; the bound then
+ * admits both values.  Per sample s, with e the FP32 allowance and b = 2^-8:
+ *   output error     de = e3 + e (|err| + e3); dgo = 2 de / n + 3 e 2 (|err| + de) / n
+ *   g2_i             dg2 = (|go| + dgo) |w3_i| (1 + e) if |z2_i| <= e2_i, else
+ *                    [z2_i > 0] (dgo + e (|go| + dgo)) |w3_i|; |g2_i| <= M2_i;
+ *                    as a BF16 operand dg2b = dg2 + b M2
+ *   dH1_j            d = sum_i dg2b |W2_ij| + g(2H+2) sum_i M2b |W2_ij|, magnitude MH
+ *   g1_j             dg1 = MH + d if |z1_j| <= g(10) S1_j, else [z1_j > 0] d
+ * and the parameter bounds sum these over the samples with the summation
+ * allowance g(2n) of their magnitudes.  bound[P] bounds the loss. */
+double orc_mlp_loss_grad_bound(const double *params, int H, const double *x, const double *label, int64_t n,
+                               double *grad, double *bound)
+{
+    const double *W1 = params;
+    const double *b1 = W1 + (int64_t)H * 4;
+    const double *W2 = b1 + H;
+    const double *b2 = W2 + (int64_t)H * H;
+    const double *w3 = b2 + H;
+    const double *b3 = w3 + H;
+    int64_t P = (int64_t)H * 4 + H + (int64_t)H * H + H + H + 1;
+    double *bW1 = bound;
+    double *bb1 = bW1 + (int64_t)H * 4;
+    double *bW2 = bb1 + H;
+    double *bb2 = bW2 + (int64_t)H * H;
+    double *bw3 = bb2 + H;
+    double *bb3 = bw3 + H;
+    const double ub = 1.0 / 256.0, uf = 1.0 / 8388608.0;
+    const double g10 = orc_gamma(10), gH = orc_gamma(2 * H + 2), gn = orc_gamma((int)(2 * n + 2 < 2000000000 ? 2 * n + 2 : 2000000000));
+    double loss = orc_mlp_loss_grad(params, H, x, label, n, grad);
+    /* per-parameter sums over the samples: propagated errors and magnitudes */
+    double *acc = (double *)calloc((size_t)(2 * (P + 1)), sizeof(double));
+    double *mag = acc + P + 1;
+    double *z1 = (double *)malloc((size_t)H * 8), *h1 = (double *)malloc((size_t)H * 8);
+    double *E1 = (double *)malloc((size_t)H * 8), *e1 = (double *)malloc((size_t)H * 8);
+    double *z2 = (double *)malloc((size_t)H * 8), *h2 = (double *)malloc((size_t)H * 8);
+    double *e2 = (double *)malloc((size_t)H * 8);
+    double *dg2b = (double *)malloc((size_t)H * 8), *M2b = (double *)malloc((size_t)H * 8);
+    for (int64_t s = 0; s < n; ++s) {
+        const double *xs = x + s * 4;
+        for (int j = 0; j < H; ++j) {
+            double z = b1[j], S = fabs(b1[j]);
+            for (int m = 0; m < 4; ++m) {
+                z += W1[j * 4 + m] * xs[m];
+                S += fabs(W1[j * 4 + m] * xs[m]);
+            }
+            z1[j] = z;
+            h1[j] = z > 0.0 ? z : 0.0;
+            E1[j] = g10 * S;
+            e1[j] = ub * (h1[j] + E1[j]) + E1[j];
+        }
+        double y = b3[0], A3 = fabs(b3[0]), p3 = 0.0;
+        for (int i = 0; i < H; ++i) {
+            double z = b2[i], A = fabs(b2[i]), pr = 0.0;
+            for (int j = 0; j < H; ++j) {
+                double w = W2[(int64_t)i * H + j];
+                z += w * h1[j];
+                A += fabs(w) * (h1[j] + e1[j]);
+                pr += fabs(w) * e1[j];
+            }
+            z2[i] = z;
+            h2[i] = z > 0.0 ? z : 0.0;
+            e2[i] = pr + gH * A;
+            y += w3[i] * h2[i];
+            A3 += fabs(w3[i]) * (h2[i] + e2[i]);
+            p3 += fabs(w3[i]) * e2[i];
+        }
+        const double e3 = p3 + gH * A3;
+        const double err = y - label[s];
+        const double de = e3 + uf * (fabs(err) + e3);
+        const double go = 2.0 * err / (double)n;
+        const double dgo = 2.0 * de / (double)n + 3.0 * uf * 2.0 * (fabs(err) + de) / (double)n;
+        const double ago = fabs(go) + dgo;
+        /* output layer and its bias */
+        acc[P - 1] += dgo;
+        mag[P - 1] += ago;
+        for (int i = 0; i < H; ++i) {
+            acc[(bw3 - bound) + i] += fabs(go) * e2[i] + dgo * (h2[i] + e2[i]) + uf * ago * (h2[i] + e2[i]);
+            mag[(bw3 - bound) + i] += ago * (h2[i] + e2[i]);
+            const int amb = fabs(z2[i]) <= e2[i];
+            const int on = z2[i] > 0.0 || amb;
+            const double M2 = on ? ago * fabs(w3[i]) * (1.0 + uf) : 0.0;
+            const double dg2 = amb ? M2 : (z2[i] > 0.0 ? (dgo + uf * ago) * fabs(w3[i]) : 0.0);
+            acc[(bb2 - bound) + i] += dg2;
+            mag[(bb2 - bound) + i] += M2;
+            dg2b[i] = dg2 + ub * M2;
+            M2b[i] = M2 * (1.0 + ub);
+        }
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < H; ++j) {
+                acc[(bW2 - bound) + (int64_t)i * H + j] += dg2b[i] * (h1[j] + e1[j]) + M2b[i] * e1[j];
+                mag[(bW2 - bound) + (int64_t)i * H + j] += M2b[i] * (h1[j] + e1[j]);
+            }
+        for (int j = 0; j < H; ++j) {
+            double d = 0.0, MH = 0.0;
+            for (int i = 0; i < H; ++i) {
+                d += dg2b[i] * fabs(W2[(int64_t)i * H + j]);
+                MH += M2b[i] * fabs(W2[(int64_t)i * H + j]);
+            }
+            d += gH * MH;
+            MH *= 1.0 + gH;
+            const int amb = fabs(z1[j]) <= E1[j];
+            const int on = z1[j] > 0.0 || amb;
+            const double dg1 = amb ? MH + d : (z1[j] > 0.0 ? d : 0.0);
+            const double M1 = on ? MH + d : 0.0;
+            acc[(bb1 - bound) + j] += dg1;
+            mag[(bb1 - bound) + j] += M1;
+            for (int m = 0; m < 4; ++m) {
+                acc[(bW1 - bound) + j * 4 + m] += dg1 * fabs(xs[m]) + uf * M1 * fabs(xs[m]);
+                mag[(bW1 - bound) + j * 4 + m] += M1 * fabs(xs[m]);
+            }
+        }
+        acc[P] += (2.0 * fabs(err) * de + de * de) / (double)n;
+        mag[P] += (fabs(err) + de) * (fabs(err) + de) / (double)n;
+    }
+    for (int64_t q = 0; q <= P; ++q)
+        bound[q] = acc[q] + gn * mag[q];
+    (void)bb3;
+    free(acc);
+    free(z1);
+    free(h1);
+    free(E1);
+    free(e1);
+    free(z2);
+    free(h2);
+    free(e2);
+    free(dg2b);
+    free(M2b);
+    return loss;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -11,9 +11,11 @@
 // Features: the query coordinates and log(max(d2_leaf, 1e-30)), where d2_leaf
 // is the squared distance to the node where a greedy close-child descent from
 // the root ends, normalised by training mean and standard deviation.
-// Network: 4 -> 64 -> 64 -> 1 with ReLU, weights rounded to BF16, biases and
-// all arithmetic in FP32.  Training: MSE against 0.5*log(d2 of the exact k-th
-// neighbour), Adam, deterministic reductions.
+// Network: 4 -> 64 -> 64 -> 1 with ReLU, weights rounded to BF16, biases in
+// FP32; the 64 x 64 contractions take BF16 operands (weights and hidden
+// activations / gradients) with FP32 accumulation on the tensor cores
+// (kdt_mlp_tc.cu), everything else is FP32.  Training: MSE against
+// 0.5*log(d2 of the exact k-th neighbour), Adam, deterministic reductions.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
@@ -41,7 +43,7 @@ constexpr int OB3 = OW3 + H;
 static_assert(OB3 + 1 == P, "parameter layout");
 static_assert(OW2 % 4 == 0, "W2 must be float4 aligned");
 
-constexpr int TS = 64;  // samples (threads) per training block
+constexpr int TS = 64;  // minibatch sizes are multiples of this
 
 __host__ __device__ inline bool is_weight(int i)
 {
@@ -80,150 +82,6 @@ __global__ void __launch_bounds__(256) features_kernel(const float4 *__restrict_
         float4 f = make_float4(q[0], q[1], q[2], leaf_feature(d2));
         reinterpret_cast<float4 *>(feat)[i] = f;
     }
-}
-
-// Loss and gradient of one block of TS samples; block partial sums of every
-// parameter gradient (and of the squared errors in slot P) go to
-// partial[blockIdx.x][P + 1].  Gradients are taken through the rounded weights
-// (the same values the forward pass uses).
-__global__ void __launch_bounds__(TS) mlp_grad_kernel(const float *__restrict__ wts, const float *__restrict__ x,
-                                                      const float *__restrict__ label, int64_t begin, int64_t count,
-                                                      float inv_count, float *__restrict__ partial)
-{
-    extern __shared__ float4 s_dyn[];
-    float *w = reinterpret_cast<float *>(s_dyn);
-    float *A1 = w + ((P + 3) & ~3);  // h1 [TS][H]
-    float *A2 = A1 + TS * H;         // h2, then dLoss/dz2 [TS][H]
-    float *G1 = A2 + TS * H;         // dLoss/dz1 [TS][H]
-    float *X = G1 + TS * H;          // features [TS][4]
-    float *GO = X + TS * 4;          // dLoss/dy [TS]
-    float *E2 = GO + TS;             // squared error [TS]
-    const int s = threadIdx.x;
-    for (int i = s; i < P; i += TS)
-        w[i] = wts[i];
-    const int64_t idx = begin + (int64_t)blockIdx.x * TS + s;
-    const bool valid = idx < begin + count;
-    float xs[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        xs[j] = valid ? x[idx * 4 + j] : 0.f;
-    const float lab = valid ? label[idx] : 0.f;
-    __syncthreads();
-
-    float h1[H];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        float a = w[OB1 + i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            a = __fmaf_rn(w[OW1 + 4 * i + j], xs[j], a);
-        h1[i] = fmaxf(a, 0.f);
-        A1[s * H + i] = h1[i];
-    }
-    float y = w[OB3];
-    for (int i = 0; i < H; ++i) {
-        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
-        float a = w[OB2 + i];
-#pragma unroll
-        for (int j = 0; j < H / 4; ++j) {
-            const float4 r = row[j];
-            a = __fmaf_rn(r.x, h1[4 * j + 0], a);
-            a = __fmaf_rn(r.y, h1[4 * j + 1], a);
-            a = __fmaf_rn(r.z, h1[4 * j + 2], a);
-            a = __fmaf_rn(r.w, h1[4 * j + 3], a);
-        }
-        const float h2 = fmaxf(a, 0.f);
-        A2[s * H + i] = h2;
-        y = __fmaf_rn(w[OW3 + i], h2, y);
-    }
-    const float e = valid ? __fsub_rn(y, lab) : 0.f;
-    const float go = __fmul_rn(__fmul_rn(2.f, e), inv_count);
-    GO[s] = go;
-    E2[s] = __fmul_rn(e, e);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        X[s * 4 + j] = xs[j];
-
-    // back through layer 2: g1_j = relu'(z1_j) * sum_i W2_ij g2_i
-    float g1[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j)
-        g1[j] = 0.f;
-    for (int i = 0; i < H; ++i) {
-        const float g2 = A2[s * H + i] > 0.f ? __fmul_rn(go, w[OW3 + i]) : 0.f;
-        const float4 *row = reinterpret_cast<const float4 *>(w + OW2 + i * H);
-#pragma unroll
-        for (int j = 0; j < H / 4; ++j) {
-            const float4 r = row[j];
-            g1[4 * j + 0] = __fmaf_rn(r.x, g2, g1[4 * j + 0]);
-            g1[4 * j + 1] = __fmaf_rn(r.y, g2, g1[4 * j + 1]);
-            g1[4 * j + 2] = __fmaf_rn(r.z, g2, g1[4 * j + 2]);
-            g1[4 * j + 3] = __fmaf_rn(r.w, g2, g1[4 * j + 3]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < H; ++j)
-        G1[s * H + j] = h1[j] > 0.f ? g1[j] : 0.f;
-    __syncthreads();
-
-    // block sums over the samples; thread t owns output unit t of each layer
-    float *out = partial + (size_t)blockIdx.x * (P + 1);
-    const int t = s;
-    {
-        float gw3 = 0.f, gb2 = 0.f;
-        const float w3t = w[OW3 + t];
-        for (int r = 0; r < TS; ++r) {
-            const float h2 = A2[r * H + t];
-            gw3 = __fmaf_rn(GO[r], h2, gw3);
-            gb2 = __fadd_rn(gb2, h2 > 0.f ? __fmul_rn(GO[r], w3t) : 0.f);
-        }
-        out[OW3 + t] = gw3;
-        out[OB2 + t] = gb2;
-    }
-    __syncthreads();
-    // turn column t of A2 into dLoss/dz2
-    {
-        const float w3t = w[OW3 + t];
-        for (int r = 0; r < TS; ++r) {
-            const float h2 = A2[r * H + t];
-            A2[r * H + t] = h2 > 0.f ? __fmul_rn(GO[r], w3t) : 0.f;
-        }
-    }
-    __syncthreads();
-    for (int i = 0; i < H; ++i) {
-        float acc = 0.f;
-        for (int r = 0; r < TS; ++r)
-            acc = __fmaf_rn(A2[r * H + i], A1[r * H + t], acc);
-        out[OW2 + i * H + t] = acc;
-    }
-    {
-        float gb1 = 0.f, gw[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int r = 0; r < TS; ++r) {
-            const float g = G1[r * H + t];
-            gb1 = __fadd_rn(gb1, g);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                gw[j] = __fmaf_rn(g, X[r * 4 + j], gw[j]);
-        }
-        out[OB1 + t] = gb1;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            out[OW1 + 4 * t + j] = gw[j];
-    }
-    if (t == 0) {
-        float gb3 = 0.f, l = 0.f;
-        for (int r = 0; r < TS; ++r) {
-            gb3 = __fadd_rn(gb3, GO[r]);
-            l = __fadd_rn(l, E2[r]);
-        }
-        out[OB3] = gb3;
-        out[P] = l;
-    }
-}
-
-constexpr size_t grad_smem_bytes()
-{
-    return (size_t)(((P + 3) & ~3) + 3 * TS * H + TS * 4 + 2 * TS) * sizeof(float);
 }
 
 // fixed-order sum over blocks: grad[i] = sum_b partial[b][i]
@@ -665,13 +523,13 @@ int kdt_mlp_forward(const float *h_params, const float *d_x, int64_t n, float *d
     return KDT_OK;
 }
 
+// loss and gradient on the tensor cores (BF16 operands, FP32 accumulation),
+// then the fixed-order sum over the blocks
 static int loss_grad_dev(const float *d_w, const float *d_x, const float *d_label, int64_t begin, int64_t count,
-                         float *d_partial, float *d_grad, cudaStream_t s)
+                         float *d_partial, float *d_grad, int *d_err, cudaStream_t s)
 {
-    const int nb = (int)((count + TS - 1) / TS);
-    const size_t smem = grad_smem_bytes();
-    KDT_CUDA(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    KDT_LAUNCH mlp_grad_kernel<<<nb, TS, smem, s>>>(d_w, d_x, d_label, begin, count, 1.0f / (float)count, d_partial);
+    int nb = 0;
+    KDT_TRY(tc_loss_grad(d_w, d_x, d_label, begin, count, d_partial, d_err, s, &nb));
     KDT_LAUNCH grad_reduce_kernel<<<(P + 1 + 255) / 256, 256, 0, s>>>(d_partial, nb, d_grad);
     KDT_CUDA(cudaGetLastError());
     return KDT_OK;
@@ -685,18 +543,24 @@ int kdt_mlp_loss_grad(const float *h_params, const float *d_x, const float *d_la
     if (n > (1 << 24))
         return set_error(KDT_EINVAL, "n must be <= 2^24");
     cudaStream_t s = (cudaStream_t)stream;
-    const int nb = (int)((n + TS - 1) / TS);
+    const int nb = (int)((n + 127) / 128);
     Dev buf(s);
     size_t wb = ((P * 4 + 255) & ~(size_t)255);
-    KDT_CUDA(cudaMallocAsync(&buf.p, 2 * wb + (size_t)nb * (P + 1) * 4, s));
+    KDT_CUDA(cudaMallocAsync(&buf.p, 2 * wb + 256 + (size_t)nb * (P + 1) * 4, s));
     float *w = (float *)buf.p;
     float *grad = (float *)((char *)buf.p + wb);
-    float *partial = (float *)((char *)buf.p + 2 * wb);
+    int *err = (int *)((char *)buf.p + 2 * wb);
+    float *partial = (float *)((char *)buf.p + 2 * wb + 256);
+    KDT_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     KDT_TRY(upload_rounded(h_params, w, s));
-    KDT_TRY(loss_grad_dev(w, d_x, d_label, 0, n, partial, grad, s));
+    KDT_TRY(loss_grad_dev(w, d_x, d_label, 0, n, partial, grad, err, s));
     std::vector<float> g(P + 1);
+    int h = 0;
     KDT_CUDA(cudaMemcpyAsync(g.data(), grad, (P + 1) * sizeof(float), cudaMemcpyDeviceToHost, s));
+    KDT_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     KDT_CUDA(cudaStreamSynchronize(s));
+    if (h)
+        return set_error(KDT_ECUDA, "the tensor-core MMA did not signal completion in time");
     memcpy(h_grad, g.data(), P * sizeof(float));
     if (h_loss)
         *h_loss = g[P] / (float)n;
@@ -833,7 +697,7 @@ int kdt_radius_model_train(kdt_tree *t, const float *d_q, int64_t Qt, int k, con
         KDT_CUDA(cudaMemsetAsync(loss_acc, 0, 8, s));
         for (int64_t b0 = 0; b0 < Qt; b0 += o.batch) {
             const int64_t cnt = std::min<int64_t>(o.batch, Qt - b0);
-            KDT_TRY(loss_grad_dev(w, feat, lab, b0, cnt, part, grad, s));
+            KDT_TRY(loss_grad_dev(w, feat, lab, b0, cnt, part, grad, t->err, s));
             b1t *= 0.9;
             b2t *= 0.999;
             const float lr = (float)(0.5 * o.lr * (1.0 + cos(M_PI * (double)step / (double)steps_total)));

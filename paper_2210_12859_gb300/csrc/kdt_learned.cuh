@@ -19,5 +19,9 @@ void free_model(kdt_tree *t);
 int tc_radius(const kdt_tree *t, const float *wts, const float *d_q, int64_t Q, const uint32_t *perm, float r2_user,
               float *r2q, cudaStream_t s, const unsigned long long *n_lim = nullptr);
 int tc_forward(const float *wts, const float *d_x, int64_t n, float *d_y, int *d_err, cudaStream_t s);
+// tensor-core loss and gradient over samples [begin, begin + count): one block
+// per 128 samples, partial[block][KDT_MLP_PARAMS + 1]; *blocks receives their number
+int tc_loss_grad(const float *wts, const float *d_x, const float *d_label, int64_t begin, int64_t count,
+                 float *d_partial, int *d_err, cudaStream_t s, int *blocks);
 void fill_inf(float *p, int64_t n, cudaStream_t s);
 }  // namespace kdt

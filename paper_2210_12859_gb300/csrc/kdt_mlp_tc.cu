@@ -270,6 +270,281 @@ __global__ void __launch_bounds__(TILE_M) mlp_tc_kernel(const TcArgs a)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------- training
+//
+// Loss and gradient of the model on the tensor cores, BF16 operands and FP32
+// accumulation, one CTA of 128 threads per tile of 128 samples (thread r holds
+// sample r).  With H1 the hidden activations of layer 1 (BF16) and G2 the
+// gradient at the pre-activations of the hidden layer (BF16), three
+// contractions of the validated shape (M = 128, N = 64, both operands K-major
+// in shared memory, FP32 accumulator in TMEM):
+//   Z2  = H1 . W2^T           rows = samples, K = 64   (TMEM columns 0..63)
+//   dH1 = G2 . W2             rows = samples, K = 64   (columns 64..127)
+//   dW2 = G2^T . H1           rows = the 64 hidden units (padded to 128 with
+//                             zero rows), K = 128 samples  (columns 128..191)
+// Layers 1 and 3, the ReLU masks and the sums over the tile's samples of the
+// small gradients (W1, b1, b2, w3, b3, the loss) run on the CUDA cores in
+// FP32, in a fixed order.  partial[blockIdx.x][P + 1] receives the tile's sums
+// (slot P: the squared errors).
+constexpr int GK = TILE_M;                      // samples per tile: K of the weight-gradient contraction
+constexpr int RED_LD = H + 1;                   // row stride of the FP32 reduction buffer (no bank conflicts)
+constexpr int G_W2 = 0;                         // B of Z2: row i, K = j
+constexpr int G_W2T = G_W2 + H * H * 2;         // B of dH1: row j, K = i
+constexpr int G_H1 = G_W2T + H * H * 2;         // A of Z2: row r, K = j
+constexpr int G_G2 = G_H1 + TILE_M * H * 2;     // A of dH1: row r, K = i
+constexpr int G_G2T = G_G2 + TILE_M * H * 2;    // A of dW2: row i (64..127 zero), K = r
+constexpr int G_H1T = G_G2T + 128 * GK * 2;     // B of dW2: row j, K = r
+constexpr int G_RED = G_H1T + H * GK * 2;       // FP32 [128][RED_LD]
+constexpr int G_SW = G_RED + ((TILE_M * RED_LD * 4 + 1023) & ~1023);  // W1, b1, b2, w3, b3 (FP32)
+constexpr int G_BAR = G_SW + 2048;              // mbarrier, TMEM slot, abort flag
+constexpr int G_SMEM = G_BAR + 64;
+constexpr uint32_t G_TMEM_COLS = 256;
+static_assert(G_H1 % 1024 == 0 && G_G2 % 1024 == 0 && G_G2T % 1024 == 0 && G_H1T % 1024 == 0, "tile alignment");
+static_assert(4 * H + 3 * H + 1 <= 2048 / 4, "small weights");
+
+// byte offset of element (row r, k) in a K-major no-swizzle tile with K columns
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K)
+{
+    return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// ksteps MMAs of K = 16 into the accumulator at taddr (the first one
+// overwrites it); sbo: the tiles' 8-row group strides (K * 16 bytes)
+__device__ __forceinline__ void mma_k_major(uint32_t taddr, uint32_t a0, uint32_t b0, int ksteps, uint32_t sbo_a,
+                                            uint32_t sbo_b)
+{
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const uint64_t ad = smem_desc(a0 + ks * 256, 128, sbo_a);
+        const uint64_t bd = smem_desc(b0 + ks * 256, 128, sbo_b);
+        const uint32_t acc = ks > 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+            : "memory");
+    }
+}
+
+// column sums of the reduction buffer in row order: thread t < H sums column t
+__device__ __forceinline__ float column_sum(const float *red, int t)
+{
+    float a = 0.f;
+    for (int r = 0; r < TILE_M; ++r)
+        a = __fadd_rn(a, red[r * RED_LD + t]);
+    return a;
+}
+
+__global__ void __launch_bounds__(TILE_M) mlp_tc_grad_kernel(const float *__restrict__ wts, const float *__restrict__ x,
+                                                             const float *__restrict__ label, int64_t begin,
+                                                             int64_t count, float inv_count,
+                                                             float *__restrict__ partial, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *red = reinterpret_cast<float *>(smem + G_RED);
+    float *sw = reinterpret_cast<float *>(smem + G_SW);  // W1 [4H], b1 [H], b2 [H], w3 [H], b3
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + G_BAR + 16);
+    int *abort_flag = reinterpret_cast<int *>(smem + G_BAR + 24);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    float *out = partial + (size_t)blockIdx.x * (KDT_MLP_PARAMS + 1);
+
+    for (int e = tid; e < H * H; e += TILE_M) {
+        const int i = e / H, j = e % H;
+        const __nv_bfloat16 v = __float2bfloat16_rn(wts[OW2 + e]);  // W2[i][j] (BF16-valued already)
+        *reinterpret_cast<__nv_bfloat16 *>(smem + G_W2 + kmajor_off(i, j, H)) = v;
+        *reinterpret_cast<__nv_bfloat16 *>(smem + G_W2T + kmajor_off(j, i, H)) = v;
+    }
+    for (int e = tid; e < 64 * GK; e += TILE_M)
+        *reinterpret_cast<__nv_bfloat16 *>(smem + G_G2T + kmajor_off(64 + e / GK, e % GK, GK)) = __float2bfloat16_rn(0.f);
+    for (int i = tid; i < 5 * H; i += TILE_M)
+        sw[i] = wts[i];  // W1, b1
+    for (int i = tid; i < 2 * H + 1; i += TILE_M)
+        sw[5 * H + i] = wts[OB2 + i];  // b2, w3, b3
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(G_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const float *W1 = sw;
+    const float *b1 = sw + 4 * H;
+    const float *b2 = sw + 5 * H;
+    const float *w3 = sw + 6 * H;
+    const float b3v = wts[OB2 + 2 * H];
+
+    const int64_t idx = begin + (int64_t)blockIdx.x * TILE_M + tid;
+    const bool valid = idx < begin + count;
+    float xs[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        xs[j] = valid ? x[idx * 4 + j] : 0.f;
+    const float lab = valid ? label[idx] : 0.f;
+    __syncthreads();  // small weights in place
+
+    // layer 1 (FP32), ReLU, BF16 rows of H1 and columns of H1^T
+    uint64_t mask1 = 0;  // z1_j > 0
+#pragma unroll
+    for (int g = 0; g < H / 8; ++g) {
+        __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = g * 8 + e;
+            float a = b1[j];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                a = __fmaf_rn(W1[4 * j + m], xs[m], a);
+            const bool on = valid && a > 0.f;
+            mask1 |= (uint64_t)on << j;
+            hb[e] = __float2bfloat16_rn(on ? a : 0.f);
+            *reinterpret_cast<__nv_bfloat16 *>(smem + G_H1T + kmajor_off(j, tid, GK)) = hb[e];
+        }
+        *reinterpret_cast<uint4 *>(smem + G_H1 + kmajor_off(tid, g * 8, H)) = *reinterpret_cast<const uint4 *>(hb);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tslot;
+    const uint32_t s0 = smem_addr(smem);
+    if (tid == 0) {
+        mma_k_major(taddr, s0 + G_H1, s0 + G_W2, H / 16, H * 16, H * 16);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(bar))
+                     : "memory");
+        if (!mbar_wait(bar, 0))
+            *abort_flag = 1;
+    }
+    __syncthreads();
+    uint32_t pending = 0;  // parity of the MMA batch being waited for
+    if (!*abort_flag) {
+        pending = 1;
+        tc_fence_after();
+        // epilogue of Z2: hidden layer, output, error
+        float z2[H];
+#pragma unroll
+        for (int c = 0; c < H; c += 16) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                z2[c + e] = __fadd_rn(v[e], b2[c + e]);
+        }
+        float y = b3v;
+#pragma unroll
+        for (int i = 0; i < H; ++i)
+            y = __fmaf_rn(w3[i], fmaxf(z2[i], 0.f), y);
+        const float err_s = valid ? __fsub_rn(y, lab) : 0.f;
+        const float go = __fmul_rn(__fmul_rn(2.f, err_s), inv_count);
+        // dLoss/dw3 = sum of go * h2, dLoss/db2 = sum of g2 (FP32)
+#pragma unroll
+        for (int i = 0; i < H; ++i)
+            red[tid * RED_LD + i] = __fmul_rn(go, fmaxf(z2[i], 0.f));
+        __syncthreads();
+        if (tid < H)
+            out[OB2 + H + tid] = column_sum(red, tid);  // w3 follows b2
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float g2 = (valid && z2[i] > 0.f) ? __fmul_rn(go, w3[i]) : 0.f;
+            red[tid * RED_LD + i] = g2;
+            const __nv_bfloat16 gb = __float2bfloat16_rn(g2);
+            *reinterpret_cast<__nv_bfloat16 *>(smem + G_G2 + kmajor_off(tid, i, H)) = gb;
+            *reinterpret_cast<__nv_bfloat16 *>(smem + G_G2T + kmajor_off(i, tid, GK)) = gb;
+        }
+        __syncthreads();
+        if (tid < H)
+            out[OB2 + tid] = column_sum(red, tid);
+        __syncthreads();
+        red[tid * RED_LD + 0] = go;
+        red[tid * RED_LD + 1] = __fmul_rn(err_s, err_s);
+        __syncthreads();
+        if (tid == 0) {
+            float gb3 = 0.f, l = 0.f;
+            for (int r = 0; r < TILE_M; ++r) {
+                gb3 = __fadd_rn(gb3, red[r * RED_LD + 0]);
+                l = __fadd_rn(l, red[r * RED_LD + 1]);
+            }
+            out[OB2 + 2 * H] = gb3;
+            out[KDT_MLP_PARAMS] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            mma_k_major(taddr + 64, s0 + G_G2, s0 + G_W2T, H / 16, H * 16, H * 16);
+            mma_k_major(taddr + 128, s0 + G_G2T, s0 + G_H1T, GK / 16, GK * 16, GK * 16);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(bar))
+                         : "memory");
+            if (!mbar_wait(bar, 1))
+                *abort_flag = 1;
+        }
+        __syncthreads();
+    }
+    if (!*abort_flag) {
+        tc_fence_after();
+        // g1 = relu'(z1) * (G2 W2) row of this sample
+        float g1[H];
+#pragma unroll
+        for (int c = 0; c < H; c += 16) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(64 + c), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                g1[c + e] = ((mask1 >> (c + e)) & 1ull) ? v[e] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < H; ++j)
+            red[tid * RED_LD + j] = g1[j];
+        __syncthreads();
+        if (tid < H)
+            out[OB1 + tid] = column_sum(red, tid);
+        for (int m = 0; m < 4; ++m) {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < H; ++j)
+                red[tid * RED_LD + j] = __fmul_rn(g1[j], xs[m]);
+            __syncthreads();
+            if (tid < H)
+                out[OW1 + 4 * tid + m] = column_sum(red, tid);
+        }
+        // dW2: TMEM lanes 0..63 (warps 0 and 1) hold rows i = 0..63
+        if (warp < 2) {
+#pragma unroll
+            for (int c = 0; c < H; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(128 + c), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    out[OW2 + tid * H + c + e] = v[e];
+            }
+        }
+    } else {
+        // an MMA did not signal in time: record it, give the pending ones one
+        // more bounded wait before the accumulator is released
+        if (tid == 0) {
+            atomicOr(err, ERR_TRAVERSAL);
+            mbar_wait(bar, pending);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(G_TMEM_COLS) : "memory");
+}
+
 constexpr size_t tc_smem_bytes() { return SMEM_FIXED; }
 
 int launch_tc(int mode, const TcArgs &a, cudaStream_t s)
@@ -323,6 +598,19 @@ int tc_forward(const float *wts, const float *d_x, int64_t n, float *d_y, int *d
     a.y = d_y;
     a.err = d_err;
     return launch_tc(1, a, s);
+}
+
+int tc_loss_grad(const float *wts, const float *d_x, const float *d_label, int64_t begin, int64_t count,
+                 float *d_partial, int *d_err, cudaStream_t s, int *blocks)
+{
+    const int nb = (int)((count + TILE_M - 1) / TILE_M);
+    KDT_CUDA(cudaFuncSetAttribute((const void *)mlp_tc_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  G_SMEM));
+    KDT_LAUNCH mlp_tc_grad_kernel<<<nb, TILE_M, G_SMEM, s>>>(wts, d_x, d_label, begin, count, 1.0f / (float)count,
+                                                            d_partial, d_err);
+    KDT_CUDA(cudaGetLastError());
+    *blocks = nb;
+    return KDT_OK;
 }
 
 }  // namespace kdt

@@ -594,6 +594,154 @@ def test_mlp_forward_bound_covers_cancellation_in_layer1():
     assert bound[0] >= 2.0 ** -27
 
 
+def _simulate_bf16_in_grad(p, H, x, lab, reverse=False):
+    """An FP32 training step with BF16 operands in the 64 x 64 contractions:
+    the hidden activations of layer 1 and the gradient at the hidden layer's
+    pre-activations rounded to bfloat16 there, sums over samples and units in
+    FP32 (in index order, or reversed).  Returns (loss, grad float64[P])."""
+    f = np.float32
+    W1 = p[: 4 * H].reshape(H, 4).astype(f)
+    b1 = p[4 * H: 5 * H].astype(f)
+    W2 = p[5 * H: 5 * H + H * H].reshape(H, H).astype(f)
+    b2 = p[5 * H + H * H: 6 * H + H * H].astype(f)
+    w3 = p[6 * H + H * H: 7 * H + H * H].astype(f)
+    b3 = f(p[-1])
+    xs, ls = x.astype(f), lab.astype(f)
+    n = xs.shape[0]
+    order = range(n - 1, -1, -1) if reverse else range(n)
+    units = range(H - 1, -1, -1) if reverse else range(H)
+    z1 = np.repeat(b1[None, :], n, 0)
+    for m in range(4):
+        z1 = (z1 + (W1[:, m][None, :] * xs[:, m:m + 1]).astype(f)).astype(f)
+    h1b = _bf16(np.maximum(z1, f(0)))
+    z2 = np.zeros((n, H), dtype=f)
+    for j in units:
+        z2 = (z2 + (h1b[:, j:j + 1] * W2[:, j][None, :]).astype(f)).astype(f)
+    z2 = (z2 + b2[None, :]).astype(f)
+    h2 = np.maximum(z2, f(0))
+    y = np.full(n, b3, dtype=f)
+    for i in units:
+        y = (y + (w3[i] * h2[:, i]).astype(f)).astype(f)
+    err = (y - ls).astype(f)
+    go = ((f(2) * err).astype(f) * f(1.0 / n)).astype(f)
+    g2 = np.where(z2 > 0, (go[:, None] * w3[None, :]).astype(f), f(0)).astype(f)
+    g2b = _bf16(g2)
+    dH1 = np.zeros((n, H), dtype=f)
+    for i in units:
+        dH1 = (dH1 + (g2b[:, i:i + 1] * W2[i, :][None, :]).astype(f)).astype(f)
+    g1 = np.where(z1 > 0, dH1, f(0)).astype(f)
+    gW1 = np.zeros((H, 4), f); gb1 = np.zeros(H, f); gW2 = np.zeros((H, H), f)
+    gb2 = np.zeros(H, f); gw3 = np.zeros(H, f); gb3 = f(0); loss = f(0)
+    for s_ in order:
+        gW1 = (gW1 + (g1[s_][:, None] * xs[s_][None, :]).astype(f)).astype(f)
+        gb1 = (gb1 + g1[s_]).astype(f)
+        gW2 = (gW2 + (g2b[s_][:, None] * h1b[s_][None, :]).astype(f)).astype(f)
+        gb2 = (gb2 + g2[s_]).astype(f)
+        gw3 = (gw3 + (go[s_] * h2[s_]).astype(f)).astype(f)
+        gb3 = f(gb3 + go[s_])
+        loss = f(loss + f(err[s_] * err[s_]))
+    grad = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gw3, [gb3]]).astype(np.float64)
+    return float(loss) / n, grad
+
+
+@pytest.mark.parametrize("reverse", [False, True])
+def test_mlp_grad_bound_covers_bf16_in_fp32_training(reverse):
+    """Simulated BF16-in / FP32 training steps stay within the per-parameter
+    bound (and the loss within its bound), on the model's width and a narrow
+    one; the rounding does show in the simulated gradient."""
+    for H, seed, n in ((64, 31, 700), (8, 32, 300)):
+        p = _bf16_params(H, seed, 0.4)
+        g = np.random.default_rng(seed + 7)
+        x = g.standard_normal((n, 4)).astype(np.float32).astype(np.float64)
+        lab = g.standard_normal(n).astype(np.float32).astype(np.float64)
+        loss, grad, bound, lbound = oracle.mlp_loss_grad_bound(p, H, x, lab)
+        l2, g2 = oracle.mlp_loss_grad(p, H, x, lab)
+        assert loss == l2 and np.array_equal(grad, g2)
+        sl, sg = _simulate_bf16_in_grad(p, H, x, lab, reverse)
+        assert np.all(np.abs(sg - grad) <= bound), float(np.max(np.abs(sg - grad) / np.maximum(bound, 1e-300)))
+        assert abs(sl - loss) <= lbound
+        assert np.max(np.abs(sg - grad)) > 0
+
+
+def test_mlp_grad_bound_tight_for_one_rounded_activation():
+    """One sample, one hidden unit of activation 1 + 2^-8 (rounds to 1 in
+    bfloat16), identity weights, label 0: the model's dW2 is
+    2 (1 + 2^-8)^2, the BF16-in step's 2; the bound covers the difference
+    and is within a factor of three of it."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0            # W1[0][0]
+    p[4] = 2.0 ** -8      # b1
+    p[5] = 1.0            # W2
+    p[7] = 1.0            # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    lab = np.array([0.0])
+    loss, grad, bound, _ = oracle.mlp_loss_grad_bound(p, H, x, lab)
+    _, sg = _simulate_bf16_in_grad(p, H, x, lab)
+    assert grad[5] == 2.0 * (1.0 + 2.0 ** -8) ** 2 and sg[5] == 2.0
+    d = grad[5] - sg[5]
+    assert d <= bound[5] <= 3.0 * d
+
+
+def test_mlp_grad_bound_covers_rounded_back_propagation():
+    """h1 = 1 exactly, label -(4 + 2^-6): the error 5 + 2^-6 gives go =
+    10 + 2^-5, which lies halfway between the bfloat16 neighbours 10 and
+    10.0625 and rounds to 10.  The gradient at the first layer's bias is that
+    operand times W2 = 1: 10 instead of 10 + 2^-5; only the bound's rounding
+    allowance for the back-propagated operand covers it."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0    # W1[0][0]
+    p[5] = 1.0    # W2
+    p[7] = 1.0    # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    lab = np.array([-(4.0 + 2.0 ** -6)])
+    loss, grad, bound, _ = oracle.mlp_loss_grad_bound(p, H, x, lab)
+    _, sg = _simulate_bf16_in_grad(p, H, x, lab)
+    assert grad[4] == 10.0 + 2.0 ** -5 and sg[4] == 10.0
+    assert np.all(np.abs(sg - grad) <= bound)
+
+
+def test_mlp_grad_bound_covers_rounded_activation_in_dw2():
+    """An activation of 1 + 2^-8 (rounds to 1) with label -(1 + 2^-8): the
+    weight gradient dW2 = go h1 is (4 + 2^-6)(1 + 2^-8) for the model and 4
+    for the rounded step; the bound must carry the activation's error into
+    the weight gradient."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0            # W1[0][0]
+    p[4] = 2.0 ** -8      # b1
+    p[5] = 1.0            # W2
+    p[7] = 1.0            # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    lab = np.array([-(1.0 + 2.0 ** -8)])
+    loss, grad, bound, _ = oracle.mlp_loss_grad_bound(p, H, x, lab)
+    _, sg = _simulate_bf16_in_grad(p, H, x, lab)
+    assert sg[5] == 4.0 and grad[5] > 4.0 + 2.0 ** -6
+    assert np.all(np.abs(sg - grad) <= bound)
+
+
+def test_mlp_grad_bound_admits_a_flipped_mask():
+    """A hidden pre-activation of 2^-12 is within its forward bound of 0: the
+    layer-1 activation 1 + 2^-9 rounds to 1 in bfloat16, so with the bias
+    -(1 + 2^-9) + 2^-12 the model's pre-activation is 2^-12 and the rounded
+    evaluation's is 2^-12 - 2^-9 < 0.  Its ReLU switches off there and the
+    unit's gradient is 0 instead of go w3; the bound admits both values."""
+    H = 1
+    p = np.zeros(oracle.mlp_param_count(H))
+    p[0] = 1.0                    # W1[0][0]
+    p[4] = 2.0 ** -9              # b1: h1 = 1 + 2^-9, rounds to 1
+    p[5] = 1.0                    # W2
+    p[6] = -(1.0 + 2.0 ** -9) + 2.0 ** -12   # b2: z2 = 2^-12 exactly, 2^-12 - 2^-9 < 0 after rounding
+    p[7] = 1.0                    # w3
+    x = np.array([[1.0, 0, 0, 0]])
+    lab = np.array([-1.0])
+    loss, grad, bound, _ = oracle.mlp_loss_grad_bound(p, H, x, lab)
+    _, sg = _simulate_bf16_in_grad(p, H, x, lab)
+    assert grad[6] != 0.0 and sg[6] == 0.0          # db2: the mask switched off
+    assert np.all(np.abs(sg - grad) <= bound)
+
+
 def test_mlp_forward_bound_value_exact_for_integer_model():
     """Small-integer weights, biases and inputs: every value is exact in
     bfloat16 and FP32, so a BF16-in / FP32 evaluation gives the FP64 forward's

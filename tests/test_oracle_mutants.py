@@ -285,6 +285,22 @@ MUTANTS = {
     "bound_layer1_fp32_dropped": [(
         "            e1[i] = ub * (h1[i] + g1 * S) + g1 * S;",
         "            e1[i] = ub * h1[i];")],
+    # gradient bound: a pre-activation within its bound of 0 not treated as switchable
+    "grad_bound_no_mask_flip": [(
+        "            const double dg2 = amb ? M2 : (z2[i] > 0.0 ? (dgo + uf * ago) * fabs(w3[i]) : 0.0);",
+        "            const double dg2 = z2[i] > 0.0 ? (dgo + uf * ago) * fabs(w3[i]) : 0.0;")],
+    # gradient bound: the bfloat16 rounding of the back-propagated operand dropped
+    "grad_bound_no_g2_rounding": [(
+        "            dg2b[i] = dg2 + ub * M2;",
+        "            dg2b[i] = dg2;")],
+    # gradient bound: the activation error not carried into the weight gradient
+    "grad_bound_no_h1_error_in_dw2": [(
+        "acc[(bW2 - bound) + (int64_t)i * H + j] += dg2b[i] * (h1[j] + e1[j]) + M2b[i] * e1[j];",
+        "acc[(bW2 - bound) + (int64_t)i * H + j] += dg2b[i] * h1[j];")],
+    # gradient bound: the output error not carried into go
+    "grad_bound_no_output_error": [(
+        "        const double de = e3 + uf * (fabs(err) + e3);",
+        "        const double de = uf * fabs(err);")],
     # payload reductions: the payload row stride dropped
     "reduce_payload_stride": [(
         "s = s + payload[(int64_t)hits[i] * C + c];",
