@@ -414,7 +414,7 @@ def main():
         t0 = time.perf_counter()
         # the gate (all queries, the far ones, none) is timed on the training
         # queries with the bench's query flags and the fastest kept
-        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=20, seed=1, query_flags=flags)
+        loss = kdt.kdt_radius_model_train(tree, train_q, K_NN, epochs=40, seed=1, query_flags=flags)
         train_s = time.perf_counter() - t0
         gate = kdt.kdt_radius_model_gate(tree)
         li = torch.empty_like(out_i)
@@ -439,7 +439,7 @@ def main():
                    "gate": {kdt.KDT_GATE_ALL: "all", kdt.KDT_GATE_FAR: "far", kdt.KDT_GATE_NONE: "none"}[gate],
                    "gated_queries": gated, "fallback_rate": fb / n, "radius_ratio": ratio,
                    "identical_to_plain": same, "visits_per_query": lv_sum / n, "train_s": train_s,
-                   "train_loss": loss, "train_queries": 1 << 20, "train_epochs": 20,
+                   "train_loss": loss, "train_queries": 1 << 20, "train_epochs": 40,
                    "train_weighting": "plain-traversal work (resampled)",
                    "roofline": {"bound": "hbm", "achieved": l_ach, "peak": hbm, "unit": "GB/s", "frac": l_ach / hbm,
                                 "bytes_per_query": l_bytes / n, "peak_source": peak_src,

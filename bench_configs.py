@@ -141,7 +141,7 @@ def run_config(args):
             # 1.25: the fixed margin of the configuration; 0: calibrated by the library
             kdt.kdt_autotune(tree, dq, k, F)
             t0 = time.perf_counter()
-            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=20, seed=1, margin=margin, query_flags=F)
+            loss = kdt.kdt_radius_model_train(tree, dt, k, epochs=40, seed=1, margin=margin, query_flags=F)
             train_s = time.perf_counter() - t0
             used_margin = kdt.kdt_radius_model_get(tree)[2]
             out_i = torch.empty((n, k), dtype=torch.int32, device="cuda")

@@ -499,15 +499,10 @@ struct Walker {
         }
     }
 
-    // whether the subtree below node c is exactly L levels deep: its leftmost
-    // descendant L levels down, (c + 1) 2^L - 1, exists and the one a level
-    // further down does not
-    template <int L>
-    __device__ __forceinline__ static bool depth_is(int c, int N)
-    {
-        const uint64_t c1 = (uint64_t)c + 1ull;
-        return (c1 << L) - 1ull < (uint64_t)N && (c1 << (L + 1)) - 1ull >= (uint64_t)N;
-    }
+    // The subtree below node c is at least L levels deep iff its leftmost
+    // descendant L levels down, (c + 1) 2^L - 1, exists, i.e. iff
+    // c < floor(N / 2^L) = N >> L: the depth tests of a step are compares
+    // against these thresholds.
 
     // One or more steps; returns true when the traversal has finished.  With
     // RUNS and light_run > 1 a call continues with further steps while the next one is
@@ -539,23 +534,34 @@ struct Walker {
         int next;
         const int rc = lc + 1;
         const int dim1 = dim + 1 == D ? 0 : dim + 1;
-        if (INLINE >= 4 && from_parent && depth_is<4>(curr, N)) {
+        // whole subtrees below at most INLINE (and at least one) levels deep
+        // are processed in this step
+        // (for INLINE <= 2 from the children's indices, which keeps the
+        // depth-2 kernel at 64 registers)
+        bool inl;
+        if constexpr (INLINE >= 3)
+            inl = from_parent && curr < (N >> 1) && curr >= (N >> (INLINE + 1));
+        else if constexpr (INLINE == 2)
+            inl = from_parent && lc < N && 2u * (2u * (uint32_t)lc + 1u) + 1u >= (uint32_t)N;
+        else
+            inl = INLINE == 1 && from_parent && lc < N && 2 * lc + 1 >= N;
+        if (INLINE >= 4 && inl && curr < (N >> 4)) {
             // the subtree below is four levels deep: its two depth-3 halves,
             // each as two depth-2 blocks of seven loads issued together
             walk_below<4, STAGE, 4>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
-        } else if (INLINE >= 3 && from_parent && depth_is<3>(curr, N)) {
+        } else if (INLINE >= 3 && inl && curr < (N >> 3)) {
             // three levels deep: both children (each with the depth-1 or
             // depth-2 subtree below it) in the machine's order, each child's
             // seven nodes loaded at once when the machine enters that child
             walk_below<3, STAGE, 3>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
-        } else if (INLINE >= 2 && from_parent && depth_is<2>(curr, N)) {
+        } else if (INLINE >= 2 && inl && (INLINE >= 3 ? curr < (N >> 2) : 2 * lc + 1 < N)) {
             // the children have only leaves below them: the whole depth-2
             // subtree in the machine's order, its six loads issued first
             walk_below<2, STAGE, 2>(curr, sd, dim1, D, nodes, ids, s_nodes, staged, N, q, list, visits);
             next = parent;
-        } else if (INLINE >= 1 && from_parent && lc < N && 2 * lc + 1 >= N) {
+        } else if (inl) {
             // both children are leaves (the right one may be missing): both
             // loads first
             const NodeVal<LAYOUT> a = fetch<LAYOUT, STAGE>(nodes, s_nodes, staged, lc);
@@ -603,7 +609,9 @@ struct Walker {
         // stop before a heavy step (entering a node whose bottom subtree is
         // processed whole), so that it starts the next call
         if (curr > prev && 2 * curr + 1 < N &&
-            ((((uint64_t)curr + 1ull) << (INLINE + 1)) - 1ull >= (uint64_t)N))
+            (INLINE >= 3 ? curr >= (N >> (INLINE + 1))
+                         : (INLINE == 2 ? 2u * (2u * (2u * (uint32_t)curr + 1u) + 1u) + 1u >= (uint32_t)N
+                                        : 2 * (2 * curr + 1) + 1 >= N)))
             return false;
       }
     }

@@ -153,7 +153,7 @@ def test_fullsize_learned_radius(kdt, work):
     w = work
     mix = synth.gmm_mixture(64, 3, 0.01, SEED)
     train_q = torch.from_numpy(synth.gmm_queries(mix, 1 << 20, 0.1, synth.BASE_SEED + 77)).cuda()
-    kdt.kdt_radius_model_train(w["tree"], train_q, 8, epochs=20, seed=1)
+    kdt.kdt_radius_model_train(w["tree"], train_q, 8, epochs=40, seed=1)
     gi, gd = kdt.kdt_knn(w["tree"], w["dq"], 8, math.inf, w["flags"] | kdt.KDT_LEARNED)
     torch.cuda.synchronize()
     kdt.kdt_status(w["tree"])
