@@ -84,7 +84,7 @@ def _load():
         lib.orc_knn_stackfree.restype = i32
         lib.orc_knn_stackfree_batch.argtypes = [P, P, i64, i32, P, i64, i32, f32, i32, P, P, P]
         lib.orc_knn_stackfree_batch.restype = i32
-        lib.orc_descent_leaf.argtypes = [P, P, i64, i32, P]
+        lib.orc_descent_leaf.argtypes = [P, P, P, i64, i32, P]
         lib.orc_descent_leaf.restype = f32
         lib.orc_round_bf16.argtypes = [f32]
         lib.orc_round_bf16.restype = f32
@@ -415,16 +415,22 @@ def knn_tree(points, node_pid, queries, k, max_radius=float("inf"), ordered=True
     return ids, d2, nv
 
 
-def descent_leaf_d2(points, node_pid, queries) -> np.ndarray:
-    """FP32 squared distance to the point where the greedy close-child descent ends."""
+def descent_leaf_d2(points, node_pid, queries, node_dim=None) -> np.ndarray:
+    """FP32 squared distance to the point where the greedy close-child descent
+    ends; node_dim: the split dimension stored per node (build_widest), else
+    level mod D."""
     pts, qs = _f32(points), _f32(queries)
     node_pid = np.ascontiguousarray(node_pid, dtype=np.int32)
     N, D = pts.shape
+    dims = None if node_dim is None else np.ascontiguousarray(node_dim, dtype=np.uint8)
+    if dims is not None and dims.shape != (N,):
+        raise ValueError("node_dim must hold one dimension per node")
     lib = _load()
     out = np.empty(qs.shape[0], dtype=np.float32)
     for i in range(qs.shape[0]):
         qi = np.ascontiguousarray(qs[i])
-        out[i] = lib.orc_descent_leaf(_ptr(pts), _ptr(node_pid), N, D, _ptr(qi))
+        out[i] = lib.orc_descent_leaf(_ptr(pts), _ptr(node_pid), None if dims is None else _ptr(dims), N, D,
+                                      _ptr(qi))
     return out
 
 

@@ -628,13 +628,15 @@ int orc_knn_stackfree_batch(const float *pts, const int32_t *node_pid, int64_t N
 
 /* Greedy descent from the root, always to the close child (the child on the
  * query's side, Sec. 3.2 closeSide rule), until that child does not exist.
- * Returns the FP32 squared distance from q to the last valid node's point. */
-float orc_descent_leaf(const float *pts, const int32_t *node_pid, int64_t N, int D,
+ * Returns the FP32 squared distance from q to the last valid node's point.
+ * node_dim NULL: split dimension level mod D; else the dimension stored per
+ * node by orc_build_widest (Sec. 3.1's stored-split variant). */
+float orc_descent_leaf(const float *pts, const int32_t *node_pid, const uint8_t *node_dim, int64_t N, int D,
                        const float *q)
 {
     int64_t node = 0;
     for (;;) {
-        int dim = orc_level(node) % D;
+        int dim = node_dim ? node_dim[node] : orc_level(node) % D;
         float sd = q[dim] - pts[(int64_t)node_pid[node] * D + dim];
         int64_t child = 2 * node + 1 + (sd > 0.0f);
         if (child >= N)

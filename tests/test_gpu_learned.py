@@ -81,6 +81,27 @@ def test_descent_features_match_oracle(kdt, surface):
     assert np.allclose(f[:, 3], want, rtol=0, atol=4e-6 * np.maximum(1.0, np.abs(want)).max())
 
 
+def test_descent_features_stored_dims_match_oracle(kdt, surface):
+    """Features on a tree that stores each node's widest dimension: the
+    device descent reads the dimension kept in the node's id word; the
+    oracle descends its own widest-split tree with its recorded dimensions."""
+    pts, qs, _ = surface
+    sub = qs[:4000]
+    pid, dims = oracle.build_widest(pts)
+    tree = kdt.kdt_build(cu(pts), opts=kdt.KDT_BUILD_WIDEST)
+    try:
+        f = kdt.kdt_descent_features(tree, cu(sub)).cpu().numpy()
+        assert np.array_equal(kdt.kdt_tree_split_dims(tree).cpu().numpy(), dims)
+    finally:
+        tree.free()
+    assert np.array_equal(bits(f[:, :3]), bits(sub))
+    d2 = oracle.descent_leaf_d2(pts, pid, sub, node_dim=dims)
+    # the stored dimensions change the descent on this data
+    assert not np.array_equal(d2, oracle.descent_leaf_d2(pts, oracle.build(pts), sub))
+    want = np.log(np.maximum(d2, np.float32(1e-30)).astype(np.float64))
+    assert np.allclose(f[:, 3], want, rtol=0, atol=4e-6 * np.maximum(1.0, np.abs(want)).max())
+
+
 def test_mlp_forward_matches_oracle(kdt):
     """The inference forward (hidden layer on the tensor cores, BF16 operands,
     FP32 accumulation) against the oracle's FP64 model with the same

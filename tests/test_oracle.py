@@ -428,18 +428,47 @@ def test_descent_leaf_is_first_leaf_of_ordered_traversal():
         assert leaf_d2[i] == np.float32(np.float32(t[0] + t[1]) + t[2])
 
 
+@pytest.mark.parametrize("widest", [False, True])
 @pytest.mark.parametrize("N", [2, 3, 10, 255, 256, 1000])
-def test_descent_from_a_leaf_point_ends_on_it(N):
+def test_descent_from_a_leaf_point_ends_on_it(N, widest):
     """With distinct coordinates every split separates strictly, so a query
     equal to the point stored at a leaf follows the close child down to that
-    leaf (the last node N - 1 included) and finds distance 0."""
+    leaf (the last node N - 1 included) and finds distance 0; on a tree with
+    the split dimension stored per node only if the descent reads each node's
+    own dimension (the points are stretched along x, so the stored dimensions
+    differ from level mod D)."""
     g = np.random.default_rng(N)
-    pts = g.random((N, 3)).astype(np.float32)
-    pid = oracle.build(pts)
+    pts = (g.random((N, 3)) * np.array([8.0, 1.0, 0.25])).astype(np.float32)
+    dims = None
+    if widest:
+        pid, dims = oracle.build_widest(pts)
+        if N >= 255:
+            assert (dims != np.array([oracle_level(n) % 3 for n in range(N)])).mean() > 0.3
+    else:
+        pid = oracle.build(pts)
     leaves = [n for n in range(N) if 2 * n + 1 >= N]
     assert N - 1 in leaves
-    d2 = oracle.descent_leaf_d2(pts, pid, pts[pid[leaves]])
+    d2 = oracle.descent_leaf_d2(pts, pid, pts[pid[leaves]], node_dim=dims)
     assert (d2 == 0).all()
+
+
+def oracle_level(n: int) -> int:
+    return (n + 1).bit_length() - 1
+
+
+def test_descent_leaf_with_stored_dims_bounds_the_nearest():
+    """The descent ends on a point of the set, so its distance is at least the
+    brute-force nearest distance and equals it for queries at stored points;
+    with the level-mod-D dimensions passed explicitly it is the plain descent."""
+    pts, qs = synth.uniform_small(2000, 300)
+    pid, dims = oracle.build_widest(pts)
+    d2 = oracle.descent_leaf_d2(pts, pid, qs, node_dim=dims)
+    _, bd = oracle.knn_brute(pts, qs, 1)
+    assert (d2 >= bd[:, 0]).all() and (d2 > bd[:, 0]).any()
+    plain = oracle.build(pts)
+    lvl = np.array([oracle_level(n) % 3 for n in range(len(pts))], dtype=np.uint8)
+    assert np.array_equal(oracle.descent_leaf_d2(pts, plain, qs, node_dim=lvl).view(np.uint32),
+                          oracle.descent_leaf_d2(pts, plain, qs).view(np.uint32))
 
 
 # ---------------------------------------------------------------- MLP

@@ -196,8 +196,16 @@ MUTANTS = {
         "if (sd > 0.0f) {")],
     # learned-radius feature: the descent splits every level in dimension 0
     "descent_dim_zero": [(
-        "        int dim = orc_level(node) % D;",
-        "        int dim = 0;")],
+        "        int dim = node_dim ? node_dim[node] : orc_level(node) % D;",
+        "        int dim = node_dim ? node_dim[node] : 0;")],
+    # learned-radius feature on stored-split trees: the stored dimension ignored
+    "descent_ignores_stored_dim": [(
+        "        int dim = node_dim ? node_dim[node] : orc_level(node) % D;",
+        "        int dim = orc_level(node) % D;")],
+    # learned-radius feature on stored-split trees: the parent's dimension read
+    "descent_stored_dim_of_parent": [(
+        "        int dim = node_dim ? node_dim[node] : orc_level(node) % D;",
+        "        int dim = node_dim ? node_dim[node ? (node - 1) / 2 : 0] : orc_level(node) % D;")],
     # result emission: empty slots marked with id 0
     "empty_slot_id_zero": [(
         "            ids[i] = -1;\n            d2[i] = INFINITY;\n        }\n    }\n}",
