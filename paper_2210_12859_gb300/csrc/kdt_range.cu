@@ -31,6 +31,17 @@ namespace {
 constexpr int RANGE_THREADS = 128;
 // traversal steps between two claim rounds of a warp (as for kNN, 64 beats 16)
 constexpr int RANGE_CLAIM_STEPS = 64;
+// levels below a bottom node that one traversal step walks with it, per
+// processNode action.  Measured on the clustered 2^24 set (2^22 ball queries):
+// one level takes the count pass from 103 to 74 ms at r = 0.004 (3852 nodes
+// per query) and leaves it unchanged at r = 0.001 (172 nodes); two levels gain
+// more on long queries (59 ms) but cost registers, and so resident warps, on
+// short ones (+9 %).  The fill, whose hit staging already holds more
+// registers, is fastest without inlining at r = 0.001 and within 6 % of the
+// best at r = 0.004.
+constexpr int RANGE_COUNT_LEVELS = 1;
+constexpr int RANGE_FILL_LEVELS = 0;
+constexpr int RANGE_REDUCE_LEVELS = 1;
 enum : int { ACT_COUNT = 0, ACT_FILL = 1, ACT_REDUCE = 2 };
 // binary32 rounding of pi
 constexpr float PI_F = 3.14159265358979323846f;
@@ -81,51 +92,195 @@ __device__ __forceinline__ float finish_reduce(float s, int64_t n, int mode, flo
     return s;
 }
 
+// One lane's range query: the query box / ball and the processNode action's
+// state.  node() is processNode for a node entered from its parent; cull()
+// gives which children can hold a point in range (their existence is the
+// caller's test).  The fill's pending group of up to three hits waits in
+// registers (a staging buffer in shared memory measured slower: the carve-out
+// it takes shrinks the L1 that neighbouring lanes share nodes through).
+// fill: the last `ns` hits (ns < 4) not yet written, newest in the last slot
+template <bool FILL>
+struct FillStage {
+};
+template <>
+struct FillStage<true> {
+    int64_t base;
+    int32_t limit;
+    int32_t sid0, sid1, sid2, sid3;
+    float sd20, sd21, sd22, sd23;
+    int ns;
+};
+
+template <int LAYOUT, int KIND, int ACT>
+struct RangeLane : FillStage<ACT == ACT_FILL> {
+    static constexpr int NC = LayoutTraits<LAYOUT>::NC;
+    float lo[NC], hi[KIND == 1 ? NC : 1];
+    float acc[ACT == ACT_REDUCE ? KDT_PAYLOAD_MAX_C : 1];
+    int32_t count, visits;  // hits and nodes of one query are below N < 2^30
+
+    __device__ __forceinline__ void start(const RangeArgs &a, int64_t qi)
+    {
+        load_query<LAYOUT>(a.a, qi, a.D, lo);
+        if constexpr (KIND == 1)
+            load_query<LAYOUT>(a.b, qi, a.D, hi);
+        count = 0;
+        visits = 0;
+        if constexpr (ACT == ACT_FILL) {
+            this->base = a.offsets[qi];
+            // saturated: a slice longer than any hit count, or negative, still
+            // ends with count != limit and the range error
+            const int64_t len = a.offsets[qi + 1] - this->base;
+            this->limit = (int32_t)(len < 0 ? -1 : (len > INT32_MAX ? INT32_MAX : len));
+            this->ns = 0;
+        }
+        if constexpr (ACT == ACT_REDUCE) {
+#pragma unroll
+            for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                acc[c] = 0.f;
+        }
+    }
+
+    __device__ __forceinline__ void node(const RangeArgs &a, const NodeVal<LAYOUT> &nd, int n)
+    {
+        if constexpr (ACT == ACT_COUNT)
+            ++visits;
+        bool hit;
+        float d2 = 0.f;
+        if constexpr (KIND == 0) {
+            d2 = dist2<NC>(nd.c, lo);
+            hit = d2 <= a.r2;
+        } else {
+            hit = true;
+#pragma unroll
+            for (int j = 0; j < NC; ++j)
+                hit = hit && lo[j] <= nd.c[j] && nd.c[j] <= hi[j];
+        }
+        if (!hit)
+            return;
+        if constexpr (ACT == ACT_FILL) {
+            if (count < this->limit) {
+                const int32_t id = (int32_t)node_id<LAYOUT>(nd, a.ids, n);
+                const int64_t pos = this->base + count;
+                if (!a.vec_fill || (this->ns == 0 && (pos & 3) != 0)) {
+                    // before the slice's first 16-byte boundary (or unaligned outputs)
+                    a.out_ids[pos] = id;
+                    if (KIND == 0 && a.out_d2)
+                        a.out_d2[pos] = d2;
+                } else {
+                    this->sid0 = this->sid1; this->sid1 = this->sid2; this->sid2 = this->sid3; this->sid3 = id;
+                    this->sd20 = this->sd21; this->sd21 = this->sd22; this->sd22 = this->sd23; this->sd23 = d2;
+                    if (++this->ns == 4) {  // positions pos - 3 .. pos, pos - 3 on a 16-byte boundary
+                        *reinterpret_cast<int4 *>(a.out_ids + pos - 3) =
+                            make_int4(this->sid0, this->sid1, this->sid2, this->sid3);
+                        if (KIND == 0 && a.out_d2)
+                            *reinterpret_cast<float4 *>(a.out_d2 + pos - 3) =
+                                make_float4(this->sd20, this->sd21, this->sd22, this->sd23);
+                        this->ns = 0;
+                    }
+                }
+            }
+        }
+        if constexpr (ACT == ACT_REDUCE) {
+            const float *p = a.payload + (int64_t)n * a.C;
+#pragma unroll
+            for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                if (c < a.C)
+                    acc[c] = __fadd_rn(acc[c], __ldg(p + c));
+        }
+        ++count;
+    }
+
+    __device__ __forceinline__ void cull(const RangeArgs &a, const NodeVal<LAYOUT> &nd, int sdim, bool &left_ok,
+                                         bool &right_ok) const
+    {
+        const float split = select_dim<NC>(nd.c, sdim);
+        if constexpr (KIND == 0) {
+            const float sd = __fsub_rn(select_dim<NC>(lo, sdim), split);
+            const float sd2 = __fmul_rn(sd, sd);
+            left_ok = sd <= 0.f || sd2 <= a.r2;
+            right_ok = sd > 0.f || sd2 <= a.r2;
+        } else {
+            // left subtree coordinates are <= split, right ones >= split
+            left_ok = select_dim<NC>(lo, sdim) <= split;
+            right_ok = select_dim<NC>(hi, sdim) >= split;
+        }
+    }
+
+    // the query's end: the last partial group of the fill, the count or the
+    // reduction written out
+    __device__ __forceinline__ void finish(const RangeArgs &a, int64_t qi)
+    {
+        if constexpr (ACT == ACT_FILL) {
+            // the newest ns hits end at position base + min(count, limit) - 1
+            const int64_t end = this->base + (count < this->limit ? count : this->limit);
+            if (this->ns >= 3) {
+                a.out_ids[end - 3] = this->sid1;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 3] = this->sd21;
+            }
+            if (this->ns >= 2) {
+                a.out_ids[end - 2] = this->sid2;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 2] = this->sd22;
+            }
+            if (this->ns >= 1) {
+                a.out_ids[end - 1] = this->sid3;
+                if (KIND == 0 && a.out_d2)
+                    a.out_d2[end - 1] = this->sd23;
+            }
+            this->ns = 0;
+            if (count != this->limit)
+                atomicOr(a.err, ERR_RANGE);
+        } else {
+            if (a.counts)
+                a.counts[qi] = ACT == ACT_COUNT && a.count_visits ? visits : count;
+            if constexpr (ACT == ACT_REDUCE) {
+#pragma unroll
+                for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
+                    if (c < a.C)
+                        a.out[qi * a.C + c] = finish_reduce(acc[c], count, a.mode, a.r2);
+            }
+        }
+    }
+};
+
 // KIND 0: ball of squared radius r2 around a[q]; KIND 1: box [a[q], b[q]].
 // Persistent blocks; every lane claims its next query when its current one
 // ends (checked every RANGE_CLAIM_STEPS steps), as in the kNN kernel; the step
-// bound 3N + 3 is checked once per round.
+// bound 3N + 3 is checked once per round.  A node entered from its parent
+// whose subtree spans at most L + 1 levels (L the action's level constant; index >=
+// floor(N / 2^(L+1)) for L levels below it: its leftmost descendant L + 1
+// levels down, 2^(L+1) (i + 1) - 1, does not exist) is walked whole in one
+// step: its descendants are loaded together, then entered in the machine's
+// order (node, left subtree, right subtree) under the same cull tests, and
+// the step returns to the parent as the machine would after the node's right
+// subtree.  Hits, their order and the processed nodes are those of the
+// one-node-per-step machine.
 template <int LAYOUT, int KIND, int ACT>
 __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
 {
-    constexpr int NC = LayoutTraits<LAYOUT>::NC;
+    // levels below a node walked within its step (two float4 per node in layout 2: no inlining there)
+    constexpr int LEVELS =
+        ACT == ACT_COUNT ? RANGE_COUNT_LEVELS : (ACT == ACT_FILL ? RANGE_FILL_LEVELS : RANGE_REDUCE_LEVELS);
+    constexpr int INL = LAYOUT != 2 ? LEVELS : 0;
+    RangeLane<LAYOUT, KIND, ACT> L;
     int64_t qi = -1;
     bool exhausted = false;
-    float lo[NC], hi[NC];
-    float acc[KDT_PAYLOAD_MAX_C];
     int curr = 0, prev = -1, dim = 0;
     uint32_t steps = 0;
-    int64_t count = 0, base = 0, limit = 0, visits = 0;
-    // fill: the last `ns` hits (ns < 4) not yet written, newest in the last slot
-    int32_t sid0 = 0, sid1 = 0, sid2 = 0, sid3 = 0;
-    float sd20 = 0.f, sd21 = 0.f, sd22 = 0.f, sd23 = 0.f;
-    int ns = 0;
     const uint32_t cap = 3u * (uint32_t)a.N + 3u;
+    const int last = a.N - 1, bottom = a.N >> (INL + 1);
     for (;;) {
         const bool need = qi < 0 && !exhausted;
         const int64_t slot = claim_slot(need, a.counter);
         if (need) {
             if (slot < a.Q) {
                 qi = a.perm ? (int64_t)a.perm[slot] : slot;
-                load_query<LAYOUT>(a.a, qi, a.D, lo);
-                if (KIND == 1)
-                    load_query<LAYOUT>(a.b, qi, a.D, hi);
+                L.start(a, qi);
                 curr = 0;
                 prev = -1;
                 dim = 0;
                 steps = 0;
-                count = 0;
-                visits = 0;
-                if (ACT == ACT_FILL) {
-                    base = a.offsets[qi];
-                    limit = a.offsets[qi + 1] - base;
-                    ns = 0;
-                }
-                if (ACT == ACT_REDUCE) {
-#pragma unroll
-                    for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
-                        acc[c] = 0.f;
-                }
             } else {
                 exhausted = true;
             }
@@ -143,75 +298,62 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
             ++steps;
             const NodeVal<LAYOUT> nd = fetch<LAYOUT, false>(a.nodes, nullptr, 0, curr);
             const bool from_parent = prev < curr;
-            if (from_parent) {
-                if (ACT == ACT_COUNT)
-                    ++visits;
-                bool hit;
-                float d2 = 0.f;
-                if constexpr (KIND == 0) {
-                    d2 = dist2<NC>(nd.c, lo);
-                    hit = d2 <= a.r2;
-                } else {
-                    hit = true;
-#pragma unroll
-                    for (int j = 0; j < NC; ++j)
-                        hit = hit && lo[j] <= nd.c[j] && nd.c[j] <= hi[j];
-                }
-                if (hit) {
-                    if (ACT == ACT_FILL && count < limit) {
-                        const int32_t id = (int32_t)node_id<LAYOUT>(nd, a.ids, curr);
-                        const int64_t pos = base + count;
-                        if (!a.vec_fill || (ns == 0 && (pos & 3) != 0)) {
-                            // before the slice's first 16-byte boundary (or unaligned outputs)
-                            a.out_ids[pos] = id;
-                            if (KIND == 0 && a.out_d2)
-                                a.out_d2[pos] = d2;
-                        } else {
-                            sid0 = sid1; sid1 = sid2; sid2 = sid3; sid3 = id;
-                            sd20 = sd21; sd21 = sd22; sd22 = sd23; sd23 = d2;
-                            if (++ns == 4) {  // positions pos - 3 .. pos, pos - 3 on a 16-byte boundary
-                                *reinterpret_cast<int4 *>(a.out_ids + pos - 3) = make_int4(sid0, sid1, sid2, sid3);
-                                if (KIND == 0 && a.out_d2)
-                                    *reinterpret_cast<float4 *>(a.out_d2 + pos - 3) =
-                                        make_float4(sd20, sd21, sd22, sd23);
-                                ns = 0;
-                            }
-                        }
-                    }
-                    if (ACT == ACT_REDUCE) {
-                        const float *p = a.payload + (int64_t)curr * a.C;
-#pragma unroll
-                        for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
-                            if (c < a.C)
-                                acc[c] = __fadd_rn(acc[c], __ldg(p + c));
-                    }
-                    ++count;
-                }
-            }
-            const int sdim = split_dim_of<LAYOUT>(nd, dim);
-            const float split = select_dim<NC>(nd.c, sdim);
-            bool left_ok, right_ok;
-            if constexpr (KIND == 0) {
-                const float sd = __fsub_rn(select_dim<NC>(lo, sdim), split);
-                const float sd2 = __fmul_rn(sd, sd);
-                left_ok = sd <= 0.f || sd2 <= a.r2;
-                right_ok = sd > 0.f || sd2 <= a.r2;
-            } else {
-                // left subtree coordinates are <= split, right ones >= split
-                left_ok = select_dim<NC>(lo, sdim) <= split;
-                right_ok = select_dim<NC>(hi, sdim) >= split;
-            }
             const int lc = 2 * curr + 1, rc = lc + 1;
             const int parent = (curr - 1) >> 1;
-            left_ok = left_ok && lc < a.N;
-            right_ok = right_ok && rc < a.N;
             int next;
-            if (from_parent)
-                next = left_ok ? lc : (right_ok ? rc : parent);
-            else if (prev == lc)
-                next = right_ok ? rc : parent;
-            else
+            if (INL > 0 && from_parent && curr >= bottom) {
+                // children lc, rc (one 32-byte sector); with two levels also
+                // the grandchildren 2 lc + 1 .. 2 rc + 2 (indices clamped to
+                // the last node for the loads, tested before use)
+                const int c1 = min(lc, last), c2 = min(rc, last);
+                const NodeVal<LAYOUT> n1 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, c1);
+                const NodeVal<LAYOUT> n2 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, c2);
+                NodeVal<LAYOUT> m1, m2, m3, m4;
+                if constexpr (INL >= 2) {
+                    m1 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, min(2 * c1 + 1, last));
+                    m2 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, min(2 * c1 + 2, last));
+                    m3 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, min(2 * c2 + 1, last));
+                    m4 = fetch<LAYOUT, false>(a.nodes, nullptr, 0, min(2 * c2 + 2, last));
+                }
+                const int dim1 = dim + 1 == a.D ? 0 : dim + 1;
+                bool l, r, l1, r1;
+                L.node(a, nd, curr);
+                L.cull(a, nd, split_dim_of<LAYOUT>(nd, dim), l, r);
+                if (l && lc < a.N) {
+                    L.node(a, n1, lc);
+                    if constexpr (INL >= 2) {
+                        L.cull(a, n1, split_dim_of<LAYOUT>(n1, dim1), l1, r1);
+                        if (l1 && 2 * lc + 1 < a.N)
+                            L.node(a, m1, 2 * lc + 1);
+                        if (r1 && 2 * lc + 2 < a.N)
+                            L.node(a, m2, 2 * lc + 2);
+                    }
+                }
+                if (r && rc < a.N) {
+                    L.node(a, n2, rc);
+                    if constexpr (INL >= 2) {
+                        L.cull(a, n2, split_dim_of<LAYOUT>(n2, dim1), l1, r1);
+                        if (l1 && 2 * rc + 1 < a.N)
+                            L.node(a, m3, 2 * rc + 1);
+                        if (r1 && 2 * rc + 2 < a.N)
+                            L.node(a, m4, 2 * rc + 2);
+                    }
+                }
                 next = parent;
+            } else {
+                if (from_parent)
+                    L.node(a, nd, curr);
+                bool left_ok, right_ok;
+                L.cull(a, nd, split_dim_of<LAYOUT>(nd, dim), left_ok, right_ok);
+                left_ok = left_ok && lc < a.N;
+                right_ok = right_ok && rc < a.N;
+                if (from_parent)
+                    next = left_ok ? lc : (right_ok ? rc : parent);
+                else if (prev == lc)
+                    next = right_ok ? rc : parent;
+                else
+                    next = parent;
+            }
             if (next < 0) {
                 done = true;
                 break;
@@ -225,37 +367,7 @@ __global__ void __launch_bounds__(RANGE_THREADS) range_kernel(const RangeArgs a)
         }
         if (!done)
             continue;
-        if (ACT == ACT_FILL) {
-            // the last partial group: the newest ns hits end at position base + min(count, limit) - 1
-            const int64_t end = base + (count < limit ? count : limit);
-            if (ns >= 3) {
-                a.out_ids[end - 3] = sid1;
-                if (KIND == 0 && a.out_d2)
-                    a.out_d2[end - 3] = sd21;
-            }
-            if (ns >= 2) {
-                a.out_ids[end - 2] = sid2;
-                if (KIND == 0 && a.out_d2)
-                    a.out_d2[end - 2] = sd22;
-            }
-            if (ns >= 1) {
-                a.out_ids[end - 1] = sid3;
-                if (KIND == 0 && a.out_d2)
-                    a.out_d2[end - 1] = sd23;
-            }
-            ns = 0;
-            if (count != limit)
-                atomicOr(a.err, ERR_RANGE);
-        } else {
-            if (a.counts)
-                a.counts[qi] = (int32_t)(ACT == ACT_COUNT && a.count_visits ? visits : count);
-            if (ACT == ACT_REDUCE) {
-#pragma unroll
-                for (int c = 0; c < KDT_PAYLOAD_MAX_C; ++c)
-                    if (c < a.C)
-                        a.out[qi * a.C + c] = finish_reduce(acc[c], count, a.mode, a.r2);
-            }
-        }
+        L.finish(a, qi);
         qi = -1;
     }
 }
