@@ -264,6 +264,33 @@ def run_config(args):
                              "unit": "GB/s", "frac": fill_bytes / (fill_ms / 1e3) / 1e9 / hbm,
                              "bytes_per_query": fill_bytes / nq},
               oracle_sample_sets_equal=ok)
+        # long queries: r = 0.004 reaches ~1400 points and ~3900 nodes per query
+        rl = 0.004
+        lcnt_ms = timeit(lambda: kdt.kdt_radius_count(tree, dq, rl, F), 3)
+        lcounts = kdt.kdt_radius_count(tree, dq, rl, F)
+        loff, ltotal = kdt.kdt_offsets(lcounts)
+        lfill_ms = timeit(lambda: kdt.kdt_radius_fill(tree, dq, rl, loff, ltotal, True, F), 3)
+        lids, ld2 = kdt.kdt_radius_fill(tree, dq, rl, loff, ltotal, True, F)
+        kdt.kdt_status(tree)
+        lo_h = loff.cpu().numpy()
+        lsample = sample[:16]
+        _, lwoff, lwids, _ = oracle.radius_brute(pts, qs[lsample], rl)
+        # only the sampled slices come back (the whole hit list is ~24 GB)
+        lok = all(np.array_equal(np.sort(lids[int(lo_h[q]):int(lo_h[q + 1])].cpu().numpy()),
+                                 lwids[lwoff[j]:lwoff[j + 1]]) for j, q in enumerate(lsample))
+        del ld2
+        lvisits = kdt.kdt_radius_count(tree, dq, rl, F | kdt.KDT_RANGE_VISITS).double().sum().item()
+        lbytes = nq * (12 + 16) + 16.0 * lvisits + 8.0 * ltotal
+        _emit(config=f"range: gmm N=2^24, Q=2^22 (90% mixture, 10% uniform), ball r={rl}",
+              form="ball count / offsets / fill (long queries)", queries_per_s=nq / ((lcnt_ms + lfill_ms) / 1e3),
+              hits=int(ltotal), hits_per_query=ltotal / nq, count_ms=lcnt_ms, fill_ms=lfill_ms,
+              visits_per_query=lvisits / nq,
+              roofline_count={"bound": "hbm", "achieved": (nq * 16 + 16.0 * lvisits) / (lcnt_ms / 1e3) / 1e9,
+                              "peak": hbm, "unit": "GB/s",
+                              "frac": (nq * 16 + 16.0 * lvisits) / (lcnt_ms / 1e3) / 1e9 / hbm},
+              roofline_fill={"bound": "hbm", "achieved": lbytes / (lfill_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": lbytes / (lfill_ms / 1e3) / 1e9 / hbm, "bytes_per_query": lbytes / nq},
+              oracle_sample_sets_equal=lok)
         lo, hi = (dq - r).contiguous(), (dq + r).contiguous()
         bc_ms = timeit(lambda: kdt.kdt_box_count(tree, lo, hi, F), 3)
         bcounts = kdt.kdt_box_count(tree, lo, hi, F)

@@ -292,8 +292,11 @@ typedef struct kdt_train_opts {
                              and of the learned forms (all queries gated, the far ones) are counted,
                              and the network pass's cost per gated query is measured in
                              processed-node equivalents (its time per query over the plain
-                             traversal's time per processed node); the form that saves the most
-                             nodes net of that cost is kept, KDT_GATE_NONE when none saves any) */
+                             traversal's time per processed node); a gated call's nodes are
+                             charged 1.08 plain nodes each (the bounded pass's measured
+                             per-node overhead, rounded up); the form that saves the most
+                             nodes net of these costs is kept, KDT_GATE_NONE when none saves
+                             any) */
     int query_flags;      /* flags of the queries the automatic gate is judged with (default
                              KDT_MORTON | KDT_COST_ORDER) */
 } kdt_train_opts;

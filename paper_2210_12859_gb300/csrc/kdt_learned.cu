@@ -465,8 +465,15 @@ int choose_gate(kdt_tree *t, const float *d_q, int64_t n, int k, int qflags, cud
         return rc;
     // network pass per query, in processed-node equivalents of the plain traversal
     const double c = (t_net / (double)n) / (t_plain / std::max(v_plain, 1.0));
-    const double score_all = (v_plain - v_all) - c * (double)n;
-    const double score_far = (v_plain - v_far) - c * n_far;
+    // every query of a gated call, gated or not, runs in the bounded pass, and
+    // a node there costs more than one of the plain traversal (restart state
+    // and its registers): fitted to two full-size forms (clustered k = 8 with
+    // the far gate, surface k = 32 with every query gated) as 5.9 % per node
+    // beside a fixed per-query part, taken as 8 % so that a gate is chosen
+    // only for a clear saving
+    constexpr double BOUNDED_NODE_COST = 1.08;
+    const double score_all = v_plain - BOUNDED_NODE_COST * v_all - c * (double)n;
+    const double score_far = v_plain - BOUNDED_NODE_COST * v_far - c * n_far;
     int best = KDT_GATE_NONE;
     double best_score = 0.0;
     if (score_all > best_score) {
