@@ -481,6 +481,8 @@ def main():
         e2e_s = max_over_ranks(statistics.median(ts), dist, dev)
         e2e = {"value": world * n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(pts.nbytes + qs.nbytes),
                "d2h_bytes_per_step": int(hi.numel() * 4 + hd.numel() * 4), "seconds": e2e_s,
+               "transfer": "pinned host buffers: points copied to the device, queries read and results written "
+                           "in place by the query kernels through the host link",
                "identical": bool(np.array_equal(hi.numpy(), res_i))}
 
     if rank == 0:

@@ -230,10 +230,13 @@ int kdt_status(kdt_tree *tree, void *stream);
 /* Release a tree and its device memory (synchronises the device first). */
 void kdt_free(kdt_tree *tree);
 
-/* One call from host memory to host memory: copies h_points and h_queries to
- * the device, builds the tree, runs kdt_knn, copies the results back into
+/* One call from host memory to host memory: copies h_points to the device,
+ * builds the tree, runs kdt_knn on h_queries and writes the results into
  * h_ids int32 [Q][k] and h_d2 float32 [Q][k], and frees everything.
- * Synchronous.  Page-locked host buffers copy fastest. */
+ * Synchronous.  Page-locked (pinned or registered) query and result buffers
+ * are used in place: the query kernels read the queries and store the results
+ * through the host link themselves, with no staging copy; other host buffers
+ * are copied to and from device scratch. */
 int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_queries, int64_t Q,
                  int k, float max_radius, int flags, int32_t *h_ids, float *h_d2);
 

@@ -604,6 +604,18 @@ void kdt_free(kdt_tree *t)
     delete t;
 }
 
+// device address of a host buffer the GPU can address directly (page-locked
+// or registered host memory), else NULL; unregistered memory is copied
+static void *mapped_host(const void *p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_q, int64_t Q, int k, float max_radius,
                  int flags, int32_t *h_ids, float *h_d2)
 {
@@ -620,17 +632,24 @@ int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_q, int6
     int rc = KDT_OK;
     kdt_tree *t = nullptr;
     {
+        // page-locked queries are read and page-locked outputs written in
+        // place through the host link (the kernels' own loads and stores,
+        // spread over the query launch); other host buffers are copied
+        float *mq = Q > 0 ? (float *)mapped_host(h_q) : nullptr;
+        int32_t *mi = Q > 0 ? (int32_t *)mapped_host(h_ids) : nullptr;
+        float *md = Q > 0 ? (float *)mapped_host(h_d2) : nullptr;
+        const bool direct_out = mi && md;
         Scratch sc(s);
-        size_t pb = (size_t)N * D * 4, qb = (size_t)Q * D * 4, ob = (size_t)Q * k * 4;
+        size_t pb = (size_t)N * D * 4, qb = mq ? 0 : (size_t)Q * D * 4, ob = direct_out ? 0 : (size_t)Q * k * 4;
         rc = sc.alloc(carve_size({pb, qb, ob, ob}));
         if (rc == KDT_OK) {
             Carve c{(char *)sc.p};
             float *dp = c.take<float>((size_t)N * D);
-            float *dq = c.take<float>((size_t)Q * D);
-            int32_t *di = c.take<int32_t>((size_t)Q * k);
-            float *dd = c.take<float>((size_t)Q * k);
+            float *dq = mq ? mq : c.take<float>((size_t)Q * D);
+            int32_t *di = direct_out ? mi : c.take<int32_t>((size_t)Q * k);
+            float *dd = direct_out ? md : c.take<float>((size_t)Q * k);
             cudaError_t e = cudaMemcpyAsync(dp, h_points, pb, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess && Q > 0)
+            if (e == cudaSuccess && Q > 0 && !mq)
                 e = cudaMemcpyAsync(dq, h_q, qb, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess)
                 rc = cuda_error(e, "host to device copy", __FILE__, __LINE__);
@@ -638,7 +657,7 @@ int kdt_knn_host(const float *h_points, int64_t N, int D, const float *h_q, int6
                 rc = kdt_build_ex(dp, N, D, 0, s, &t);
             if (rc == KDT_OK && Q > 0)
                 rc = kdt_knn(t, dq, Q, k, max_radius, flags, di, dd, s);
-            if (rc == KDT_OK && Q > 0) {
+            if (rc == KDT_OK && Q > 0 && !direct_out) {
                 e = cudaMemcpyAsync(h_ids, di, ob, cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(h_d2, dd, ob, cudaMemcpyDeviceToHost, s);

@@ -178,6 +178,8 @@ def _host(a, dtype, name: str) -> tuple:
     if isinstance(a, torch.Tensor):
         if a.is_cuda:
             raise TypeError(f"{name} must be a host array")
+        if a.dtype != {np.float32: torch.float32, np.int32: torch.int32}[dtype]:
+            raise TypeError(f"{name} must be {np.dtype(dtype).name}, got {a.dtype}")
         if not a.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
         return ctypes.c_void_p(a.data_ptr()), a

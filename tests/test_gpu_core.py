@@ -232,6 +232,28 @@ def test_host_entry_point(kdt):
     assert np.array_equal(ids, wi) and np.array_equal(bits(d2), bits(wd))
 
 
+@pytest.mark.parametrize("k", [8, 5])
+@pytest.mark.parametrize("pin", ["all", "queries", "outputs", "none", "unaligned"])
+def test_host_entry_point_in_place(kdt, pin, k):
+    """Page-locked query and result buffers are used in place (the kernels
+    read and write host memory); pageable ones are copied; a result buffer
+    off a 16-byte boundary takes the word stores.  Same results each way."""
+    pts, qs = synth.uniform_small(6000, 2500)
+    pq = torch.from_numpy(qs)
+    if pin in ("all", "queries"):
+        pq = pq.pin_memory()
+    pinned_out = pin in ("all", "outputs", "unaligned")
+    ids = torch.empty(2500 * k + 1, dtype=torch.int32)
+    d2 = torch.empty(2500 * k + 1, dtype=torch.float32)
+    if pinned_out:
+        ids, d2 = ids.pin_memory(), d2.pin_memory()
+    o = 1 if pin == "unaligned" else 0
+    oi, od = ids[o:o + 2500 * k].view(2500, k), d2[o:o + 2500 * k].view(2500, k)
+    kdt.kdt_knn_host(pts, pq, k, out_ids=oi, out_d2=od, flags=kdt.KDT_MORTON)
+    wi, wd = oracle.knn_brute(pts, qs, k)
+    assert np.array_equal(oi.numpy(), wi) and np.array_equal(bits(od.numpy()), bits(wd))
+
+
 def test_fp64_cross_check(kdt, small):
     pts, qs, tree, dq, _ = small
     sub = slice(0, 1024)
