@@ -187,6 +187,20 @@ def _host(a, dtype, name: str) -> tuple:
     return ctypes.c_void_p(arr.ctypes.data), arr
 
 
+def _host_out(a, dtype, name: str, shape) -> ctypes.c_void_p:
+    """An output host array is written in place: it must already have the
+    dtype, shape and contiguous layout (no converted copy to lose results in)."""
+    if isinstance(a, torch.Tensor):
+        p, t = _host(a, dtype, name)
+    else:
+        if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{name} must be a C-contiguous {np.dtype(dtype).name} array")
+        p, t = ctypes.c_void_p(a.ctypes.data), a
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return p
+
+
 class Tree:
     """A library-owned tree (``kdt_tree*``); freed with ``kdt_free``."""
 
@@ -470,8 +484,10 @@ def kdt_knn_host(points, queries, k: int, max_radius: float = math.inf, flags: i
         out_ids = np.empty((Q, k), dtype=np.int32)
     if out_d2 is None:
         out_d2 = np.empty((Q, k), dtype=np.float32)
-    ip, _ = _host(out_ids, np.int32, "out_ids")
-    dp, _ = _host(out_d2, np.float32, "out_d2")
+    if Q > 0 and (qk.ndim != 2 or qk.shape[1] != D):
+        raise ValueError(f"queries must be [Q, {D}]")
+    ip = _host_out(out_ids, np.int32, "out_ids", (Q, k))
+    dp = _host_out(out_d2, np.float32, "out_d2", (Q, k))
     _check(_lib.kdt_knn_host(pp, N, D, qp, Q, k, float(max_radius), flags, ip, dp))
     return out_ids, out_d2
 

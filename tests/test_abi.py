@@ -126,3 +126,24 @@ def test_binding_without_library_raises(tmp_path):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_host_entry_outputs_are_written_in_place_or_rejected():
+    """kdt_knn_host writes into the caller's arrays: an output of the wrong
+    dtype, layout or shape is rejected before the call (a converted copy would
+    receive the results and drop them)."""
+    import numpy as np
+
+    from paper_2210_12859_gb300 import kdt
+
+    pts = np.zeros((16, 3), np.float32)
+    qs = np.zeros((4, 3), np.float32)
+    good_i, good_d = np.empty((4, 2), np.int32), np.empty((4, 2), np.float32)
+    with pytest.raises(TypeError):
+        kdt.kdt_knn_host(pts, qs, 2, out_ids=np.empty((4, 2), np.int64), out_d2=good_d)
+    with pytest.raises(TypeError):
+        kdt.kdt_knn_host(pts, qs, 2, out_ids=good_i, out_d2=np.empty((2, 4), np.float32).T)
+    with pytest.raises(ValueError):
+        kdt.kdt_knn_host(pts, qs, 2, out_ids=np.empty((4, 3), np.int32), out_d2=good_d)
+    with pytest.raises(ValueError):
+        kdt.kdt_knn_host(pts, np.zeros((4, 2), np.float32), 2, out_ids=good_i, out_d2=good_d)
